@@ -1,0 +1,395 @@
+"""Benchmark of the linear-complexity Silhouette on one GB300 (or N replicas).
+
+Headline workload (one step = one pass of the whole forward hot path:
+sil_aggregate + sil_score = pass 1, finalisation, pass 2, s_i and S):
+  at_scale: N = 10,000,000 points, D = 64, K = 100 clusters, FP32 Gaussian
+  blobs (centres U[-5,5]^D, sigma 1, truncated rank-Zipf(1.1) sizes, shuffled),
+  squared Euclidean distance.
+Metric: points/s (whole job).  Beside it, per pass: achieved HBM GB/s and the
+roofline of the dominant kernel, the same step through host buffers (e2e),
+the FP64 oracle's linear form on the host cores (cpu_baseline), and variant
+lines (cosine, BF16 storage, fwd+bwd ms, batched labelings, the 1e8-point
+precision workload) measured in the same run.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Multi-GPU runs (torchrun) are replicas: every rank scores its own copy of the
+workload with no data-path collective ("scaling": "weak").
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Silhouette points/s & HBM GB/s, FP32 vs BF16 at |ΔS|≤1e-4; fwd+bwd ms"
+WORKLOAD = {"workload": "at_scale Gaussian blobs, sq-Euclidean", "N": 10_000_000, "D": 64, "K": 100,
+            "sizes": "rank-Zipf(1.1)", "storage": "fp32"}
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return {"hbm_gbs": float(d["hbm_gbs"]), "bf16_tflops": float(d["bf16_tflops"]),
+                "bf16_tflops_sustained": float(d.get("bf16_tflops_sustained", d["bf16_tflops"])),
+                "sm_max_mhz": float(d.get("sm_max_mhz", 2070.0)), "source": "measured"}
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+            "sm_max_mhz": 2070.0, "source": "fallback"}
+
+
+# FP32 FFMA peak of a GB300: 152 SMs x 128 FP32 lanes x 2 flop x SM clock.
+def ffma_peak_tflops(sm_mhz: float) -> float:
+    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+class ClockSampler:
+    """nvidia-smi samples (every 200 ms) while the timed region runs."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup(n_gpus):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def cpu_oracle_sample(X_host, labels_host, K, metric="sqeuclidean", target_s=12.0):
+    """Time the FP64 oracle's linear form (aggregate + score) on a row sample."""
+    import numpy as np
+    import oracle
+    M = min(200_000, X_host.shape[0])
+    while True:
+        Xs = X_host[:M].astype(np.float64)
+        ls = labels_host[:M]
+        t0 = time.perf_counter()
+        r = oracle.linear(Xs, ls, K, metric)
+        dt = time.perf_counter() - t0
+        if dt * 3 > target_s or M >= X_host.shape[0]:
+            break
+        M = min(X_host.shape[0], int(M * max(2.0, target_s / max(dt, 1e-3) * 0.8)))
+    return {"value": M / dt, "unit": "points/s", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"first {M} rows of the workload as a dataset of their own: FP64 aggregates "
+                      f"(Eq. 6/8) + linear scoring (Eq. 11) of every sampled point, {dt:.2f} s",
+            "S_sample": r["S"]}
+
+
+def run_reference(args):
+    """--impl reference: the FP64 oracle (linear form) on the host cores."""
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import numpy as np
+    import oracle
+    from paper_2303_14102_gb300 import synth
+    M = 300_000
+    w = synth.workload_at_scale(device="cpu", N=M)  # same recipe and seed, first-M sample
+    X = w.X.double().numpy()
+    lab = w.labels.numpy()
+    for _ in range(args.warmup):
+        oracle.linear(X[:20000], lab[:20000], w.K)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.linear(X, lab, w.K)
+    dt = time.perf_counter() - t0
+    v = M * args.steps / dt
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "points/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": dict(WORKLOAD, sample_rows=M),
+            "cpu_baseline": {"value": v, "unit": "points/s", "cores": oracle.num_threads(),
+                             "kind": "oracle",
+                             "sample": f"{M} points of the at_scale recipe per step: FP64 aggregates + "
+                                       f"linear scoring on the host cores"},
+            "e2e": {"value": v, "unit": "points/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def timed(fn, steps, stream):
+    import torch
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for _ in range(steps):
+        fn()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    return ev0.elapsed_time(ev1) / 1e3
+
+
+def variant_lines(dev, steps, budget_s):
+    """Secondary measurements, each bounded in time."""
+    import torch
+    from paper_2303_14102_gb300 import sil, synth
+    from paper_2303_14102_gb300.autograd import silhouette_loss
+    out = {}
+    t_start = time.time()
+
+    def left():
+        return budget_s - (time.time() - t_start)
+
+    # fwd+bwd on the differentiation workload (N=1e6, D=256, K=1000 unit-normalised)
+    if left() > 0:
+        w = synth.workload_grad(device=dev)
+        X, lab = w.X, w.labels
+        for metric in ("sqeuclidean", "cosine"):
+            def step():
+                Xg = X.detach().requires_grad_(True)
+                S = silhouette_loss(Xg, lab, w.K, metric)
+                S.backward()
+            step()
+            n = max(1, min(steps, 3))
+            s = timed(step, n, torch.cuda.current_stream())
+            out[f"fwd_bwd_grad_{metric}"] = {"ms": s / n * 1e3, "N": 1_000_000, "D": 256, "K": 1000}
+        del X, lab, w
+        torch.cuda.empty_cache()
+    # batched labelings (N=2e6, D=32, B=256, k ~ U{2..512})
+    if left() > 0:
+        X, labs, ks = synth.workload_batched(device=dev)
+        sil.score_batched(X, labs, ks)
+        s = timed(lambda: sil.score_batched(X, labs, ks), 1, torch.cuda.current_stream())
+        out["batched"] = {"labelings_per_s": len(ks) / s, "point_labelings_per_s": len(ks) * X.shape[0] / s,
+                          "ms": s * 1e3, "N": X.shape[0], "D": 32, "B": len(ks), "sum_k": int(sum(ks))}
+        del X, labs
+        torch.cuda.empty_cache()
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--variants", type=int, default=1, help="also measure the variant lines")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+    from paper_2303_14102_gb300 import sil, synth
+
+    world, rank, local = dist_setup(args.gpus)
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    sil.load()
+    pk = peaks()
+    w = synth.workload_at_scale(device=dev)
+    X, lab, K = w.X, w.labels, w.K
+    N, D = X.shape
+    stream = torch.cuda.current_stream(dev)
+    status = sil.new_status(dev)
+
+    # one step: pass 1 + pass 2 (sq-Euclidean), events between the two calls
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    agg_buf = (torch.zeros(K, dtype=torch.int64, device=dev), torch.zeros(K, D, dtype=torch.float64, device=dev),
+               torch.zeros(K, dtype=torch.float64, device=dev))
+
+    def step(record=None):
+        if record is not None:
+            ev[0].record(stream)
+        agg = sil.aggregate(X, lab, K, out=agg_buf, status=status)
+        if record is not None:
+            ev[1].record(stream)
+        r = sil.score(X, lab, K, agg, status=status)
+        if record is not None:
+            ev[2].record(stream)
+            torch.cuda.synchronize()
+            record.append((ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])))
+        return r
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    sil.check_status(status, "bench warm-up")
+
+    barrier(world)
+    with ClockSampler(dev.index) as clk:
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            r = step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+        t = e0.elapsed_time(e1) / 1e3
+        # per-pass split (same launches, events between the two calls)
+        split = []
+        for _ in range(args.steps):
+            step(record=split)
+    clocks = clk.summary()
+    t = max_over_ranks(t, world)
+    S_val = float(r.S.item())
+    sil.check_status(status, "bench")
+    value = N * args.steps * world / t
+    ms_pass1 = statistics.mean(s[0] for s in split)
+    ms_pass2 = statistics.mean(s[1] for s in split)
+
+    # roofline of the dominant kernel (the longer pass)
+    bytes_pass1 = N * D * 4 + N * 4          # one read of X and labels
+    bytes_pass2 = N * D * 4 + N * 4          # one read of X and labels
+    flops_pass2 = 2.0 * N * K * D            # the K dot products per point
+    sm_mhz = clocks["sm_mhz"] or pk["sm_max_mhz"]
+    if ms_pass2 >= ms_pass1:
+        achieved = flops_pass2 / (ms_pass2 / 1e3) / 1e12
+        peak = ffma_peak_tflops(pk["sm_max_mhz"])
+        roof = {"kernel": "k_score_simt (pass 2)", "bound": "alu", "achieved": achieved, "peak": peak,
+                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x max SM clock (derived)",
+                "algorithmic": f"2*N*K*D = {flops_pass2:.3e} flop per launch"}
+    else:
+        achieved = bytes_pass1 / (ms_pass1 / 1e3) / 1e9
+        roof = {"kernel": "k_aggregate (pass 1)", "bound": "hbm", "achieved": achieved,
+                "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": achieved / pk["hbm_gbs"], "traffic": None,
+                "peak_source": f"{pk['source']} copy bandwidth",
+                "algorithmic": f"N*(4D+4) = {bytes_pass1:.3e} B per launch"}
+    pass_info = {"pass1_ms": ms_pass1, "pass1_hbm_gbs": bytes_pass1 / (ms_pass1 / 1e3) / 1e9,
+                 "pass2_ms": ms_pass2, "pass2_hbm_gbs": bytes_pass2 / (ms_pass2 / 1e3) / 1e9,
+                 "pass2_tflops": flops_pass2 / (ms_pass2 / 1e3) / 1e12}
+
+    # end to end through the public API from pinned host buffers
+    Xh = X.cpu().pin_memory()
+    lh = lab.cpu().pin_memory()
+    Xd = torch.empty_like(X)
+    ld = torch.empty_like(lab)
+    S_host = torch.empty((), dtype=torch.float64).pin_memory()
+
+    def e2e_step():
+        Xd.copy_(Xh, non_blocking=True)
+        ld.copy_(lh, non_blocking=True)
+        res = sil.silhouette(Xd, ld, K, status=status)
+        S_host.copy_(res.S, non_blocking=True)
+
+    e2e_step()
+    torch.cuda.synchronize()
+    te = timed(e2e_step, args.steps, stream)
+    te = max_over_ranks(te, world)
+    e2e = {"value": N * args.steps * world / te, "unit": "points/s",
+           "h2d_bytes_per_step": int(Xh.numel() * 4 + lh.numel() * 4), "d2h_bytes_per_step": 8}
+    del Xd, ld
+
+    variants = {}
+    if args.variants and rank == 0:
+        # same workload, cosine and BF16 storage
+        for name, fn in (("cosine_fp32", lambda: sil.silhouette(X, lab, K, "cosine", status=status)),):
+            fn()
+            s = timed(fn, args.steps, stream)
+            variants[name] = {"points_per_s": N * args.steps / s, "ms": s / args.steps * 1e3}
+        Xb = X.to(torch.bfloat16)
+        fn = lambda: sil.silhouette(Xb, lab, K, status=status)  # noqa: E731
+        rb = fn()
+        s = timed(fn, args.steps, stream)
+        variants["sqeuclidean_bf16"] = {"points_per_s": N * args.steps / s, "ms": s / args.steps * 1e3,
+                                        "S": float(rb.S.item()), "S_fp32": S_val,
+                                        "dS_vs_fp32": abs(float(rb.S.item()) - S_val)}
+        del Xb
+        torch.cuda.empty_cache()
+        variants.update(variant_lines(dev, args.steps, budget_s=120.0))
+
+    cpu = None
+    if rank == 0 and world >= 1 and not args.no_cpu_baseline and args.gpus == 1:
+        cpu = cpu_oracle_sample(X.cpu().numpy(), lab.cpu().numpy(), K)
+
+    if rank == 0:
+        launches_per_step = 9  # pass 1: rep_init, rep_find, shift_build, aggregate, publish;
+        #                        pass 2: fin_global, fin_clusters, score, reduce_S
+        line = {"metric": METRIC, "value": value, "unit": "points/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": t / args.steps * 1e3,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic",
+                "config": dict(WORKLOAD, parallelism="replicas" if world > 1 else "single",
+                               l2="inputs (2.6 GB) larger than L2 (129 MB); no flush"),
+                "S": S_val, "passes": pass_info, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+                "clocks": clocks, "gpu_launches": launches_per_step * args.steps,
+                "variants": variants}
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,173 @@
+/*
+ * sil.h -- C ABI of libsil, a GB300 (sm_103a) implementation of the
+ * linear-complexity Silhouette of Gaido, "Distributed Silhouette Algorithm:
+ * Evaluating Clustering on Big Data" (arXiv 2303.14102).
+ *
+ * The Silhouette of a clustering (Sec. II, Eq. 1-2): for every point i with
+ * label c, a_i is its mean distance to the other members of c, b_i the
+ * smallest mean distance to another non-empty cluster, s_i = (b_i - a_i) /
+ * max(a_i, b_i), and S = sum_i s_i / N.  The paper (Sec. III) removes the
+ * O(N^2) pairwise work: for the squared Euclidean distance (Eq. 4-11) and the
+ * cosine distance (Eq. 12-18) the mean distance from a point to a cluster is a
+ * closed form in per-cluster aggregates (count, sum of vectors, sum of
+ * squared norms -- or the sum of normalised vectors for cosine), which one
+ * pass over the data produces.  This library runs that as two GPU passes:
+ *
+ *   sil_aggregate       pass 1, a segmented per-cluster reduction (Eq. 6, 8, 16)
+ *   sil_score           pass 2, every point against all K aggregates
+ *                       (Eq. 11 / Eq. 18), own cluster over N_c - 1, b_i the
+ *                       minimum over the other clusters, s_i and the mean S
+ *   sil_score_backward  dS/dX with labels fixed (no counterpart in the paper)
+ *   sil_score_batched   S for many labelings of the same points
+ *
+ * Conventions shared by every entry point
+ *   - Every pointer named as "device" must be memory the current CUDA device
+ *     can read/write (cudaMalloc or torch CUDA tensors); "host" pointers are
+ *     ordinary process memory.  The caller owns every buffer.  The library
+ *     never allocates, never frees and never synchronises: each call only
+ *     enqueues kernels (and, where stated, cudaMemsetAsync) on `stream`, a
+ *     cudaStream_t passed as void* (NULL = the legacy default stream).
+ *   - X is row-major: row i starts at element i*ldx, ldx >= d.  dtype selects
+ *     float32, bfloat16 or FP8 E4M3 storage; FP8 takes a per-column positive
+ *     scale col_scale[d] (device, float32) and the value a kernel uses is
+ *     q * col_scale[l].  Computation is FP32 per point with FP64 aggregates
+ *     and an FP64 mean.
+ *   - labels are int32 dense ids in [0, k); ids with no point are allowed
+ *     and are not clusters.  A label outside [0, k) sets SIL_ELABEL in
+ *     *dev_status and the row is ignored.
+ *   - Return value: SIL_OK, or a host-side argument error (SIL_EINVAL,
+ *     SIL_EWORKSPACE, SIL_EUNSUPPORTED) / launch error (SIL_ECUDA) detected
+ *     before or while enqueueing; nothing is enqueued after an error.
+ *   - dev_status (device, one uint32, nullable) receives data-dependent
+ *     errors OR-ed in as bit flags (SIL_ELABEL, SIL_EDEGENERATE,
+ *     SIL_EZERONORM, SIL_ETIMEOUT).  The library never clears it.  When such
+ *     a flag is raised by a scoring call, S is written as NaN.  Kernels never
+ *     trap or assert.
+ *   - ws is a device workspace of at least sil_workspace_size(...) bytes,
+ *     256-byte aligned.  Its contents are scratch between calls.
+ */
+#ifndef SIL_H_
+#define SIL_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Distance measures of Sec. III-A (squared Euclidean, Eq. 4) and Sec. III-B
+ * (cosine distance 1 - cs, Eq. 12). */
+typedef enum { SIL_SQEUCLIDEAN = 0, SIL_COSINE = 1 } sil_distance_t;
+
+/* Storage type of X. */
+typedef enum { SIL_F32 = 0, SIL_BF16 = 1, SIL_FP8_E4M3 = 2 } sil_dtype_t;
+
+/* Return codes (single values) and device status flags (OR-ed bits). */
+typedef enum {
+  SIL_OK = 0,
+  SIL_EINVAL = 1,        /* bad argument (null pointer, size, ldx < d, ...) */
+  SIL_ELABEL = 2,        /* device flag: a label outside [0, k) */
+  SIL_EDEGENERATE = 4,   /* device flag: fewer than two non-empty clusters */
+  SIL_EZERONORM = 8,     /* device flag: cosine with an all-zero row */
+  SIL_ECUDA = 16,        /* a CUDA launch or memset failed */
+  SIL_ETIMEOUT = 32,     /* device flag: a bounded wait inside a kernel gave up */
+  SIL_EWORKSPACE = 64,   /* ws is NULL, misaligned or smaller than required */
+  SIL_EUNSUPPORTED = 128 /* valid arguments this build does not serve */
+} sil_status_t;
+
+/* Pass-2 implementation choice for sil_score. */
+typedef enum {
+  SIL_PATH_AUTO = 0,   /* library picks from (k, d, dtype) */
+  SIL_PATH_SIMT = 1,   /* FP32 FFMA with the centroids staged in shared memory */
+  SIL_PATH_TENSOR = 2  /* tcgen05 tensor-core GEMM with a fused epilogue */
+} sil_path_t;
+
+/* Flags of sil_aggregate. */
+#define SIL_AGG_ACCUMULATE 1u /* add into count/s1/s2 instead of overwriting */
+
+/* Bytes of workspace any call below needs for these sizes (batch = number of
+ * labelings for sil_score_batched, 1 otherwise; k = the largest k). */
+size_t sil_workspace_size(int64_t n, int32_t d, int32_t k, int32_t dtype, int32_t dist,
+                          int32_t batch);
+
+/* Bytes of the per-point record sil_score can save for the backward pass
+ * (a_i and b_i as float32, the b_i argmin cluster as int32: 12 bytes/point). */
+size_t sil_saved_size(int64_t n);
+
+/*
+ * Pass 1 (Sec. III-A Eq. 5-9 and its footnotes; Sec. III-B Eq. 15-16): the
+ * per-cluster aggregates in one pass over X.
+ *   count[k] (device int64)   N_k, the number of points with label k
+ *   s1[k*d + l] (device f64)  squared Euclidean: Y_{k,l} = sum of x_{il}
+ *                             (Eq. 8); cosine: Omega_{k,l} = sum of x_{il} /
+ *                             ||x_i|| (Eq. 16)
+ *   s2[k] (device f64)        squared Euclidean: Psi_k = sum of ||x_i||^2
+ *                             (Eq. 6); cosine: sum of ||x_i/||x_i|| ||^2
+ * These are exactly additive over any split of the rows, so aggregates of
+ * several calls on disjoint row ranges can be merged by adding them (the
+ * per-worker partial sums of the paper's distributed form); with
+ * SIL_AGG_ACCUMULATE the call adds into the outputs instead of overwriting
+ * them.  Inside a kernel, partial sums are formed in FP32 on values shifted
+ * by a per-cluster reference point and folded into FP64 once per block.
+ */
+int sil_aggregate(const void* X, int32_t dtype, int64_t n, int32_t d, int64_t ldx,
+                  const float* col_scale, const int32_t* labels, int32_t k, int32_t dist,
+                  int64_t* count, double* s1, double* s2, uint32_t flags, void* ws,
+                  size_t ws_bytes, uint32_t* dev_status, void* stream);
+
+/*
+ * Pass 2 (Sec. III-A Eq. 10-11, Sec. III-B Eq. 17-18, Sec. II Eq. 1-2): score
+ * every point from the aggregates of sil_aggregate over the SAME rows and
+ * labels.  For point i with label c:
+ *   a_i = mean distance to the other N_c - 1 members of c (0 if N_c = 1)
+ *   b_i = min over non-empty k != c of the mean distance to cluster k
+ *   s_i = (b_i - a_i) / max(a_i, b_i), 0 when N_c = 1 or max = 0
+ *   S   = sum_i s_i / n   (S_out: device, one double; NaN on a data error)
+ * s_out (device float[n], nullable) receives s_i.  saved (device,
+ * sil_saved_size(n) bytes, nullable) receives a_i, b_i and the argmin of b_i
+ * (lowest index on ties) for sil_score_backward.  N x K distances are never
+ * stored.  path selects the pass-2 kernel (SIL_PATH_AUTO recommended).
+ */
+int sil_score(const void* X, int32_t dtype, int64_t n, int32_t d, int64_t ldx,
+              const float* col_scale, const int32_t* labels, int32_t k, int32_t dist,
+              const int64_t* count, const double* s1, const double* s2, float* s_out,
+              double* S_out, void* saved, int32_t path, void* ws, size_t ws_bytes,
+              uint32_t* dev_status, void* stream);
+
+/*
+ * dS/dX with the labels fixed and b_i's argmin held at its value (the min
+ * and max of Eq. 1 taken as subgradients).  grad_S (device, one double,
+ * nullable = 1.0) scales the result, dX (device float32, row-major n x d,
+ * row stride lddx >= d) receives grad_S * dS/dX.  saved is the record of
+ * sil_score on the same inputs, or NULL to recompute it.  Cost: two passes
+ * over X plus the write of dX (the pass-2 scores again when saved is NULL).
+ */
+int sil_score_backward(const void* X, int32_t dtype, int64_t n, int32_t d, int64_t ldx,
+                       const float* col_scale, const int32_t* labels, int32_t k, int32_t dist,
+                       const int64_t* count, const double* s1, const double* s2,
+                       const void* saved, const double* grad_S, float* dX, int64_t lddx,
+                       void* ws, size_t ws_bytes, uint32_t* dev_status, void* stream);
+
+/*
+ * S for `batch` labelings of the same X.  labels is device int32 of
+ * batch x n (labeling b at labels + b*ldl), k_host (host int32[batch]) the
+ * number of label ids of each labeling, S_out (device double[batch]).
+ * Equivalent to sil_aggregate + sil_score per labeling.
+ */
+int sil_score_batched(const void* X, int32_t dtype, int64_t n, int32_t d, int64_t ldx,
+                      const float* col_scale, const int32_t* labels, int64_t ldl,
+                      const int32_t* k_host, int32_t batch, int32_t dist, double* S_out,
+                      void* ws, size_t ws_bytes, uint32_t* dev_status, void* stream);
+
+/* Human-readable name of a return code or of one status flag. */
+const char* sil_status_string(int32_t status);
+
+/* Library version, major*10000 + minor*100 + patch. */
+int32_t sil_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SIL_H_ */

@@ -1,0 +1,366 @@
+// The C ABI of libsil (declared in include/sil.h): argument validation,
+// workspace carving and the sequence of kernel launches of each entry point.
+// No allocation, no synchronisation: every call only enqueues work on the
+// caller's stream.
+#include <cmath>
+
+#include "sil_internal.cuh"
+
+namespace sil {
+
+WsLayout ws_layout(int64_t n, int32_t d, int32_t k, int32_t dtype, int32_t dist, int32_t batch) {
+  (void)dtype;
+  (void)dist;
+  const size_t dz = size_t(round_up(d, 4));
+  const size_t K = size_t(k), N = size_t(n);
+  WsLayout L{};
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    size_t at = o;
+    o += align256(bytes);
+    return at;
+  };
+  L.misc = take(64 * 4);
+  L.rep = take(K * 4);
+  L.rs = take(K * dz * 4);
+  L.g = take(dz * 8);
+  L.gf = take(dz * 4);
+  L.zf = take(K * dz * 4);
+  L.cl = take(K * 16);
+  L.invnorm = take(N * 4);
+  L.partials = take(size_t(kMaxPartials) * 8);
+  L.bw_w = take(2 * K * 8);
+  L.bw_p = take(2 * K * size_t(d) * 8);
+  L.bw_ab = take(2 * N * 4);
+  L.bw_f = take((K * dz + K) * 4);
+  L.saved = take(N * 12);
+  L.zbf = take(2 * size_t(round_up(k, 256)) * size_t(round_up(d, 64)) * 2 + size_t(round_up(k, 256)) * 16);
+  L.batch = take(K * (size_t(d) + 2) * 8);
+  L.total = o;
+  return L;
+}
+
+}  // namespace sil
+
+using namespace sil;
+
+namespace {
+
+template <typename T>
+T* at(void* ws, size_t off) {
+  return reinterpret_cast<T*>(static_cast<char*>(ws) + off);
+}
+
+int check_common(const void* X, int32_t dtype, int64_t n, int32_t d, int64_t ldx, const float* cs,
+                 const int32_t* labels, int32_t k, int32_t dist) {
+  if (n < 0 || d <= 0 || k <= 0 || ldx < d) return SIL_EINVAL;
+  if (dtype < SIL_F32 || dtype > SIL_FP8_E4M3) return SIL_EINVAL;
+  if (dist != SIL_SQEUCLIDEAN && dist != SIL_COSINE) return SIL_EINVAL;
+  if (n > 0 && (X == nullptr || labels == nullptr)) return SIL_EINVAL;
+  if (dtype == SIL_FP8_E4M3 && cs == nullptr) return SIL_EINVAL;
+  if (k > (1 << 22) || d > (1 << 16)) return SIL_EUNSUPPORTED;
+  if (n >= (int64_t(1) << 40)) return SIL_EUNSUPPORTED;
+  return SIL_OK;
+}
+
+int check_ws(void* ws, size_t ws_bytes, int64_t n, int32_t d, int32_t k, int32_t dtype, int32_t dist,
+             int32_t batch) {
+  if (ws == nullptr || (reinterpret_cast<uintptr_t>(ws) & 255u) != 0) return SIL_EWORKSPACE;
+  if (ws_bytes < ws_layout(n, d, k, dtype, dist, batch).total) return SIL_EWORKSPACE;
+  return SIL_OK;
+}
+
+inline int cu(cudaError_t e) { return e == cudaSuccess ? SIL_OK : SIL_ECUDA; }
+
+#define SIL_TRY(expr)              \
+  do {                             \
+    int rc_ = (expr);              \
+    if (rc_ != SIL_OK) return rc_; \
+  } while (0)
+
+// Pass 1 into (count, s1, s2), status into the workspace word.
+int run_aggregate(const void* X, int32_t dtype, int64_t n, int32_t d, int64_t ldx, const float* cs,
+                  const int32_t* labels, int32_t k, int32_t dist, int64_t* count, double* s1,
+                  double* s2, bool accumulate, void* ws, const WsLayout& L, cudaStream_t st) {
+  uint32_t* wst = at<uint32_t>(ws, L.misc);
+  if (!accumulate) {
+    SIL_TRY(cu(cudaMemsetAsync(count, 0, size_t(k) * 8, st)));
+    SIL_TRY(cu(cudaMemsetAsync(s1, 0, size_t(k) * size_t(d) * 8, st)));
+    SIL_TRY(cu(cudaMemsetAsync(s2, 0, size_t(k) * 8, st)));
+  }
+  if (n == 0) return SIL_OK;
+  float* rs = at<float>(ws, L.rs);
+  SIL_TRY(cu(launch_shift(X, dtype, n, d, ldx, cs, labels, k, dist, at<int32_t>(ws, L.rep), rs, st)));
+  const float* invnorm = nullptr;
+  if (dist == SIL_COSINE && agg_needs_invnorm(d, k, false)) {
+    SIL_TRY(cu(launch_invnorm(X, dtype, n, d, ldx, cs, at<float>(ws, L.invnorm), wst, st)));
+    invnorm = at<float>(ws, L.invnorm);
+  }
+  AggLaunch a{};
+  a.X = X;
+  a.dtype = dtype;
+  a.n = n;
+  a.d = d;
+  a.ldx = ldx;
+  a.cs = cs;
+  a.labels = labels;
+  a.k = k;
+  a.dist = dist;
+  a.rs = rs;
+  a.invnorm = invnorm;
+  a.count = reinterpret_cast<unsigned long long*>(count);
+  a.s1 = s1;
+  a.s2 = s2;
+  a.status = wst;
+  a.stream = st;
+  return cu(launch_aggregate(a));
+}
+
+int run_finalize(const int64_t* count, const double* s1, const double* s2, int32_t k, int32_t d,
+                 int32_t dist, void* ws, const WsLayout& L, cudaStream_t st) {
+  FinLaunch f{};
+  f.count = reinterpret_cast<const unsigned long long*>(count);
+  f.s1 = s1;
+  f.s2 = s2;
+  f.k = k;
+  f.d = d;
+  f.dist = dist;
+  f.g = at<double>(ws, L.g);
+  f.gf = at<float>(ws, L.gf);
+  f.zf = at<float>(ws, L.zf);
+  f.cl = at<float4>(ws, L.cl);
+  f.status = at<uint32_t>(ws, L.misc);
+  f.stream = st;
+  return cu(launch_finalize(f));
+}
+
+// Pass 2 over finalized constants; writes partial sums, returns their count.
+int run_score(const void* X, int32_t dtype, int64_t n, int32_t d, int64_t ldx, const float* cs,
+              const int32_t* labels, int32_t k, int32_t dist, float* s_out, float* sa, float* sb,
+              int32_t* skstar, int32_t path, void* ws, const WsLayout& L, cudaStream_t st,
+              int32_t* np) {
+  if (path == SIL_PATH_TENSOR) return SIL_EUNSUPPORTED;
+  ScoreLaunch s{};
+  s.X = X;
+  s.dtype = dtype;
+  s.n = n;
+  s.d = d;
+  s.ldx = ldx;
+  s.cs = cs;
+  s.labels = labels;
+  s.k = k;
+  s.dist = dist;
+  s.zf = at<float>(ws, L.zf);
+  s.cl = at<float4>(ws, L.cl);
+  s.gf = at<float>(ws, L.gf);
+  s.s_out = s_out;
+  s.sa = sa;
+  s.sb = sb;
+  s.skstar = skstar;
+  s.partials = at<double>(ws, L.partials);
+  s.n_partials = np;
+  s.status = at<uint32_t>(ws, L.misc);
+  s.stream = st;
+  return cu(launch_score_simt(s));
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t sil_workspace_size(int64_t n, int32_t d, int32_t k, int32_t dtype, int32_t dist,
+                          int32_t batch) {
+  if (n < 0 || d <= 0 || k <= 0) return 0;
+  return ws_layout(n, d, k, dtype, dist, batch < 1 ? 1 : batch).total;
+}
+
+size_t sil_saved_size(int64_t n) { return n < 0 ? 0 : size_t(n) * 12; }
+
+int sil_aggregate(const void* X, int32_t dtype, int64_t n, int32_t d, int64_t ldx,
+                  const float* col_scale, const int32_t* labels, int32_t k, int32_t dist,
+                  int64_t* count, double* s1, double* s2, uint32_t flags, void* ws,
+                  size_t ws_bytes, uint32_t* dev_status, void* stream) {
+  SIL_TRY(check_common(X, dtype, n, d, ldx, col_scale, labels, k, dist));
+  if (!count || !s1 || !s2) return SIL_EINVAL;
+  SIL_TRY(check_ws(ws, ws_bytes, n, d, k, dtype, dist, 1));
+  const WsLayout L = ws_layout(n, d, k, dtype, dist, 1);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  uint32_t* wst = at<uint32_t>(ws, L.misc);
+  SIL_TRY(cu(cudaMemsetAsync(wst, 0, 4, st)));
+  SIL_TRY(run_aggregate(X, dtype, n, d, ldx, col_scale, labels, k, dist, count, s1, s2,
+                        (flags & SIL_AGG_ACCUMULATE) != 0, ws, L, st));
+  return cu(launch_publish_status(wst, dev_status, st));
+}
+
+int sil_score(const void* X, int32_t dtype, int64_t n, int32_t d, int64_t ldx,
+              const float* col_scale, const int32_t* labels, int32_t k, int32_t dist,
+              const int64_t* count, const double* s1, const double* s2, float* s_out,
+              double* S_out, void* saved, int32_t path, void* ws, size_t ws_bytes,
+              uint32_t* dev_status, void* stream) {
+  SIL_TRY(check_common(X, dtype, n, d, ldx, col_scale, labels, k, dist));
+  if (!count || !s1 || !s2) return SIL_EINVAL;
+  if (path < SIL_PATH_AUTO || path > SIL_PATH_TENSOR) return SIL_EINVAL;
+  SIL_TRY(check_ws(ws, ws_bytes, n, d, k, dtype, dist, 1));
+  const WsLayout L = ws_layout(n, d, k, dtype, dist, 1);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  uint32_t* wst = at<uint32_t>(ws, L.misc);
+  SIL_TRY(cu(cudaMemsetAsync(wst, 0, 4, st)));
+  SIL_TRY(run_finalize(count, s1, s2, k, d, dist, ws, L, st));
+  float* sa = nullptr;
+  float* sb = nullptr;
+  int32_t* skstar = nullptr;
+  if (saved) {
+    sa = static_cast<float*>(saved);
+    sb = sa + n;
+    skstar = reinterpret_cast<int32_t*>(sb + n);
+  }
+  int32_t np = 0;
+  SIL_TRY(run_score(X, dtype, n, d, ldx, col_scale, labels, k, dist, s_out, sa, sb, skstar, path, ws,
+                    L, st, &np));
+  return cu(launch_reduce_S(at<double>(ws, L.partials), np, n, wst, dev_status, S_out, st));
+}
+
+int sil_score_backward(const void* X, int32_t dtype, int64_t n, int32_t d, int64_t ldx,
+                       const float* col_scale, const int32_t* labels, int32_t k, int32_t dist,
+                       const int64_t* count, const double* s1, const double* s2,
+                       const void* saved, const double* grad_S, float* dX, int64_t lddx,
+                       void* ws, size_t ws_bytes, uint32_t* dev_status, void* stream) {
+  SIL_TRY(check_common(X, dtype, n, d, ldx, col_scale, labels, k, dist));
+  if (!count || !s1 || !s2 || (n > 0 && !dX) || lddx < d) return SIL_EINVAL;
+  SIL_TRY(check_ws(ws, ws_bytes, n, d, k, dtype, dist, 1));
+  const WsLayout L = ws_layout(n, d, k, dtype, dist, 1);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  uint32_t* wst = at<uint32_t>(ws, L.misc);
+  SIL_TRY(cu(cudaMemsetAsync(wst, 0, 4, st)));
+  if (n == 0) return cu(launch_publish_status(wst, dev_status, st));
+  SIL_TRY(run_finalize(count, s1, s2, k, d, dist, ws, L, st));
+  float* rs = at<float>(ws, L.rs);
+  SIL_TRY(cu(launch_shift(X, dtype, n, d, ldx, col_scale, labels, k, dist, at<int32_t>(ws, L.rep), rs,
+                          st)));
+  const float* sa;
+  const float* sb;
+  const int32_t* skstar;
+  if (saved) {
+    sa = static_cast<const float*>(saved);
+  } else {
+    float* wsa = at<float>(ws, L.saved);
+    int32_t np = 0;
+    SIL_TRY(run_score(X, dtype, n, d, ldx, col_scale, labels, k, dist, nullptr, wsa, wsa + n,
+                      reinterpret_cast<int32_t*>(wsa + 2 * n), SIL_PATH_AUTO, ws, L, st, &np));
+    sa = wsa;
+  }
+  sb = sa + n;
+  skstar = reinterpret_cast<const int32_t*>(sb + n);
+
+  BackLaunch b{};
+  b.X = X;
+  b.dtype = dtype;
+  b.n = n;
+  b.d = d;
+  b.ldx = ldx;
+  b.cs = col_scale;
+  b.labels = labels;
+  b.k = k;
+  b.dist = dist;
+  b.zf = at<float>(ws, L.zf);
+  b.cl = at<float4>(ws, L.cl);
+  b.gf = at<float>(ws, L.gf);
+  b.rs = rs;
+  b.sa = sa;
+  b.sb = sb;
+  b.skstar = skstar;
+  b.grad_S = grad_S;
+  b.dX = dX;
+  b.lddx = lddx;
+  b.stream = st;
+  float* w1 = at<float>(ws, L.bw_ab);
+  float* w2 = w1 + n;
+  SIL_TRY(cu(launch_backward_weights(b, w1, w2)));
+
+  double* bw_w = at<double>(ws, L.bw_w);
+  double* bw_p = at<double>(ws, L.bw_p);
+  SIL_TRY(cu(cudaMemsetAsync(bw_w, 0, size_t(2) * k * 8, st)));
+  SIL_TRY(cu(cudaMemsetAsync(bw_p, 0, size_t(2) * k * size_t(d) * 8, st)));
+  const float* invnorm = nullptr;
+  if (dist == SIL_COSINE && agg_needs_invnorm(d, k, true)) {
+    SIL_TRY(cu(launch_invnorm(X, dtype, n, d, ldx, col_scale, at<float>(ws, L.invnorm), wst, st)));
+    invnorm = at<float>(ws, L.invnorm);
+  }
+  AggLaunch a{};
+  a.X = X;
+  a.dtype = dtype;
+  a.n = n;
+  a.d = d;
+  a.ldx = ldx;
+  a.cs = col_scale;
+  a.labels = labels;
+  a.labels2 = skstar;
+  a.w1 = w1;
+  a.w2 = w2;
+  a.k = k;
+  a.dist = dist;
+  a.rs = rs;
+  a.invnorm = invnorm;
+  a.s1 = bw_p;
+  a.wsum = bw_w;
+  a.status = wst;
+  a.stream = st;
+  SIL_TRY(cu(launch_aggregate(a)));
+  float* Wf = at<float>(ws, L.bw_f);
+  float* Cf = Wf + size_t(k) * size_t(round_up(d, 4));
+  SIL_TRY(cu(launch_backward_prep(bw_w, bw_p, k, d, Wf, Cf, st)));
+  SIL_TRY(cu(launch_backward_grad(b, Wf, Cf)));
+  return cu(launch_publish_status(wst, dev_status, st));
+}
+
+int sil_score_batched(const void* X, int32_t dtype, int64_t n, int32_t d, int64_t ldx,
+                      const float* col_scale, const int32_t* labels, int64_t ldl,
+                      const int32_t* k_host, int32_t batch, int32_t dist, double* S_out,
+                      void* ws, size_t ws_bytes, uint32_t* dev_status, void* stream) {
+  if (batch <= 0 || !k_host || !S_out || ldl < n) return SIL_EINVAL;
+  int32_t kmax = 0;
+  for (int32_t b = 0; b < batch; ++b) {
+    if (k_host[b] <= 0) return SIL_EINVAL;
+    kmax = k_host[b] > kmax ? k_host[b] : kmax;
+  }
+  SIL_TRY(check_common(X, dtype, n, d, ldx, col_scale, labels, kmax, dist));
+  SIL_TRY(check_ws(ws, ws_bytes, n, d, kmax, dtype, dist, batch));
+  const WsLayout L = ws_layout(n, d, kmax, dtype, dist, batch);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  uint32_t* wst = at<uint32_t>(ws, L.misc);
+  int64_t* count = at<int64_t>(ws, L.batch);
+  double* s1 = reinterpret_cast<double*>(count + kmax);
+  double* s2 = s1 + size_t(kmax) * d;
+  for (int32_t b = 0; b < batch; ++b) {
+    const int32_t kb = k_host[b];
+    const int32_t* lab = labels + b * ldl;
+    SIL_TRY(cu(cudaMemsetAsync(wst, 0, 4, st)));
+    SIL_TRY(run_aggregate(X, dtype, n, d, ldx, col_scale, lab, kb, dist, count, s1, s2, false, ws, L,
+                          st));
+    SIL_TRY(run_finalize(count, s1, s2, kb, d, dist, ws, L, st));
+    int32_t np = 0;
+    SIL_TRY(run_score(X, dtype, n, d, ldx, col_scale, lab, kb, dist, nullptr, nullptr, nullptr,
+                      nullptr, SIL_PATH_AUTO, ws, L, st, &np));
+    SIL_TRY(cu(launch_reduce_S(at<double>(ws, L.partials), np, n, wst, dev_status, S_out + b, st)));
+  }
+  return SIL_OK;
+}
+
+const char* sil_status_string(int32_t status) {
+  switch (status) {
+    case SIL_OK: return "SIL_OK";
+    case SIL_EINVAL: return "SIL_EINVAL: invalid argument";
+    case SIL_ELABEL: return "SIL_ELABEL: label outside [0, k)";
+    case SIL_EDEGENERATE: return "SIL_EDEGENERATE: fewer than two non-empty clusters";
+    case SIL_EZERONORM: return "SIL_EZERONORM: cosine distance of an all-zero row";
+    case SIL_ECUDA: return "SIL_ECUDA: CUDA launch or memset failed";
+    case SIL_ETIMEOUT: return "SIL_ETIMEOUT: a bounded device wait gave up";
+    case SIL_EWORKSPACE: return "SIL_EWORKSPACE: workspace missing, misaligned or too small";
+    case SIL_EUNSUPPORTED: return "SIL_EUNSUPPORTED: not served by this build";
+    default: return "unknown status";
+  }
+}
+
+int32_t sil_version(void) { return 100; }
+
+}  // extern "C"

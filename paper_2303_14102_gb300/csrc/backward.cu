@@ -1,0 +1,244 @@
+// Backward pass: dS/dX with the labels fixed and b_i's argmin k*_i held at
+// its value (the min of b_i and the max of Eq. 1 taken as subgradients).
+// The paper has no backward pass; the derivation (written out in the design
+// notes) gives, with
+//   alpha_i = (ds_i/da_i) / (n_c - 1),   beta_i = (ds_i/db_i) / n_{k*_i},
+//   A_k = sum_{c(i)=k} alpha_i,  P_k = sum_{c(i)=k} alpha_i v_i,
+//   B_k = sum_{k*_i=k} beta_i,   Q_k = sum_{k*_i=k} beta_i v_i,
+// (v = x for the squared Euclidean distance, v = x_hat for cosine):
+//   sq-Euclidean  dS/dx_m = (2/N)[alpha_m n_c (x_m - mu_c) + beta_m n_k* (x_m - mu_k*)
+//                                + A_c x_m - P_c + B_c x_m - Q_c]
+//   cosine        g = -(1/N)[alpha_m n_c mu_c + beta_m n_k* mu_k* + P_c + Q_c]
+//                 dS/dx_m = (g - x_hat (x_hat.g)) / ||x_m||
+// with c = c(m), k* = k*_m, mu the cluster means (of x_hat for cosine).
+// The four segmented sums come from ONE extra pass over X: the pass-1 kernel
+// in its weighted dual-entry form (each row adds alpha_i v_i to bucket c(i)
+// and beta_i v_i to bucket k + k*_i), again shifted by the per-cluster
+// reference points.  A second pass writes dX, one warp per row.
+#include "sil_internal.cuh"
+
+namespace sil {
+
+namespace {
+
+__device__ __forceinline__ void silhouette_partials(float a, float b, float* dsa, float* dsb) {
+  const float m = fmaxf(a, b);
+  if (!(m > 0.f)) {
+    *dsa = 0.f;
+    *dsb = 0.f;
+  } else if (a <= b) {
+    *dsa = -1.f / b;
+    *dsb = a / (b * b);
+  } else {
+    *dsa = -b / (a * a);
+    *dsb = 1.f / a;
+  }
+}
+
+// alpha and beta of one point from its saved (a, b, k*).
+__device__ __forceinline__ void point_weights(int64_t i, const int32_t* labels, int32_t k,
+                                              const float4* cl, const float* sa, const float* sb,
+                                              const int32_t* skstar, float* alpha, float* beta,
+                                              int* c_out, int* ks_out) {
+  const int c = labels[i];
+  const int ks = skstar[i];
+  *alpha = 0.f;
+  *beta = 0.f;
+  *c_out = c;
+  *ks_out = ks;
+  if (c < 0 || c >= k || ks < 0 || ks >= k) return;
+  const float nc = cl[c].w;
+  if (nc < 1.5f) return;
+  float dsa, dsb;
+  silhouette_partials(sa[i], sb[i], &dsa, &dsb);
+  *alpha = dsa / (nc - 1.f);
+  *beta = dsb / cl[ks].w;
+}
+
+__global__ void k_bw_weights(int64_t n, const int32_t* labels, int32_t k, const float4* cl,
+                             const float* sa, const float* sb, const int32_t* skstar, float* w1,
+                             float* w2) {
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+       i += int64_t(gridDim.x) * blockDim.x) {
+    float al, be;
+    int c, ks;
+    point_weights(i, labels, k, cl, sa, sb, skstar, &al, &be, &c, &ks);
+    w1[i] = al;
+    w2[i] = be;
+  }
+}
+
+// Per cluster: W_c = P'_c + Q'_c (float), C_c = A_c + B_c.
+__global__ void k_bw_prep(const double* bw_w, const double* bw_p, int32_t k, int32_t d, int32_t dz,
+                          float* Wf, float* Cf) {
+  const int c = blockIdx.x;
+  for (int l = threadIdx.x; l < dz; l += blockDim.x)
+    Wf[int64_t(c) * dz + l] =
+        l < d ? float(bw_p[int64_t(c) * d + l] + bw_p[int64_t(k + c) * d + l]) : 0.f;
+  if (threadIdx.x == 0) Cf[c] = float(bw_w[c] + bw_w[k + c]);
+}
+
+struct GradK {
+  const void* X;
+  int64_t n;
+  int32_t d;
+  int32_t dz;
+  int64_t ldx;
+  const float* cs;
+  const int32_t* labels;
+  int32_t k;
+  int32_t cosine;
+  int32_t vec;
+  const float4* cl;
+  const float* zf;
+  const float* gf;
+  const float* rs;
+  const float* Wf;
+  const float* Cf;
+  const float* sa;
+  const float* sb;
+  const int32_t* skstar;
+  const double* grad_S;
+  float* dX;
+  int64_t lddx;
+};
+
+// One warp per row of dX.
+template <int DT>
+__global__ void k_bw_grad(GradK a) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
+  const double gsd = a.grad_S ? *a.grad_S : 1.0;
+  const float inv_n = float(1.0 / double(a.n));
+  for (int64_t m = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; m < a.n; m += nw) {
+    float al, be;
+    int c, ks;
+    point_weights(m, a.labels, a.k, a.cl, a.sa, a.sb, a.skstar, &al, &be, &c, &ks);
+    float* out = a.dX + m * a.lddx;
+    if (c < 0 || c >= a.k) {
+      for (int l = lane; l < a.d; l += 32) out[l] = 0.f;
+      continue;
+    }
+    const bool has_k = ks >= 0 && ks < a.k;
+    const int kk = has_k ? ks : c;
+    const float nc = a.cl[c].w, nk = a.cl[kk].w;
+    const float Cc = a.Cf[c];
+    const float* zc = a.zf + int64_t(c) * a.dz;
+    const float* zk = a.zf + int64_t(kk) * a.dz;
+    const float* rc = a.rs + int64_t(c) * a.dz;
+    const float* Wc = a.Wf + int64_t(c) * a.dz;
+    if (!a.cosine) {
+      const float scale = float(gsd) * 2.f * inv_n;
+      for (int l0 = 4 * lane; l0 < a.dz; l0 += 128) {
+        const float4 x = load4<DT>(a.X, m, l0, a.d, a.ldx, a.cs, a.vec);
+        const float xv[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int l = l0 + j;
+          if (l >= a.d) break;
+          const float xc = xv[j] - a.gf[l];
+          float v = Cc * (xv[j] - rc[l]) - Wc[l];
+          v = fmaf(al * nc, xc - zc[l], v);
+          if (has_k) v = fmaf(be * nk, xc - zk[l], v);
+          out[l] = scale * v;
+        }
+      }
+    } else {
+      float ss = 0.f;
+      for (int l0 = 4 * lane; l0 < a.dz; l0 += 128) {
+        const float4 x = load4<DT>(a.X, m, l0, a.d, a.ldx, a.cs, a.vec);
+        ss += x.x * x.x + x.y * x.y + x.z * x.z + x.w * x.w;
+      }
+      for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+      const float inv = ss > 0.f ? rsqrtf(ss) : 0.f;
+      // g_l = -(1/N)[al nc muh_c + be nk muh_k + W_c + C_c rhat_c],  muh = mu' + g
+      float proj = 0.f;
+      for (int l0 = 4 * lane; l0 < a.dz; l0 += 128) {
+        const float4 x = load4<DT>(a.X, m, l0, a.d, a.ldx, a.cs, a.vec);
+        const float xv[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int l = l0 + j;
+          if (l >= a.d) break;
+          float g = fmaf(Cc, rc[l], Wc[l]);
+          g = fmaf(al * nc, zc[l] + a.gf[l], g);
+          if (has_k) g = fmaf(be * nk, zk[l] + a.gf[l], g);
+          proj = fmaf(xv[j] * inv, -g * inv_n, proj);
+        }
+      }
+      for (int o = 16; o > 0; o >>= 1) proj += __shfl_xor_sync(0xffffffffu, proj, o);
+      const float sc = float(gsd) * inv;
+      for (int l0 = 4 * lane; l0 < a.dz; l0 += 128) {
+        const float4 x = load4<DT>(a.X, m, l0, a.d, a.ldx, a.cs, a.vec);
+        const float xv[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int l = l0 + j;
+          if (l >= a.d) break;
+          float g = fmaf(Cc, rc[l], Wc[l]);
+          g = fmaf(al * nc, zc[l] + a.gf[l], g);
+          if (has_k) g = fmaf(be * nk, zk[l] + a.gf[l], g);
+          g = -g * inv_n;
+          out[l] = sc * (g - xv[j] * inv * proj);
+        }
+      }
+    }
+  }
+}
+
+bool vec_ok_b(const void* X, int32_t dtype, int64_t ldx) {
+  const int esz = dtype == SIL_F32 ? 4 : dtype == SIL_BF16 ? 2 : 1;
+  return (reinterpret_cast<uintptr_t>(X) % (4 * esz) == 0) && (ldx % 4 == 0);
+}
+
+}  // namespace
+
+cudaError_t launch_backward_weights(const BackLaunch& b, float* w1, float* w2) {
+  if (b.n == 0) return cudaSuccess;
+  const unsigned grid = unsigned(std::min<int64_t>(cdiv(b.n, 256), int64_t(kNumSMs) * 8));
+  k_bw_weights<<<grid, 256, 0, b.stream>>>(b.n, b.labels, b.k, b.cl, b.sa, b.sb, b.skstar, w1, w2);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_backward_prep(const double* bw_w, const double* bw_p, int32_t k, int32_t d,
+                                 float* Wf, float* Cf, cudaStream_t stream) {
+  const int dz = int(round_up(d, 4));
+  k_bw_prep<<<k, 128, 0, stream>>>(bw_w, bw_p, k, d, dz, Wf, Cf);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_backward_grad(const BackLaunch& b, const float* Wf, const float* Cf) {
+  if (b.n == 0) return cudaSuccess;
+  GradK g{};
+  g.X = b.X;
+  g.n = b.n;
+  g.d = b.d;
+  g.dz = int(round_up(b.d, 4));
+  g.ldx = b.ldx;
+  g.cs = b.cs;
+  g.labels = b.labels;
+  g.k = b.k;
+  g.cosine = b.dist == SIL_COSINE;
+  g.vec = vec_ok_b(b.X, b.dtype, b.ldx);
+  g.cl = b.cl;
+  g.zf = b.zf;
+  g.gf = b.gf;
+  g.rs = b.rs;
+  g.Wf = Wf;
+  g.Cf = Cf;
+  g.sa = b.sa;
+  g.sb = b.sb;
+  g.skstar = b.skstar;
+  g.grad_S = b.grad_S;
+  g.dX = b.dX;
+  g.lddx = b.lddx;
+  const unsigned grid = unsigned(std::min<int64_t>(cdiv(b.n, 8), int64_t(kNumSMs) * 16));
+  switch (b.dtype) {
+    case SIL_F32: k_bw_grad<SIL_F32><<<grid, 256, 0, b.stream>>>(g); break;
+    case SIL_BF16: k_bw_grad<SIL_BF16><<<grid, 256, 0, b.stream>>>(g); break;
+    default: k_bw_grad<SIL_FP8_E4M3><<<grid, 256, 0, b.stream>>>(g); break;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace sil

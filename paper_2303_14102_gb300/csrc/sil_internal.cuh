@@ -1,0 +1,237 @@
+// Internal declarations shared by the translation units of libsil.
+//
+// Layout conventions (device memory):
+//   X        row-major n x d in its storage type, row stride ldx elements
+//   labels   int32[n]
+//   count    int64[k], s1 f64[k*d], s2 f64[k]   (the pass-1 aggregates)
+//   ws       caller workspace carved by ws_layout() below
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp8.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+
+#include "sil.h"
+
+namespace sil {
+
+constexpr int kAggRows = 128;        // rows per pass-1 tile
+constexpr int kAggThreads = 256;     // threads per pass-1 CTA
+constexpr int kScoreThreads = 256;   // threads per SIMT pass-2 CTA
+constexpr int kMaxPartials = 8192;   // per-CTA partial sums of s_i
+constexpr int kRepRows = 65536;      // rows searched for per-cluster reference points
+constexpr int kNumSMs = 152;         // GB300
+constexpr int kSmemBudget = 100 * 1024;  // dynamic shared memory per CTA we aim for
+
+__host__ __device__ inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+__host__ __device__ inline int64_t round_up(int64_t a, int64_t b) { return cdiv(a, b) * b; }
+inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// Per-cluster constants for pass 2, one float4 per cluster:
+//   x = bias  = ||mu'_k||^2 + W_k/n_k   (+inf when n_k = 0)
+//   y = an    = n_k / (n_k - 1)          (0 when n_k < 2)
+//   z = aw    = W_k / (n_k - 1)          (0 when n_k < 2)
+//   w = n_k as float
+// mu'_k = mu_k - g is the centroid in coordinates centred on the global mean
+// g, W_k = sum ||x - mu_k||^2 is the within-cluster scatter.
+
+struct WsLayout {
+  size_t misc;      // uint32 flags[64]
+  size_t rep;       // int32[k]          first row of each cluster among the first kRepRows
+  size_t rs;        // float[k*dz]       per-cluster shift (reference point)
+  size_t g;         // double[dz]        global centre
+  size_t gf;        // float[dz]
+  size_t zf;        // float[k*dz]       centred centroids mu'
+  size_t cl;        // float4[k]         per-cluster constants
+  size_t invnorm;   // float[n]          1/||x_i|| (cosine, when pass 1 is column-sliced)
+  size_t partials;  // double[kMaxPartials]
+  size_t bw_w;      // double[2k]        backward: A_k then B_k
+  size_t bw_p;      // double[2k*d]      backward: P'_k then Q'_k
+  size_t bw_ab;     // float[2n]         backward: alpha_i then beta_i
+  size_t bw_f;      // float[k*dz + k]   backward: W_c rows then C_c
+  size_t saved;     // 12 bytes * n      recomputed forward record
+  size_t zbf;       // bf16 centroid tiles for the tensor path
+  size_t batch;     // batched aggregates
+  size_t total;
+};
+
+WsLayout ws_layout(int64_t n, int32_t d, int32_t k, int32_t dtype, int32_t dist, int32_t batch);
+
+// ---------------------------------------------------------------- loaders
+template <int DT>
+struct Elem;
+template <>
+struct Elem<SIL_F32> {
+  using T = float;
+  static __device__ __forceinline__ float get(const T* p, int64_t i) { return p[i]; }
+};
+template <>
+struct Elem<SIL_BF16> {
+  using T = __nv_bfloat16;
+  static __device__ __forceinline__ float get(const T* p, int64_t i) { return __bfloat162float(p[i]); }
+};
+template <>
+struct Elem<SIL_FP8_E4M3> {
+  using T = __nv_fp8_e4m3;
+  static __device__ __forceinline__ float get(const T* p, int64_t i) { return float(p[i]); }
+};
+
+// Four consecutive elements of row `row` starting at column `col` (col % 4 == 0),
+// columns >= d read as 0.  `vec` promises that X, ldx are aligned for one
+// vector load of four elements.
+template <int DT>
+__device__ __forceinline__ float4 load4(const void* Xv, int64_t row, int col, int d, int64_t ldx,
+                                        const float* cs, bool vec) {
+  using T = typename Elem<DT>::T;
+  const T* X = static_cast<const T*>(Xv);
+  const int64_t base = row * ldx + col;
+  float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (vec && col + 3 < d) {
+    if constexpr (DT == SIL_F32) {
+      r = __ldg(reinterpret_cast<const float4*>(X + base));
+    } else if constexpr (DT == SIL_BF16) {
+      uint2 u = __ldg(reinterpret_cast<const uint2*>(X + base));
+      __nv_bfloat162 lo = *reinterpret_cast<__nv_bfloat162*>(&u.x);
+      __nv_bfloat162 hi = *reinterpret_cast<__nv_bfloat162*>(&u.y);
+      float2 a = __bfloat1622float2(lo), b = __bfloat1622float2(hi);
+      r = make_float4(a.x, a.y, b.x, b.y);
+    } else {
+      uint32_t u = __ldg(reinterpret_cast<const unsigned int*>(X + base));
+      const __nv_fp8_e4m3* q = reinterpret_cast<const __nv_fp8_e4m3*>(&u);
+      r = make_float4(float(q[0]), float(q[1]), float(q[2]), float(q[3]));
+    }
+  } else {
+    float v[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      if (col + j < d) v[j] = Elem<DT>::get(X, base + j);
+    r = make_float4(v[0], v[1], v[2], v[3]);
+  }
+  if constexpr (DT == SIL_FP8_E4M3) {
+    if (col + 0 < d) r.x *= __ldg(cs + col + 0);
+    if (col + 1 < d) r.y *= __ldg(cs + col + 1);
+    if (col + 2 < d) r.z *= __ldg(cs + col + 2);
+    if (col + 3 < d) r.w *= __ldg(cs + col + 3);
+  }
+  return r;
+}
+
+__device__ __forceinline__ void set_status(uint32_t* st, uint32_t bit) {
+  if (st) atomicOr(st, bit);
+}
+
+// ------------------------------------------------------------ host launchers
+struct AggLaunch {
+  const void* X;
+  int32_t dtype;
+  int64_t n;
+  int32_t d;
+  int64_t ldx;
+  const float* cs;
+  const int32_t* labels;   // bucket id of entry 0 of each row
+  const int32_t* labels2;  // dual mode: bucket id (minus k) of entry 1, nullable
+  const float* w1;         // weights of entry 0 (nullable: unweighted)
+  const float* w2;         // weights of entry 1 (dual)
+  int32_t k;
+  int32_t dist;
+  const float* rs;         // shift [k][dz]
+  const float* invnorm;    // nullable
+  unsigned long long* count;
+  double* s1;
+  double* s2;
+  double* wsum;
+  uint32_t* status;
+  cudaStream_t stream;
+};
+
+// Enqueue the reference-point search and shift table (ws.rep, ws.rs).
+cudaError_t launch_shift(const void* X, int32_t dtype, int64_t n, int32_t d, int64_t ldx,
+                         const float* cs, const int32_t* labels, int32_t k, int32_t dist,
+                         int32_t* rep, float* rs, cudaStream_t stream);
+// Enqueue 1/||x_i|| for every row (cosine, column-sliced pass 1).
+cudaError_t launch_invnorm(const void* X, int32_t dtype, int64_t n, int32_t d, int64_t ldx,
+                           const float* cs, float* invnorm, uint32_t* status, cudaStream_t stream);
+// Whether pass 1 for these sizes needs full rows per CTA for the cosine norm.
+bool agg_needs_invnorm(int32_t d, int32_t k, bool dual);
+// Enqueue pass 1 (outputs must be zeroed or hold sums to add to).
+cudaError_t launch_aggregate(const AggLaunch& a);
+
+struct FinLaunch {
+  const unsigned long long* count;
+  const double* s1;
+  const double* s2;
+  int32_t k;
+  int32_t d;
+  int32_t dist;
+  double* g;
+  float* gf;
+  float* zf;
+  float4* cl;
+  uint32_t* status;  // workspace status word
+  cudaStream_t stream;
+};
+cudaError_t launch_finalize(const FinLaunch& f);
+
+struct ScoreLaunch {
+  const void* X;
+  int32_t dtype;
+  int64_t n;
+  int32_t d;
+  int64_t ldx;
+  const float* cs;
+  const int32_t* labels;
+  int32_t k;
+  int32_t dist;
+  const float* zf;
+  const float4* cl;
+  const float* gf;
+  float* s_out;
+  float* sa;
+  float* sb;
+  int32_t* skstar;
+  double* partials;
+  int32_t* n_partials;  // host out: number of partials written
+  uint32_t* status;     // workspace status word
+  cudaStream_t stream;
+};
+cudaError_t launch_score_simt(ScoreLaunch& s);
+// S = sum(partials)/n, NaN when the workspace status word is non-zero; the
+// word is OR-ed into user_status.
+cudaError_t launch_reduce_S(const double* partials, int32_t np, int64_t n, const uint32_t* ws_status,
+                            uint32_t* user_status, double* S_out, cudaStream_t stream);
+cudaError_t launch_publish_status(const uint32_t* ws_status, uint32_t* user_status,
+                                  cudaStream_t stream);
+
+struct BackLaunch {
+  const void* X;
+  int32_t dtype;
+  int64_t n;
+  int32_t d;
+  int64_t ldx;
+  const float* cs;
+  const int32_t* labels;
+  int32_t k;
+  int32_t dist;
+  const float* zf;
+  const float4* cl;
+  const float* gf;
+  const float* rs;
+  const float* sa;
+  const float* sb;
+  const int32_t* skstar;
+  const double* grad_S;
+  float* dX;
+  int64_t lddx;
+  cudaStream_t stream;
+};
+// alpha_i / beta_i per point written into w1/w2 (float[n] each).
+cudaError_t launch_backward_weights(const BackLaunch& b, float* w1, float* w2);
+// Wf[c] = P'_c + Q'_c, Cf[c] = A_c + B_c from the dual weighted aggregates.
+cudaError_t launch_backward_prep(const double* bw_w, const double* bw_p, int32_t k, int32_t d,
+                                 float* Wf, float* Cf, cudaStream_t stream);
+cudaError_t launch_backward_grad(const BackLaunch& b, const float* Wf, const float* Cf);
+
+}  // namespace sil

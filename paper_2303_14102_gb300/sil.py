@@ -1,0 +1,267 @@
+"""Thin ctypes binding of libsil (C ABI in include/sil.h).
+
+Argument marshalling only: every step of the Silhouette runs in the CUDA
+kernels of libsil.so.  PyTorch supplies device memory and the current
+stream.  There is no CPU fallback: without the compiled library or a CUDA
+device every call raises.
+
+Entry points mirror the C names:
+  aggregate(X, labels, K, ...)          -> (count, s1, s2)     sil_aggregate
+  score(X, labels, K, agg, ...)         -> Score(S, s, saved)  sil_score
+  score_backward(X, labels, K, agg, ...)-> dX                  sil_score_backward
+  score_batched(X, labels, ks, ...)     -> S[B]                sil_score_batched
+  silhouette(X, labels, K, ...)         -> S (aggregate + score)
+Results stay on the device and nothing synchronises; ``check_status`` reads
+the device status word (one sync) and raises on a data error.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import os
+import threading
+
+import torch
+
+from . import _build
+
+SIL_OK, SIL_EINVAL, SIL_ELABEL, SIL_EDEGENERATE, SIL_EZERONORM = 0, 1, 2, 4, 8
+SIL_ECUDA, SIL_ETIMEOUT, SIL_EWORKSPACE, SIL_EUNSUPPORTED = 16, 32, 64, 128
+SIL_AGG_ACCUMULATE = 1
+METRICS = {"sqeuclidean": 0, "cosine": 1}
+PATHS = {"auto": 0, "simt": 1, "tensor": 2}
+EXPORTED = ("sil_workspace_size", "sil_saved_size", "sil_aggregate", "sil_score",
+            "sil_score_backward", "sil_score_batched", "sil_status_string", "sil_version")
+
+_lock = threading.Lock()
+_lib = None
+
+
+class SilError(RuntimeError):
+    """A non-zero return code or device status flag of libsil."""
+
+    def __init__(self, code: int, what: str):
+        self.code = code
+        super().__init__(f"{what}: {status_string(code)} ({code})")
+
+
+def load(build_if_stale: bool = True) -> ctypes.CDLL:
+    """Load libsil.so (compiling it first when missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if build_if_stale:
+                _build.build()
+            if not os.path.exists(_build.LIB):
+                raise RuntimeError(f"libsil.so not found at {_build.LIB}; run __graft_entry__.build()")
+            lib = ctypes.CDLL(_build.LIB)
+            vp, i32, i64, sz, u32 = (ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t,
+                                     ctypes.c_uint32)
+            lib.sil_workspace_size.argtypes = [i64, i32, i32, i32, i32, i32]
+            lib.sil_workspace_size.restype = sz
+            lib.sil_saved_size.argtypes = [i64]
+            lib.sil_saved_size.restype = sz
+            lib.sil_aggregate.argtypes = [vp, i32, i64, i32, i64, vp, vp, i32, i32, vp, vp, vp, u32,
+                                          vp, sz, vp, vp]
+            lib.sil_aggregate.restype = ctypes.c_int
+            lib.sil_score.argtypes = [vp, i32, i64, i32, i64, vp, vp, i32, i32, vp, vp, vp, vp, vp,
+                                      vp, i32, vp, sz, vp, vp]
+            lib.sil_score.restype = ctypes.c_int
+            lib.sil_score_backward.argtypes = [vp, i32, i64, i32, i64, vp, vp, i32, i32, vp, vp, vp,
+                                               vp, vp, vp, i64, vp, sz, vp, vp]
+            lib.sil_score_backward.restype = ctypes.c_int
+            lib.sil_score_batched.argtypes = [vp, i32, i64, i32, i64, vp, vp, i64, vp, i32, i32, vp,
+                                              vp, sz, vp, vp]
+            lib.sil_score_batched.restype = ctypes.c_int
+            lib.sil_status_string.argtypes = [i32]
+            lib.sil_status_string.restype = ctypes.c_char_p
+            lib.sil_version.restype = i32
+            _lib = lib
+    return _lib
+
+
+def status_string(code: int) -> str:
+    try:
+        return load(build_if_stale=False).sil_status_string(int(code)).decode()
+    except Exception:  # pragma: no cover - library not loadable
+        return "unknown"
+
+
+def _dtype_code(t: torch.Tensor) -> int:
+    if t.dtype == torch.float32:
+        return 0
+    if t.dtype == torch.bfloat16:
+        return 1
+    if t.dtype == torch.float8_e4m3fn:
+        return 2
+    raise TypeError(f"unsupported storage dtype {t.dtype}")
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream_handle(device) -> ctypes.c_void_p:
+    return ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+
+
+def _check_X(X: torch.Tensor, labels: torch.Tensor):
+    if not X.is_cuda:
+        raise RuntimeError("libsil runs on CUDA tensors only (no CPU path)")
+    if X.dim() != 2 or X.stride(1) != 1:
+        raise ValueError("X must be a 2-D tensor with unit column stride")
+    if labels.dtype != torch.int32 or not labels.is_cuda or labels.stride(-1) != 1:
+        raise ValueError("labels must be a contiguous CUDA int32 tensor")
+
+
+def _rc(rc: int, what: str):
+    if rc != SIL_OK:
+        raise SilError(rc, what)
+
+
+class _Workspace:
+    """Grow-only device workspace per device (one per process)."""
+
+    def __init__(self):
+        self._buf = {}
+
+    def get(self, device, nbytes: int) -> torch.Tensor:
+        key = torch.device(device).index
+        buf = self._buf.get(key)
+        if buf is None or buf.numel() < nbytes:
+            buf = torch.empty(max(nbytes, 1 << 20), dtype=torch.uint8, device=device)
+            self._buf[key] = buf
+        return buf
+
+
+_WS = _Workspace()
+
+
+def workspace_size(N: int, D: int, K: int, dtype=torch.float32, metric="sqeuclidean",
+                   batch: int = 1) -> int:
+    code = {torch.float32: 0, torch.bfloat16: 1, torch.float8_e4m3fn: 2}[dtype]
+    return int(load().sil_workspace_size(N, D, K, code, METRICS[metric], batch))
+
+
+def new_status(device) -> torch.Tensor:
+    """A zeroed device status word (int32 storage of the uint32 flags)."""
+    return torch.zeros(1, dtype=torch.int32, device=device)
+
+
+def check_status(status: torch.Tensor, what: str = "libsil"):
+    """Synchronise on the status word and raise SilError if a flag is set."""
+    v = int(status.item()) & 0xFFFFFFFF
+    if v:
+        raise SilError(v, what)
+
+
+def _ws_for(X, K, metric, batch=1):
+    N, D = X.shape
+    need = int(load().sil_workspace_size(N, D, K, _dtype_code(X), METRICS[metric], batch))
+    return _WS.get(X.device, need), need
+
+
+def aggregate(X: torch.Tensor, labels: torch.Tensor, K: int, metric: str = "sqeuclidean",
+              col_scale: torch.Tensor | None = None, out=None, accumulate: bool = False,
+              status: torch.Tensor | None = None):
+    """Pass 1: (count int64[K], s1 f64[K, D], s2 f64[K]) on the device."""
+    _check_X(X, labels)
+    lib = load()
+    N, D = X.shape
+    if out is None:
+        count = torch.zeros(K, dtype=torch.int64, device=X.device)
+        s1 = torch.zeros(K, D, dtype=torch.float64, device=X.device)
+        s2 = torch.zeros(K, dtype=torch.float64, device=X.device)
+    else:
+        count, s1, s2 = out
+    ws, need = _ws_for(X, K, metric)
+    rc = lib.sil_aggregate(_ptr(X), _dtype_code(X), N, D, X.stride(0), _ptr(col_scale), _ptr(labels),
+                           K, METRICS[metric], _ptr(count), _ptr(s1), _ptr(s2),
+                           SIL_AGG_ACCUMULATE if accumulate else 0, _ptr(ws), need, _ptr(status),
+                           _stream_handle(X.device))
+    _rc(rc, "sil_aggregate")
+    return count, s1, s2
+
+
+@dataclasses.dataclass
+class Score:
+    S: torch.Tensor                  # 0-d float64 on the device
+    s: torch.Tensor | None           # float32[N] or None
+    saved: torch.Tensor | None       # uint8[12 N] record for the backward pass
+
+
+def score(X: torch.Tensor, labels: torch.Tensor, K: int, agg, metric: str = "sqeuclidean",
+          col_scale: torch.Tensor | None = None, want_s: bool = False, save: bool = False,
+          path: str = "auto", status: torch.Tensor | None = None) -> Score:
+    """Pass 2 from the aggregates of :func:`aggregate` over the same rows."""
+    _check_X(X, labels)
+    lib = load()
+    N, D = X.shape
+    count, s1, s2 = agg
+    S = torch.empty((), dtype=torch.float64, device=X.device)
+    s = torch.empty(N, dtype=torch.float32, device=X.device) if want_s else None
+    saved = torch.empty(int(lib.sil_saved_size(N)), dtype=torch.uint8, device=X.device) if save else None
+    ws, need = _ws_for(X, K, metric)
+    rc = lib.sil_score(_ptr(X), _dtype_code(X), N, D, X.stride(0), _ptr(col_scale), _ptr(labels), K,
+                       METRICS[metric], _ptr(count), _ptr(s1), _ptr(s2), _ptr(s), _ptr(S),
+                       _ptr(saved), PATHS[path], _ptr(ws), need, _ptr(status),
+                       _stream_handle(X.device))
+    _rc(rc, "sil_score")
+    return Score(S=S, s=s, saved=saved)
+
+
+def unpack_saved(saved: torch.Tensor, N: int):
+    """(a float32[N], b float32[N], kstar int32[N]) views of a saved record."""
+    f = saved.view(torch.float32)
+    return f[:N], f[N:2 * N], saved.view(torch.int32)[2 * N:3 * N]
+
+
+def score_backward(X: torch.Tensor, labels: torch.Tensor, K: int, agg, metric: str = "sqeuclidean",
+                   saved: torch.Tensor | None = None, grad_S: torch.Tensor | None = None,
+                   col_scale: torch.Tensor | None = None, out: torch.Tensor | None = None,
+                   status: torch.Tensor | None = None) -> torch.Tensor:
+    """grad_S * dS/dX (float32 N x D) with labels fixed."""
+    _check_X(X, labels)
+    lib = load()
+    N, D = X.shape
+    count, s1, s2 = agg
+    dX = out if out is not None else torch.empty(N, D, dtype=torch.float32, device=X.device)
+    if grad_S is not None:
+        grad_S = grad_S.to(device=X.device, dtype=torch.float64).reshape(())
+    ws, need = _ws_for(X, K, metric)
+    rc = lib.sil_score_backward(_ptr(X), _dtype_code(X), N, D, X.stride(0), _ptr(col_scale),
+                                _ptr(labels), K, METRICS[metric], _ptr(count), _ptr(s1), _ptr(s2),
+                                _ptr(saved), _ptr(grad_S), _ptr(dX), dX.stride(0), _ptr(ws), need,
+                                _ptr(status), _stream_handle(X.device))
+    _rc(rc, "sil_score_backward")
+    return dX
+
+
+def score_batched(X: torch.Tensor, labels: torch.Tensor, ks, metric: str = "sqeuclidean",
+                  col_scale: torch.Tensor | None = None,
+                  status: torch.Tensor | None = None) -> torch.Tensor:
+    """S (float64[B]) of the B labelings in the rows of ``labels`` (B x N int32)."""
+    if labels.dim() != 2:
+        raise ValueError("labels must be B x N")
+    _check_X(X, labels[0])
+    lib = load()
+    N, D = X.shape
+    B = labels.shape[0]
+    k_host = (ctypes.c_int32 * B)(*[int(k) for k in ks])
+    S = torch.empty(B, dtype=torch.float64, device=X.device)
+    kmax = max(int(k) for k in ks)
+    ws, need = _ws_for(X, kmax, metric, batch=B)
+    rc = lib.sil_score_batched(_ptr(X), _dtype_code(X), N, D, X.stride(0), _ptr(col_scale),
+                               _ptr(labels), labels.stride(0), k_host, B, METRICS[metric], _ptr(S),
+                               _ptr(ws), need, _ptr(status), _stream_handle(X.device))
+    _rc(rc, "sil_score_batched")
+    return S
+
+
+def silhouette(X: torch.Tensor, labels: torch.Tensor, K: int, metric: str = "sqeuclidean",
+               col_scale: torch.Tensor | None = None, want_s: bool = False,
+               path: str = "auto", status: torch.Tensor | None = None) -> Score:
+    """Both passes: the Silhouette S (and optionally every s_i) of one labeling."""
+    agg = aggregate(X, labels, K, metric, col_scale=col_scale, status=status)
+    return score(X, labels, K, agg, metric, col_scale=col_scale, want_s=want_s, path=path,
+                 status=status)

@@ -125,15 +125,16 @@ def workload_batched(device: str = "cpu", N: int = 2_000_000, D: int = 32, B: in
     g.manual_seed(SEED_BASE + 3)
     ks = torch.randint(k_low, k_high + 1, (B,), generator=g).tolist()
     labels = torch.empty(B, N, dtype=torch.int32, device=device)
-    xx = (X.double() ** 2).sum(1, keepdim=True)
     for b, k in enumerate(ks):
         gb = torch.Generator(device="cpu")
         gb.manual_seed(SEED_BASE + 1000 + b)
         idx = torch.randperm(N, generator=gb)[:k].to(device)
-        C = X[idx].double()
+        C = X[idx]
+        cc = (C * C).sum(1)[None, :]
         for lo in range(0, N, 1 << 18):
             hi = min(N, lo + (1 << 18))
-            d = xx[lo:hi] + (C ** 2).sum(1)[None, :] - 2.0 * X[lo:hi].double() @ C.T
+            # ||x||^2 is common to every centre of a row, so it does not change the argmin
+            d = cc - 2.0 * (X[lo:hi] @ C.T)
             labels[b, lo:hi] = d.argmin(dim=1).to(torch.int32)
     return X, labels, ks
 

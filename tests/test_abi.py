@@ -1,0 +1,105 @@
+"""The C-ABI library builds, loads and exports what include/sil.h declares;
+host-side argument checks answer without touching a GPU (CPU only)."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+from paper_2303_14102_gb300 import _build, sil
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(__file__)), "include", "sil.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(sil_[a-z_]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    return sil.load()
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("sil_aggregate", "sil_score", "sil_score_backward", "sil_workspace_size"):
+        assert required in names
+    assert set(names) >= set(sil.EXPORTED)
+
+
+def test_every_declared_symbol_is_exported(lib):
+    out = subprocess.run(["nm", "-D", "--defined-only", _build.LIB], capture_output=True, text=True,
+                         check=True).stdout
+    exported = set(re.findall(r"\bT (sil_[a-z_]+)\b", out))
+    missing = [f for f in declared_functions() if f not in exported]
+    assert not missing, missing
+    for f in declared_functions():
+        assert hasattr(lib, f)
+
+
+def test_no_torch_or_cxx_types_in_the_abi():
+    code = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    assert "torch" not in code.lower() and "at::" not in code
+    assert "std::" not in code and "class " not in code and "template" not in code
+
+
+def test_version_and_strings(lib):
+    assert lib.sil_version() >= 100
+    assert b"SIL_ELABEL" in lib.sil_status_string(sil.SIL_ELABEL)
+    assert b"unknown" in lib.sil_status_string(12345)
+
+
+def test_workspace_and_saved_sizes(lib):
+    a = lib.sil_workspace_size(1000, 8, 5, 0, 0, 1)
+    b = lib.sil_workspace_size(100000, 8, 5, 0, 0, 1)
+    assert 0 < a < b and a % 256 == 0
+    assert lib.sil_workspace_size(10, 0, 5, 0, 0, 1) == 0
+    assert lib.sil_saved_size(1000) == 12000
+
+
+def _agg(lib, **kw):
+    args = dict(X=ctypes.c_void_p(16), dtype=0, n=10, d=4, ldx=4, cs=None, labels=ctypes.c_void_p(16),
+                k=3, dist=0, count=ctypes.c_void_p(16), s1=ctypes.c_void_p(16), s2=ctypes.c_void_p(16),
+                flags=0, ws=ctypes.c_void_p(256), ws_bytes=1 << 30, status=None, stream=None)
+    args.update(kw)
+    return lib.sil_aggregate(*args.values())
+
+
+def test_argument_errors_are_reported_before_any_launch(lib):
+    # every case below fails validation, so no CUDA call is made (no GPU here)
+    assert _agg(lib, d=0) == sil.SIL_EINVAL
+    assert _agg(lib, k=0) == sil.SIL_EINVAL
+    assert _agg(lib, ldx=3) == sil.SIL_EINVAL
+    assert _agg(lib, dtype=7) == sil.SIL_EINVAL
+    assert _agg(lib, dist=5) == sil.SIL_EINVAL
+    assert _agg(lib, X=None) == sil.SIL_EINVAL
+    assert _agg(lib, dtype=2, cs=None) == sil.SIL_EINVAL  # FP8 needs column scales
+    assert _agg(lib, count=None) == sil.SIL_EINVAL
+    assert _agg(lib, ws=None) == sil.SIL_EWORKSPACE
+    assert _agg(lib, ws=ctypes.c_void_p(256 + 8)) == sil.SIL_EWORKSPACE
+    assert _agg(lib, ws_bytes=100) == sil.SIL_EWORKSPACE
+    assert _agg(lib, k=1 << 23) == sil.SIL_EUNSUPPORTED
+
+
+def test_score_path_validation(lib):
+    vp = ctypes.c_void_p
+    rc = lib.sil_score(vp(16), 0, 10, 4, 4, None, vp(16), 3, 0, vp(16), vp(16), vp(16), None, vp(16),
+                       None, 9, vp(256), 1 << 30, None, None)
+    assert rc == sil.SIL_EINVAL
+    rc = lib.sil_score_backward(vp(16), 0, 10, 4, 4, None, vp(16), 3, 0, vp(16), vp(16), vp(16), None,
+                                None, vp(16), 2, vp(256), 1 << 30, None, None)
+    assert rc == sil.SIL_EINVAL  # lddx < d
+    ks = (ctypes.c_int32 * 2)(3, 0)
+    rc = lib.sil_score_batched(vp(16), 0, 10, 4, 4, None, vp(16), 10, ks, 2, 0, vp(16), vp(256),
+                               1 << 30, None, None)
+    assert rc == sil.SIL_EINVAL  # a labeling with k = 0
+
+
+def test_binding_refuses_cpu_tensors():
+    import torch
+    X = torch.zeros(4, 2)
+    with pytest.raises(RuntimeError, match="CUDA"):
+        sil.aggregate(X, torch.zeros(4, dtype=torch.int32), 2)
