@@ -160,6 +160,34 @@ int sil_score_batched(const void* X, int32_t dtype, int64_t n, int32_t d, int64_
                       const int32_t* k_host, int32_t batch, int32_t dist, double* S_out,
                       void* ws, size_t ws_bytes, uint32_t* dev_status, void* stream);
 
+/* Largest sizes sil_score_noalloc serves. */
+#define SIL_NOALLOC_MAX_K 1024
+#define SIL_NOALLOC_MAX_D 256
+
+/*
+ * sil_score without a workspace argument, for callers that cannot provide
+ * device memory at the point they want a score -- for example code inside a
+ * host framework that owns all device memory through its own pool, where a
+ * raw cudaMalloc can fail or fragment that pool, or a plugin whose host
+ * application forbids allocation on its hot path.  The paper has no
+ * counterpart: this is a deployment convenience.
+ *
+ * Same arguments and results as sil_score (SIMT pass 2 only), minus ws and
+ * ws_bytes.  Its scratch is one fixed device array inside the library
+ * (about 1.1 MB, sized for k <= SIL_NOALLOC_MAX_K and d <= SIL_NOALLOC_MAX_D)
+ * that the driver reserves on every device that loads the library and keeps
+ * until the process exits; the call itself allocates nothing.  Larger k or d
+ * return SIL_EUNSUPPORTED with nothing enqueued.  The first call on a device
+ * looks up the array's device address (with that device current), so make
+ * it before any stream capture starts.  All calls on a device share the
+ * array: calls whose GPU work overlaps race and must be ordered by the
+ * caller.  Each call clears what must start at zero and rewrites the rest.
+ */
+int sil_score_noalloc(const void* X, int32_t dtype, int64_t n, int32_t d, int64_t ldx,
+                      const float* col_scale, const int32_t* labels, int32_t k, int32_t dist,
+                      const int64_t* count, const double* s1, const double* s2, float* s_out,
+                      double* S_out, void* saved, uint32_t* dev_status, void* stream);
+
 /* Human-readable name of a return code or of one status flag. */
 const char* sil_status_string(int32_t status);
 

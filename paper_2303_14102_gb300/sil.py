@@ -73,6 +73,9 @@ def load(build_if_stale: bool = True) -> ctypes.CDLL:
             lib.sil_score_batched.argtypes = [vp, i32, i64, i32, i64, vp, vp, i64, vp, i32, i32, vp,
                                               vp, sz, vp, vp]
             lib.sil_score_batched.restype = ctypes.c_int
+            lib.sil_score_noalloc.argtypes = [vp, i32, i64, i32, i64, vp, vp, i32, i32, vp, vp, vp,
+                                              vp, vp, vp, vp, vp]
+            lib.sil_score_noalloc.restype = ctypes.c_int
             lib.sil_status_string.argtypes = [i32]
             lib.sil_status_string.restype = ctypes.c_char_p
             lib.sil_version.restype = i32
@@ -207,6 +210,28 @@ def score(X: torch.Tensor, labels: torch.Tensor, K: int, agg, metric: str = "sqe
                        _ptr(saved), PATHS[path], _ptr(ws), need, _ptr(status),
                        _stream_handle(X.device))
     _rc(rc, "sil_score")
+    return Score(S=S, s=s, saved=saved)
+
+
+def score_noalloc(X: torch.Tensor, labels: torch.Tensor, K: int, agg, metric: str = "sqeuclidean",
+                  col_scale: torch.Tensor | None = None, want_s: bool = False, save: bool = False,
+                  status: torch.Tensor | None = None) -> Score:
+    """sil_score_noalloc: pass 2 using the library's own fixed scratch array.
+
+    For callers that cannot provide a workspace (k <= 1024, d <= 256).  Calls
+    on one device share that scratch, so their GPU work must not overlap.
+    """
+    _check_X(X, labels)
+    lib = load()
+    N, D = X.shape
+    count, s1, s2 = agg
+    S = torch.empty((), dtype=torch.float64, device=X.device)
+    s = torch.empty(N, dtype=torch.float32, device=X.device) if want_s else None
+    saved = torch.empty(int(lib.sil_saved_size(N)), dtype=torch.uint8, device=X.device) if save else None
+    rc = lib.sil_score_noalloc(_ptr(X), _dtype_code(X), N, D, X.stride(0), _ptr(col_scale),
+                               _ptr(labels), K, METRICS[metric], _ptr(count), _ptr(s1), _ptr(s2),
+                               _ptr(s), _ptr(S), _ptr(saved), _ptr(status), _stream_handle(X.device))
+    _rc(rc, "sil_score_noalloc")
     return Score(S=S, s=s, saved=saved)
 
 
