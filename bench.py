@@ -242,6 +242,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--variants", type=int, default=1, help="also measure the variant lines")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--n", type=int, default=10_000_000,
+                    help="points of the at_scale workload (smaller only for profiling captures)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -255,7 +257,7 @@ def main():
     torch.cuda.set_device(dev)
     sil.load()
     pk = peaks()
-    w = synth.workload_at_scale(device=dev)
+    w = synth.workload_at_scale(device=dev, N=args.n)
     X, lab, K = w.X, w.labels, w.K
     N, D = X.shape
     stream = torch.cuda.current_stream(dev)
@@ -379,8 +381,8 @@ def main():
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": t / args.steps * 1e3,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                 "data": "synthetic",
-                "config": dict(WORKLOAD, parallelism="replicas" if world > 1 else "single",
-                               l2="inputs (2.6 GB) larger than L2 (129 MB); no flush"),
+                "config": dict(WORKLOAD, N=N, parallelism="replicas" if world > 1 else "single",
+                               l2=f"inputs ({N * (4 * D + 4) / 1e9:.2f} GB) larger than L2 (129 MB); no flush"),
                 "S": S_val, "passes": pass_info, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
                 "clocks": clocks, "gpu_launches": launches_per_step * args.steps,
                 "variants": variants}
