@@ -5,7 +5,9 @@
 // so the kernel is SIMT, with no tensor-core reshaping.  A CTA owns a
 // contiguous row range and a column slice (and, for very many clusters, a
 // bucket slice).  Rows are staged in shared memory one tile of 128 rows at a
-// time with coalesced 128-bit loads; the tile's labels are counting-sorted in
+// time -- by TMA (cp.async.bulk.tensor) into a ring of stages that runs ahead
+// of the computation, or, when the layout does not allow a tensor map, by
+// synchronous coalesced 128-bit loads; the tile's labels are counting-sorted in
 // shared memory (integer shared atomics only) so that every (cluster, 4-column
 // chunk) pair present in the tile is summed by ONE thread in registers and
 // added once into a per-CTA FP32 accumulator in shared memory -- no float
@@ -17,8 +19,10 @@
 // The same kernel, with per-row weights and two bucket entries per row, forms
 // the segmented sums of the backward pass.
 #include <climits>
+#include <cstdlib>
 
 #include "sil_internal.cuh"
+#include "tma.cuh"
 
 namespace sil {
 
@@ -123,6 +127,8 @@ struct AggK {
   int32_t nslc;   // column slices
   int32_t kbs;    // buckets per bucket slice
   int64_t rows_per_cta;
+  int32_t stages;      // TMA kernel: pipeline depth
+  int32_t stage_bytes; // TMA kernel: bytes of one stage
   unsigned long long* count;
   double* s1;
   double* s2;
@@ -130,17 +136,20 @@ struct AggK {
   uint32_t* status;
 };
 
+// Tensor maps of the TMA-fed kernel (X tile, labels, second labels, weights).
+struct AggMaps {
+  CUtensorMap x, lab1, lab2, w1, w2;
+};
+
+// Byte offsets of the per-CTA shared state (the part both kernels share).
 struct AggSmem {
-  // byte offsets into dynamic shared memory
-  int xs, acc, acc2, macc, mint, cnt, slot, ebk, epos, ew, order, nel, bstart, inv, wtot, nne,
-      total;
+  int acc, acc2, macc, mint, cnt, slot, ebk, epos, ew, order, nel, bstart, bsize, inv, wtot, nne, total;
 };
 
 __host__ __device__ inline AggSmem agg_smem(int dsp, int kbs, bool dual, bool weighted) {
   const int R = kAggRows, E = dual ? 2 * R : R, c4 = dsp / 4;
   AggSmem s;
   int o = 0;
-  s.xs = o; o += R * dsp * 4;
   s.acc = o; o += kbs * dsp * 4;
   s.acc2 = o; o += weighted ? 0 : kbs * c4 * 4;
   s.macc = o; o += kbs * 4;
@@ -153,228 +162,479 @@ __host__ __device__ inline AggSmem agg_smem(int dsp, int kbs, bool dual, bool we
   s.order = o; o += E * 4;
   s.nel = o; o += E * 4;
   s.bstart = o; o += (E + 1) * 4;
+  s.bsize = o; o += E * 4;
   s.inv = o; o += R * 4;
   s.wtot = o; o += 32 * 4;
   s.nne = o; o += 16;
-  s.total = (o + 15) & ~15;
+  s.total = (o + 127) & ~127;
   return s;
 }
 
-template <int DT, bool DUAL, bool WEIGHTED>
-__global__ void __launch_bounds__(kAggThreads) k_aggregate(AggK a) {
-  extern __shared__ __align__(16) unsigned char smem[];
+struct AggState {
+  float* acc;
+  float4* acc4;
+  float* acc2;
+  float* macc;
+  int* mint;
+  int* cnt;
+  int* slot;
+  int* ebk;
+  int* epos;
+  float* ew;
+  int* order;
+  int* nel;
+  int* bstart;
+  int* bsize;
+  float* inv;
+  int* wtot;
+  int* nne;  // [0] = non-empty bucket count (being built), [1] = abort flag, [2] = count of this tile
+};
+
+__device__ inline AggState agg_state(unsigned char* smem, const AggSmem& L) {
+  AggState S;
+  S.acc = reinterpret_cast<float*>(smem + L.acc);
+  S.acc4 = reinterpret_cast<float4*>(smem + L.acc);
+  S.acc2 = reinterpret_cast<float*>(smem + L.acc2);
+  S.macc = reinterpret_cast<float*>(smem + L.macc);
+  S.mint = reinterpret_cast<int*>(smem + L.mint);
+  S.cnt = reinterpret_cast<int*>(smem + L.cnt);
+  S.slot = reinterpret_cast<int*>(smem + L.slot);
+  S.ebk = reinterpret_cast<int*>(smem + L.ebk);
+  S.epos = reinterpret_cast<int*>(smem + L.epos);
+  S.ew = reinterpret_cast<float*>(smem + L.ew);
+  S.order = reinterpret_cast<int*>(smem + L.order);
+  S.nel = reinterpret_cast<int*>(smem + L.nel);
+  S.bstart = reinterpret_cast<int*>(smem + L.bstart);
+  S.bsize = reinterpret_cast<int*>(smem + L.bsize);
+  S.inv = reinterpret_cast<float*>(smem + L.inv);
+  S.wtot = reinterpret_cast<int*>(smem + L.wtot);
+  S.nne = reinterpret_cast<int*>(smem + L.nne);
+  return S;
+}
+
+// Geometry of one CTA's work item.
+struct AggItem {
+  int cslice, col0, dlim, c4, c4e, kb0, kbn;
+  int64_t row_begin, row_end;
+};
+
+__device__ inline AggItem agg_item(const AggK& a) {
+  AggItem it;
+  it.cslice = blockIdx.x % a.nslc;
+  const int kslice = blockIdx.x / a.nslc;
+  it.col0 = it.cslice * a.dsp;
+  it.dlim = min(a.d, it.col0 + a.dsp);  // columns of this slice are [col0, dlim)
+  it.c4 = a.dsp / 4;
+  it.c4e = int(cdiv(it.dlim - it.col0, 4));  // chunks holding columns < dlim
+  it.kb0 = kslice * a.kbs;
+  it.kbn = min(a.kbs, a.kb - it.kb0);  // buckets of this slice
+  it.row_begin = int64_t(blockIdx.y) * a.rows_per_cta;
+  it.row_end = min(a.n, it.row_begin + a.rows_per_cta);
+  return it;
+}
+
+__device__ inline void agg_zero(const AggState& S, const AggItem& it, int dsp, bool weighted) {
+  const int tid = threadIdx.x, T = blockDim.x;
+  for (int i = tid; i < it.kbn * dsp; i += T) S.acc[i] = 0.f;
+  if (!weighted)
+    for (int i = tid; i < it.kbn * it.c4; i += T) S.acc2[i] = 0.f;
+  for (int i = tid; i < it.kbn; i += T) {
+    S.macc[i] = 0.f;
+    S.mint[i] = 0;
+    S.cnt[i] = 0;
+  }
+  if (tid == 0) {
+    S.nne[0] = 0;
+    S.nne[1] = 0;
+  }
+}
+
+// Tile source of the generic kernel: FP32 rows already in shared memory,
+// labels and weights read from global memory.
+struct SrcGeneric {
+  const float4* xs4;
+  int c4;
+  const int32_t* lab1;
+  const int32_t* lab2;
+  const float* w1;
+  const float* w2;
+  int64_t r0;
+  __device__ float4 chunk(int r, int c) const { return xs4[r * c4 + c]; }
+  __device__ int label1(int r) const { return lab1[r0 + r]; }
+  __device__ int label2(int r) const { return lab2[r0 + r]; }
+  __device__ float weight1(int r) const { return w1[r0 + r]; }
+  __device__ float weight2(int r) const { return w2[r0 + r]; }
+};
+
+// Tile source of the TMA kernel: raw storage rows, labels and weights all in
+// one pipeline stage of shared memory.
+template <int DT>
+struct SrcTma {
+  using T = typename Elem<DT>::T;
+  const T* xs;
+  int dsp;
+  const int32_t* lab1;
+  const int32_t* lab2;
+  const float* w1;
+  const float* w2;
+  const float* cs;
+  int col0, dlim;
+  __device__ float4 chunk(int r, int c) const {
+    const T* p = xs + r * dsp + 4 * c;
+    float4 v;
+    if constexpr (DT == SIL_F32) {
+      v = *reinterpret_cast<const float4*>(p);
+    } else if constexpr (DT == SIL_BF16) {
+      const uint2 u = *reinterpret_cast<const uint2*>(p);
+      const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u.x));
+      const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u.y));
+      v = make_float4(a.x, a.y, b.x, b.y);
+    } else {
+      const uint32_t u = *reinterpret_cast<const uint32_t*>(p);
+      const __nv_fp8_e4m3* q = reinterpret_cast<const __nv_fp8_e4m3*>(&u);
+      v = make_float4(float(q[0]), float(q[1]), float(q[2]), float(q[3]));
+      const int col = col0 + 4 * c;
+      v.x *= col + 0 < dlim ? __ldg(cs + col + 0) : 0.f;
+      v.y *= col + 1 < dlim ? __ldg(cs + col + 1) : 0.f;
+      v.z *= col + 2 < dlim ? __ldg(cs + col + 2) : 0.f;
+      v.w *= col + 3 < dlim ? __ldg(cs + col + 3) : 0.f;
+    }
+    return v;
+  }
+  __device__ int label1(int r) const { return lab1[r]; }
+  __device__ int label2(int r) const { return lab2[r]; }
+  __device__ float weight1(int r) const { return w1[r]; }
+  __device__ float weight2(int r) const { return w2[r]; }
+};
+
+// One 128-row tile: bucket the rows by label (counting sort in shared memory),
+// then one thread per (non-empty bucket, 4-column chunk) sums the bucket's
+// rows in registers and adds the result once into the CTA accumulator.
+// Counters are reset inside; the caller syncs before the next tile (and
+// before its staging buffer is refilled).
+template <bool DUAL, bool WEIGHTED, class Src>
+__device__ void agg_tile(const AggK& a, const AggState& S, const AggItem& it, const Src& src,
+                         int rows, int64_t r0) {
   constexpr int R = kAggRows, T = kAggThreads, E = DUAL ? 2 * R : R;
   const int tid = threadIdx.x;
-  const int c4 = a.dsp / 4;
-  const AggSmem L = agg_smem(a.dsp, a.kbs, DUAL, WEIGHTED);
-  float* xs = reinterpret_cast<float*>(smem + L.xs);
-  float4* xs4 = reinterpret_cast<float4*>(smem + L.xs);
-  float4* acc4 = reinterpret_cast<float4*>(smem + L.acc);
-  float* acc = reinterpret_cast<float*>(smem + L.acc);
-  float* acc2 = reinterpret_cast<float*>(smem + L.acc2);
-  float* macc = reinterpret_cast<float*>(smem + L.macc);
-  int* mint = reinterpret_cast<int*>(smem + L.mint);
-  int* cnt = reinterpret_cast<int*>(smem + L.cnt);
-  int* slot = reinterpret_cast<int*>(smem + L.slot);
-  int* ebk = reinterpret_cast<int*>(smem + L.ebk);
-  int* epos = reinterpret_cast<int*>(smem + L.epos);
-  float* ew = reinterpret_cast<float*>(smem + L.ew);
-  int* order = reinterpret_cast<int*>(smem + L.order);
-  int* nel = reinterpret_cast<int*>(smem + L.nel);
-  int* bstart = reinterpret_cast<int*>(smem + L.bstart);
-  float* inv = reinterpret_cast<float*>(smem + L.inv);
-  int* wtot = reinterpret_cast<int*>(smem + L.wtot);
-  int* nne = reinterpret_cast<int*>(smem + L.nne);
-
-  const int cslice = blockIdx.x % a.nslc;
-  const int kslice = blockIdx.x / a.nslc;
-  const int col0 = cslice * a.dsp;
-  const int dlim = min(a.d, col0 + a.dsp);       // columns of this slice are [col0, dlim)
-  const int kb0 = kslice * a.kbs;
-  const int kbn = min(a.kbs, a.kb - kb0);          // buckets of this slice
-  const int c4e = int(cdiv(dlim - col0, 4));        // chunks holding columns < dlim
-  const int64_t row_begin = int64_t(blockIdx.y) * a.rows_per_cta;
-  const int64_t row_end = min(a.n, row_begin + a.rows_per_cta);
-  const bool in_cta_norm = a.cosine && a.invnorm == nullptr;  // full rows are in this CTA
-
-  for (int i = tid; i < kbn * a.dsp; i += T) acc[i] = 0.f;
-  if (!WEIGHTED)
-    for (int i = tid; i < kbn * c4; i += T) acc2[i] = 0.f;
-  for (int i = tid; i < kbn; i += T) {
-    macc[i] = 0.f;
-    mint[i] = 0;
-    cnt[i] = 0;
+  const bool in_cta_norm = a.cosine && a.invnorm == nullptr;  // full rows are in this tile
+  // (b) bucket entries and row scales
+  for (int e = tid; e < E; e += T) {
+    const int r = e < R ? e : e - R;
+    int lb = -1;
+    float w = 1.f;
+    if (r < rows) {
+      const int lab = (e < R) ? src.label1(r) : src.label2(r);
+      if (lab >= 0 && lab < a.k) {
+        const int bucket = (e < R) ? lab : a.k + lab;
+        if (bucket >= it.kb0 && bucket < it.kb0 + it.kbn) lb = bucket - it.kb0;
+        if (WEIGHTED) w = (e < R) ? src.weight1(r) : src.weight2(r);
+      } else if (e < R || lab != -1) {
+        // a label outside [0, k); -1 marks "no neighbour" in the second entry
+        set_status(a.status, SIL_ELABEL);
+      }
+    }
+    // one shared atomic per distinct bucket per warp: lanes with the same
+    // bucket rank themselves inside the warp and the lowest one reserves
+    // positions for all of them
+    const unsigned peers = __match_any_sync(0xffffffffu, lb);
+    const int leader = __ffs(peers) - 1;
+    const int lane = tid & 31;
+    int p = 0;
+    if (lb >= 0 && lane == leader) {
+      p = atomicAdd(&S.cnt[lb], __popc(peers));
+      if (p == 0) {
+        const int q = atomicAdd(&S.nne[0], 1);
+        S.nel[q] = lb;
+        S.slot[lb] = q;
+      }
+    }
+    p = __shfl_sync(0xffffffffu, p, leader);
+    if (lb >= 0) S.epos[e] = p + __popc(peers & ((1u << lane) - 1u));
+    S.ebk[e] = lb;
+    S.ew[e] = w;
   }
-  if (tid == 0) *nne = 0;
-  __syncthreads();
-
-  for (int64_t r0 = row_begin; r0 < row_end; r0 += R) {
-    const int rows = int((row_end - r0) < int64_t(R) ? (row_end - r0) : int64_t(R));
-    // (a) the tile's column slice, dequantised to FP32
-    for (int q = tid; q < R * c4; q += T) {
-      const int r = q / c4, c = q - r * c4;
-      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (r < rows) v = load4<DT>(a.X, r0 + r, col0 + 4 * c, dlim, a.ldx, a.cs, a.vec);
-      xs4[q] = v;
-    }
-    __syncthreads();
-    // (b) bucket entries and row scales
-    for (int e = tid; e < E; e += T) {
-      const int r = e < R ? e : e - R;
-      int lb = -1;
-      float w = 1.f;
-      if (r < rows) {
-        const int64_t row = r0 + r;
-        int32_t lab = (e < R) ? a.lab1[row] : a.lab2[row];
-        if (lab >= 0 && lab < a.k) {
-          const int bucket = (e < R) ? lab : a.k + lab;
-          if (bucket >= kb0 && bucket < kb0 + kbn) lb = bucket - kb0;
-          if (WEIGHTED) w = (e < R) ? a.w1[row] : a.w2[row];
-        } else if (e < R || lab != -1) {
-          // a label outside [0, k); -1 marks "no neighbour" in the second entry
-          set_status(a.status, SIL_ELABEL);
-        }
-      }
-      if (lb >= 0) {
-        const int p = atomicAdd(&cnt[lb], 1);
-        if (p == 0) {
-          const int q = atomicAdd(nne, 1);
-          nel[q] = lb;
-          slot[lb] = q;
-        }
-        epos[e] = p;
-      }
-      ebk[e] = lb;
-      ew[e] = w;
-    }
-    if (a.cosine) {
-      if (in_cta_norm) {
-        const int warp = tid >> 5, lane = tid & 31;
-        for (int r = warp; r < R; r += T / 32) {
-          float ss = 0.f;
-          for (int c = lane; c < a.dsp; c += 32) ss += xs[r * a.dsp + c] * xs[r * a.dsp + c];
-          for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
-          if (lane == 0) {
-            if (r < rows && !(ss > 0.f)) set_status(a.status, SIL_EZERONORM);
-            inv[r] = ss > 0.f ? rsqrtf(ss) : 0.f;
-          }
-        }
-      } else {
-        for (int r = tid; r < R; r += T) inv[r] = r < rows ? a.invnorm[r0 + r] : 0.f;
-      }
-    }
-    __syncthreads();
-    // (c) exclusive scan of the bucket sizes over the non-empty list
-    const int m = *nne;
-    {
+  if (a.cosine) {
+    if (in_cta_norm) {
       const int warp = tid >> 5, lane = tid & 31;
-      int v = (tid < m) ? cnt[nel[tid]] : 0;
-      int incl = v;
-      for (int o = 1; o < 32; o <<= 1) {
-        int t = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += t;
-      }
-      if (lane == 31) wtot[warp] = incl;
-      __syncthreads();
-      int off = 0;
-      for (int w = 0; w < warp; ++w) off += wtot[w];
-      if (tid < m) bstart[tid] = off + incl - v;
-    }
-    __syncthreads();
-    // (d) scatter entries into bucket order
-    for (int e = tid; e < E; e += T) {
-      const int lb = ebk[e];
-      if (lb >= 0) order[bstart[slot[lb]] + epos[e]] = e;
-    }
-    __syncthreads();
-    // (e) one thread per (non-empty bucket, 4-column chunk of this slice)
-    for (int p = tid; p < m * c4e; p += T) {
-      const int q = p / c4e, c = p - q * c4e;
-      const int lb = nel[q];
-      const int kc = (kb0 + lb) % a.k;  // cluster whose reference point shifts this bucket
-      const float4 rr = *reinterpret_cast<const float4*>(a.rs + int64_t(kc) * a.dz + col0 + 4 * c);
-      float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
-      float sq = 0.f, wsum = 0.f;
-      const int jb = bstart[q], je = jb + cnt[lb];
-#pragma unroll 4
-      for (int j = jb; j < je; ++j) {
-        const int e = order[j];
-        const int r = e < R ? e : e - R;
-        const float4 x = xs4[r * c4 + c];
-        const float sc = a.cosine ? inv[r] : 1.f;
-        float4 v;
-        v.x = fmaf(sc, x.x, -rr.x);
-        v.y = fmaf(sc, x.y, -rr.y);
-        v.z = fmaf(sc, x.z, -rr.z);
-        v.w = fmaf(sc, x.w, -rr.w);
-        if (WEIGHTED) {
-          const float w = ew[e];
-          v.x *= w; v.y *= w; v.z *= w; v.w *= w;
-          wsum += w;
-        } else {
-          sq = fmaf(v.x, v.x, fmaf(v.y, v.y, fmaf(v.z, v.z, fmaf(v.w, v.w, sq))));
+      for (int r = warp; r < R; r += T / 32) {
+        float ss = 0.f;
+        for (int c = lane; c < it.c4e; c += 32) {
+          const float4 v = src.chunk(r, c);
+          ss += v.x * v.x + v.y * v.y + v.z * v.z + v.w * v.w;
         }
-        s.x += v.x; s.y += v.y; s.z += v.z; s.w += v.w;
+        for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+        if (lane == 0) {
+          if (r < rows && !(ss > 0.f)) set_status(a.status, SIL_EZERONORM);
+          S.inv[r] = ss > 0.f ? rsqrtf(ss) : 0.f;
+        }
       }
-      float4 t = acc4[lb * c4 + c];
-      t.x += s.x; t.y += s.y; t.z += s.z; t.w += s.w;
-      acc4[lb * c4 + c] = t;
-      if (!WEIGHTED) acc2[lb * c4 + c] += sq;
-      if (c == 0) {
-        mint[lb] += je - jb;
-        if (WEIGHTED) macc[lb] += wsum;
-      }
+    } else {
+      for (int r = tid; r < R; r += T) S.inv[r] = r < rows ? a.invnorm[r0 + r] : 0.f;
     }
-    __syncthreads();
-    // (f) reset the counters used by this tile
-    for (int q = tid; q < m; q += T) cnt[nel[q]] = 0;
-    if (tid == 0) *nne = 0;
-    // the __syncthreads after the next tile load orders this reset before reuse
   }
   __syncthreads();
-
-  // flush: un-shift in FP64 and add into the outputs
-  const int dsl = dlim - col0;
-  for (int i = tid; i < kbn * dsl; i += T) {
-    const int lb = i / dsl, col = i - lb * dsl;
-    const int mm = mint[lb];
-    if (mm == 0) continue;
-    const int kg = kb0 + lb;
-    double v = double(acc[lb * a.dsp + col]);
-    if (!WEIGHTED) v += double(mm) * double(a.rs[int64_t(kg) * a.dz + col0 + col]);
-    atomicAdd(a.s1 + int64_t(kg) * a.d + col0 + col, v);
+  // (c) warp 0: exclusive scan of the bucket sizes over the non-empty list;
+  // it also resets the counters, so no barrier is needed after the tile
+  if (tid < 32) {
+    const int lane = tid;
+    const int m = S.nne[0];
+    const int per = (m + 31) / 32;  // consecutive entries per lane
+    const int q0 = lane * per, q1 = min(m, q0 + per);
+    int local = 0;
+    for (int q = q0; q < q1; ++q) local += S.cnt[S.nel[q]];
+    int incl = local;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += t;
+    }
+    int run = incl - local;
+    for (int q = q0; q < q1; ++q) {
+      const int lb = S.nel[q];
+      const int c = S.cnt[lb];
+      S.bstart[q] = run;
+      S.bsize[q] = c;
+      run += c;
+      S.cnt[lb] = 0;
+    }
+    __syncwarp();
+    if (lane == 0) {
+      S.nne[2] = m;
+      S.nne[0] = 0;
+    }
   }
-  for (int lb = tid; lb < kbn; lb += T) {
-    const int mm = mint[lb];
+  __syncthreads();
+  const int m = S.nne[2];
+  // (d) scatter entries into bucket order
+  for (int e = tid; e < E; e += T) {
+    const int lb = S.ebk[e];
+    if (lb >= 0) S.order[S.bstart[S.slot[lb]] + S.epos[e]] = e;
+  }
+  __syncthreads();
+  // (e) one thread per (non-empty bucket, 4-column chunk of this slice)
+  for (int p = tid; p < m * it.c4e; p += T) {
+    const int q = p / it.c4e, c = p - q * it.c4e;
+    const int lb = S.nel[q];
+    const int bg = it.kb0 + lb;
+    const int kc = bg < a.k ? bg : bg - a.k;  // cluster whose reference point shifts this bucket
+    const float4 rr =
+        *reinterpret_cast<const float4*>(a.rs + int64_t(kc) * a.dz + it.col0 + 4 * c);
+    float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+    float sq = 0.f, wsum = 0.f;
+    const int jb = S.bstart[q], je = jb + S.bsize[q];
+#pragma unroll 4
+    for (int j = jb; j < je; ++j) {
+      const int e = S.order[j];
+      const int r = DUAL ? (e < R ? e : e - R) : e;
+      const float4 x = src.chunk(r, c);
+      const float sc = a.cosine ? S.inv[r] : 1.f;
+      float4 v;
+      v.x = fmaf(sc, x.x, -rr.x);
+      v.y = fmaf(sc, x.y, -rr.y);
+      v.z = fmaf(sc, x.z, -rr.z);
+      v.w = fmaf(sc, x.w, -rr.w);
+      if (WEIGHTED) {
+        const float w = S.ew[e];
+        v.x *= w; v.y *= w; v.z *= w; v.w *= w;
+        wsum += w;
+      } else {
+        sq = fmaf(v.x, v.x, fmaf(v.y, v.y, fmaf(v.z, v.z, fmaf(v.w, v.w, sq))));
+      }
+      s.x += v.x; s.y += v.y; s.z += v.z; s.w += v.w;
+    }
+    float4 t = S.acc4[lb * it.c4 + c];
+    t.x += s.x; t.y += s.y; t.z += s.z; t.w += s.w;
+    S.acc4[lb * it.c4 + c] = t;
+    if (!WEIGHTED) S.acc2[lb * it.c4 + c] += sq;
+    if (c == 0) {
+      S.mint[lb] += je - jb;
+      if (WEIGHTED) S.macc[lb] += wsum;
+    }
+  }
+  // the caller's barrier after this tile orders (e) before the next tile's (b)
+}
+
+// Un-shift in FP64 and add the CTA's sums into the outputs.
+template <bool WEIGHTED>
+__device__ void agg_flush(const AggK& a, const AggState& S, const AggItem& it) {
+  const int tid = threadIdx.x, T = blockDim.x;
+  const int dsl = it.dlim - it.col0;
+  for (int i = tid; i < it.kbn * dsl; i += T) {
+    const int lb = i / dsl, col = i - lb * dsl;
+    const int mm = S.mint[lb];
     if (mm == 0) continue;
-    const int kg = kb0 + lb;
+    const int kg = it.kb0 + lb;
+    double v = double(S.acc[lb * a.dsp + col]);
+    if (!WEIGHTED) v += double(mm) * double(a.rs[int64_t(kg) * a.dz + it.col0 + col]);
+    atomicAdd(a.s1 + int64_t(kg) * a.d + it.col0 + col, v);
+  }
+  for (int lb = tid; lb < it.kbn; lb += T) {
+    const int mm = S.mint[lb];
+    if (mm == 0) continue;
+    const int kg = it.kb0 + lb;
     if (WEIGHTED) {
-      if (cslice == 0) atomicAdd(a.wsum + kg, double(macc[lb]));
+      if (it.cslice == 0) atomicAdd(a.wsum + kg, double(S.macc[lb]));
     } else {
       double t = 0.0;
-      for (int c = 0; c < c4e; ++c) t += double(acc2[lb * c4 + c]);
+      for (int c = 0; c < it.c4e; ++c) t += double(S.acc2[lb * it.c4 + c]);
       for (int col = 0; col < dsl; ++col) {
-        const double r = a.rs[int64_t(kg) * a.dz + col0 + col];
-        t += 2.0 * r * double(acc[lb * a.dsp + col]) + double(mm) * r * r;
+        const double r = a.rs[int64_t(kg) * a.dz + it.col0 + col];
+        t += 2.0 * r * double(S.acc[lb * a.dsp + col]) + double(mm) * r * r;
       }
       atomicAdd(a.s2 + kg, t);
-      if (cslice == 0) atomicAdd(a.count + kg, (unsigned long long)mm);
+      if (it.cslice == 0) atomicAdd(a.count + kg, (unsigned long long)mm);
     }
   }
 }
 
-// Choose (dsp, kbs) so that one CTA's shared memory stays within budget.
+// Generic pass 1: synchronous coalesced loads (any alignment, any ldx).
+template <int DT, bool DUAL, bool WEIGHTED>
+__global__ void __launch_bounds__(kAggThreads) k_aggregate(AggK a) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  constexpr int R = kAggRows, T = kAggThreads;
+  const int tid = threadIdx.x;
+  const AggSmem L = agg_smem(a.dsp, a.kbs, DUAL, WEIGHTED);
+  const AggState S = agg_state(smem, L);
+  float4* xs4 = reinterpret_cast<float4*>(smem + L.total);  // [R][dsp] FP32 tile
+  const AggItem it = agg_item(a);
+  agg_zero(S, it, a.dsp, WEIGHTED);
+  __syncthreads();
+  for (int64_t r0 = it.row_begin; r0 < it.row_end; r0 += R) {
+    const int rows = int((it.row_end - r0) < int64_t(R) ? (it.row_end - r0) : int64_t(R));
+    for (int q = tid; q < R * it.c4; q += T) {
+      const int r = q / it.c4, c = q - r * it.c4;
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (r < rows) v = load4<DT>(a.X, r0 + r, it.col0 + 4 * c, it.dlim, a.ldx, a.cs, a.vec);
+      xs4[q] = v;
+    }
+    __syncthreads();
+    const SrcGeneric src{xs4, it.c4, a.lab1, a.lab2, a.w1, a.w2, r0};
+    agg_tile<DUAL, WEIGHTED>(a, S, it, src, rows, r0);
+    __syncthreads();
+  }
+  agg_flush<WEIGHTED>(a, S, it);
+}
+
+// TMA-fed pass 1: a ring of `stages` shared-memory buffers filled by
+// cp.async.bulk.tensor (X tile, labels, weights) while earlier tiles are
+// processed.  Thread 0 refills a buffer as soon as every thread is done with
+// it.  Waits are bounded: on a timeout the CTA flags SIL_ETIMEOUT, waits
+// (bounded) for its own copies in flight and returns without flushing.
+template <int DT, bool DUAL, bool WEIGHTED>
+__global__ void __launch_bounds__(kAggThreads) k_aggregate_tma(AggK a, const __grid_constant__ AggMaps maps) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  using T = typename Elem<DT>::T;
+  constexpr int R = kAggRows;
+  constexpr int esz = sizeof(T);
+  const int tid = threadIdx.x;
+  const AggSmem L = agg_smem(a.dsp, a.kbs, DUAL, WEIGHTED);
+  const AggState S = agg_state(smem, L);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L.total);
+  unsigned char* stage0 = smem + L.total + 128;  // stage buffers, 128-byte aligned
+  const AggItem it = agg_item(a);
+  const int64_t nrows = it.row_end > it.row_begin ? it.row_end - it.row_begin : 0;
+  const int ntiles = int(cdiv(nrows, R));
+  const int xbytes = R * a.dsp * esz;
+  const int nvec = 1 + (DUAL ? 1 : 0) + (WEIGHTED ? (DUAL ? 2 : 1) : 0);
+  const uint32_t tx = uint32_t(xbytes + nvec * R * 4);
+
+  if (tid == 0) {
+    for (int s = 0; s < a.stages; ++s) mbar_init(&bars[s], 1);
+    fence_mbar_init();
+  }
+  agg_zero(S, it, a.dsp, WEIGHTED);
+  __syncthreads();
+
+  auto issue = [&](int t) {
+    const int s = t % a.stages;
+    unsigned char* buf = stage0 + s * a.stage_bytes;
+    const int32_t row = int32_t(it.row_begin + int64_t(t) * R);
+    mbar_arrive_expect_tx(&bars[s], tx);
+    tma_load_2d(buf, &maps.x, it.col0, row, &bars[s]);
+    unsigned char* v = buf + xbytes;
+    tma_load_1d(v, &maps.lab1, row, &bars[s]);
+    v += R * 4;
+    if (DUAL) {
+      tma_load_1d(v, &maps.lab2, row, &bars[s]);
+      v += R * 4;
+    }
+    if (WEIGHTED) {
+      tma_load_1d(v, &maps.w1, row, &bars[s]);
+      v += R * 4;
+      if (DUAL) tma_load_1d(v, &maps.w2, row, &bars[s]);
+    }
+  };
+  if (tid == 0) {
+    fence_proxy_async_smem();
+    for (int t = 0; t < ntiles && t < a.stages; ++t) issue(t);
+  }
+
+  int t = 0;
+  bool aborted = false;
+  for (; t < ntiles; ++t) {
+    const int s = t % a.stages;
+    if (!mbar_wait(&bars[s], uint32_t((t / a.stages) & 1))) {
+      // This thread gave up.  It still runs the tile (on whatever the buffer
+      // holds; every index stays in bounds) so that all threads meet the same
+      // barriers, and the whole CTA stops uniformly after the tile.
+      S.nne[1] = 1;
+      set_status(a.status, SIL_ETIMEOUT);
+    }
+    const int64_t r0 = it.row_begin + int64_t(t) * R;
+    const int rows = int((it.row_end - r0) < int64_t(R) ? (it.row_end - r0) : int64_t(R));
+    const unsigned char* buf = stage0 + s * a.stage_bytes;
+    const int32_t* v = reinterpret_cast<const int32_t*>(buf + xbytes);
+    SrcTma<DT> src;
+    src.xs = reinterpret_cast<const T*>(buf);
+    src.dsp = a.dsp;
+    src.lab1 = v;
+    src.lab2 = DUAL ? v + R : nullptr;
+    src.w1 = WEIGHTED ? reinterpret_cast<const float*>(v + (DUAL ? 2 : 1) * R) : nullptr;
+    src.w2 = (WEIGHTED && DUAL) ? reinterpret_cast<const float*>(v + 3 * R) : nullptr;
+    src.cs = a.cs;
+    src.col0 = it.col0;
+    src.dlim = it.dlim;
+    agg_tile<DUAL, WEIGHTED>(a, S, it, src, rows, r0);
+    __syncthreads();
+    if (S.nne[1]) {  // a thread timed out on this tile's barrier
+      aborted = true;
+      ++t;
+      break;
+    }
+    if (tid == 0 && t + a.stages < ntiles) {
+      fence_proxy_async_smem();
+      issue(t + a.stages);
+    }
+  }
+  if (aborted) {
+    // every thread stops; thread 0 waits (bounded) for this CTA's copies in flight
+    __syncthreads();
+    if (tid == 0) {
+      // tiles t-1 .. t-2+stages were issued and not consumed: one per stage
+      const int first = t - 1;
+      const int end = ntiles < first + a.stages ? ntiles : first + a.stages;
+      for (int u = first; u < end; ++u) mbar_wait(&bars[u % a.stages], uint32_t((u / a.stages) & 1));
+    }
+    __syncthreads();
+    return;
+  }
+  agg_flush<WEIGHTED>(a, S, it);
+}
+
 // Column slices of at least 32 columns keep each row read a whole number of
 // 32-byte DRAM sectors (bf16/fp32); a CTA may use up to 200 KB to get there.
 void agg_plan(int32_t d, int32_t kb, bool dual, bool weighted, int* dsp_out, int* kbs_out) {
   const int dz = int(round_up(d, 4));
+  const int dmax = dz < 256 ? dz : 256;  // the accumulation phase covers at most 64 chunks
   const int budgets[2] = {kSmemBudget, 200 * 1024};
   const int min_dsp = dz < 32 ? dz : 32;
+  auto total = [&](int dsp, int kbs) {  // generic kernel: shared state + one FP32 tile
+    return agg_smem(dsp, kbs, dual, weighted).total + kAggRows * dsp * 4;
+  };
   for (int budget : budgets) {
-    int dsp = dz;
-    while (dsp > min_dsp && agg_smem(dsp, kb, dual, weighted).total > budget)
-      dsp = std::max(min_dsp, int(round_up(dsp / 2, 4)));
-    if (agg_smem(dsp, kb, dual, weighted).total <= budget) {
+    int dsp = dmax;
+    while (dsp > min_dsp && total(dsp, kb) > budget) dsp = std::max(min_dsp, int(round_up(dsp / 2, 4)));
+    if (total(dsp, kb) <= budget) {
       *dsp_out = dsp;
       *kbs_out = kb;
       return;
@@ -383,7 +643,7 @@ void agg_plan(int32_t d, int32_t kb, bool dual, bool weighted, int* dsp_out, int
   // very many buckets: narrowest slice, then split the buckets
   int dsp = min_dsp;
   int kbs = kb;
-  while (kbs > 1 && agg_smem(dsp, kbs, dual, weighted).total > 200 * 1024) kbs = (kbs + 1) / 2;
+  while (kbs > 1 && total(dsp, kbs) > 200 * 1024) kbs = (kbs + 1) / 2;
   *dsp_out = dsp;
   *kbs_out = kbs;
 }
@@ -392,6 +652,8 @@ bool vec_ok(const void* X, int32_t dtype, int64_t ldx) {
   const int esz = dtype == SIL_F32 ? 4 : dtype == SIL_BF16 ? 2 : 1;
   return (reinterpret_cast<uintptr_t>(X) % (4 * esz) == 0) && (ldx % 4 == 0);
 }
+
+inline bool aligned16(const void* p) { return p == nullptr || reinterpret_cast<uintptr_t>(p) % 16 == 0; }
 
 }  // namespace
 
@@ -430,8 +692,10 @@ cudaError_t launch_invnorm(const void* X, int32_t dtype, int64_t n, int32_t d, i
   return cudaGetLastError();
 }
 
+namespace {
+
 template <int DT, bool DUAL, bool WEIGHTED>
-static cudaError_t launch_agg_t(const AggK& k, dim3 grid, int smem, cudaStream_t stream) {
+cudaError_t launch_generic_t(const AggK& k, dim3 grid, int smem, cudaStream_t stream) {
   auto fn = k_aggregate<DT, DUAL, WEIGHTED>;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
@@ -439,6 +703,61 @@ static cudaError_t launch_agg_t(const AggK& k, dim3 grid, int smem, cudaStream_t
   return cudaGetLastError();
 }
 
+template <int DT, bool DUAL, bool WEIGHTED>
+cudaError_t launch_tma_t(const AggK& k, const AggMaps& maps, dim3 grid, int smem, cudaStream_t stream) {
+  auto fn = k_aggregate_tma<DT, DUAL, WEIGHTED>;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  fn<<<grid, kAggThreads, smem, stream>>>(k, maps);
+  return cudaGetLastError();
+}
+
+template <bool DUAL, bool WEIGHTED>
+cudaError_t dispatch(int dtype, bool tma, const AggK& k, const AggMaps& maps, dim3 grid, int smem,
+                     cudaStream_t st) {
+  switch (dtype) {
+    case SIL_F32:
+      return tma ? launch_tma_t<SIL_F32, DUAL, WEIGHTED>(k, maps, grid, smem, st)
+                 : launch_generic_t<SIL_F32, DUAL, WEIGHTED>(k, grid, smem, st);
+    case SIL_BF16:
+      return tma ? launch_tma_t<SIL_BF16, DUAL, WEIGHTED>(k, maps, grid, smem, st)
+                 : launch_generic_t<SIL_BF16, DUAL, WEIGHTED>(k, grid, smem, st);
+    default:
+      return tma ? launch_tma_t<SIL_FP8_E4M3, DUAL, WEIGHTED>(k, maps, grid, smem, st)
+                 : launch_generic_t<SIL_FP8_E4M3, DUAL, WEIGHTED>(k, grid, smem, st);
+  }
+}
+
+// Tensor maps for the TMA kernel; false when the layout does not allow them.
+bool make_maps(const AggLaunch& L, const AggK& k, AggMaps* maps) {
+  const int esz = L.dtype == SIL_F32 ? 4 : L.dtype == SIL_BF16 ? 2 : 1;
+  const CUtensorMapDataType xt = L.dtype == SIL_F32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                 : L.dtype == SIL_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                                       : CU_TENSOR_MAP_DATA_TYPE_UINT8;
+  if ((k.dsp * esz) % 16 != 0 || k.dsp > 256 || k.dsp > L.d) return false;
+  if (!aligned16(L.labels) || !aligned16(L.labels2) || !aligned16(L.w1) || !aligned16(L.w2)) return false;
+  if (!encode_tmap_2d(&maps->x, L.X, xt, esz, uint64_t(L.d), uint64_t(L.n), uint64_t(L.ldx) * esz,
+                      uint32_t(k.dsp), uint32_t(kAggRows), CU_TENSOR_MAP_SWIZZLE_NONE))
+    return false;
+  if (!encode_tmap_1d(&maps->lab1, L.labels, CU_TENSOR_MAP_DATA_TYPE_INT32, uint64_t(L.n), kAggRows))
+    return false;
+  maps->lab2 = maps->lab1;
+  maps->w1 = maps->lab1;
+  maps->w2 = maps->lab1;
+  if (L.labels2 &&
+      !encode_tmap_1d(&maps->lab2, L.labels2, CU_TENSOR_MAP_DATA_TYPE_INT32, uint64_t(L.n), kAggRows))
+    return false;
+  if (L.w1 && !encode_tmap_1d(&maps->w1, L.w1, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, uint64_t(L.n), kAggRows))
+    return false;
+  if (L.w2 && !encode_tmap_1d(&maps->w2, L.w2, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, uint64_t(L.n), kAggRows))
+    return false;
+  return true;
+}
+
+}  // namespace
+
+// Selects the TMA kernel when the layout allows (set SIL_AGG_GENERIC=1 in the
+// environment to force the generic kernel).
 cudaError_t launch_aggregate(const AggLaunch& L) {
   if (L.n == 0) return cudaSuccess;
   const bool dual = L.labels2 != nullptr;
@@ -462,6 +781,9 @@ cudaError_t launch_aggregate(const AggLaunch& L) {
   k.invnorm = L.invnorm;
   int dsp, kbs;
   agg_plan(L.d, k.kb, dual, weighted, &dsp, &kbs);
+  const int esz = L.dtype == SIL_F32 ? 4 : L.dtype == SIL_BF16 ? 2 : 1;
+  const int box_mult = 16 / esz;  // TMA box rows must be whole 16-byte units
+  if (dsp % box_mult != 0 && round_up(dsp, box_mult) <= 256) dsp = int(round_up(dsp, box_mult));
   k.dsp = dsp;
   k.kbs = kbs;
   k.nslc = int(cdiv(L.d, dsp));
@@ -472,30 +794,40 @@ cudaError_t launch_aggregate(const AggLaunch& L) {
   k.s2 = L.s2;
   k.wsum = L.wsum;
   k.status = L.status;
-  const int smem = agg_smem(dsp, kbs, dual, weighted).total;
+
+  const int fixed = agg_smem(dsp, kbs, dual, weighted).total;
+  const int nvec = 1 + (dual ? 1 : 0) + (weighted ? (dual ? 2 : 1) : 0);
+  const int stage = int(round_up(kAggRows * dsp * esz + nvec * kAggRows * 4, 128));
+  const char* force_generic = getenv("SIL_AGG_GENERIC");
+  AggMaps maps{};
+  bool tma = !(force_generic && force_generic[0] == '1') && L.n < (int64_t(1) << 31);
+  int stages = 0, smem = 0;
+  if (tma) {
+    // two CTAs per SM when two stages fit twice, else one CTA with up to four stages
+    const int two_cta = (220 * 1024) / 2;
+    if (fixed + 128 + 2 * stage <= two_cta) {
+      stages = std::min(4, (two_cta - fixed - 128) / stage);
+    } else {
+      stages = std::min(4, (220 * 1024 - fixed - 128) / stage);
+    }
+    tma = stages >= 2 && make_maps(L, k, &maps);
+    smem = fixed + 128 + stages * stage;
+  }
+  if (!tma) smem = fixed + kAggRows * dsp * 4;
+  k.stages = stages;
+  k.stage_bytes = stage;
   const int per_sm = std::max(1, std::min(4, (220 * 1024) / std::max(smem, 1)));
   const int64_t tiles = cdiv(L.n, kAggRows);
   const int64_t slices = int64_t(k.nslc) * nkslc;
-  int64_t row_blocks = std::max<int64_t>(1, (int64_t(kNumSMs) * per_sm * 2) / slices);
+  int64_t row_blocks = std::max<int64_t>(1, (int64_t(kNumSMs) * per_sm * (tma ? 1 : 2)) / slices);
   row_blocks = std::min<int64_t>(row_blocks, tiles);
   row_blocks = std::min<int64_t>(row_blocks, 65535);
   k.rows_per_cta = cdiv(tiles, row_blocks) * kAggRows;
   row_blocks = cdiv(L.n, k.rows_per_cta);
   const dim3 grid(static_cast<unsigned>(slices), static_cast<unsigned>(row_blocks));
-  switch (L.dtype) {
-    case SIL_F32:
-      return dual ? launch_agg_t<SIL_F32, true, true>(k, grid, smem, L.stream)
-                  : weighted ? launch_agg_t<SIL_F32, false, true>(k, grid, smem, L.stream)
-                             : launch_agg_t<SIL_F32, false, false>(k, grid, smem, L.stream);
-    case SIL_BF16:
-      return dual ? launch_agg_t<SIL_BF16, true, true>(k, grid, smem, L.stream)
-                  : weighted ? launch_agg_t<SIL_BF16, false, true>(k, grid, smem, L.stream)
-                             : launch_agg_t<SIL_BF16, false, false>(k, grid, smem, L.stream);
-    default:
-      return dual ? launch_agg_t<SIL_FP8_E4M3, true, true>(k, grid, smem, L.stream)
-                  : weighted ? launch_agg_t<SIL_FP8_E4M3, false, true>(k, grid, smem, L.stream)
-                             : launch_agg_t<SIL_FP8_E4M3, false, false>(k, grid, smem, L.stream);
-  }
+  if (dual) return dispatch<true, true>(L.dtype, tma, k, maps, grid, smem, L.stream);
+  if (weighted) return dispatch<false, true>(L.dtype, tma, k, maps, grid, smem, L.stream);
+  return dispatch<false, false>(L.dtype, tma, k, maps, grid, smem, L.stream);
 }
 
 }  // namespace sil

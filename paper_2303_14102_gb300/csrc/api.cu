@@ -139,7 +139,8 @@ int run_score(const void* X, int32_t dtype, int64_t n, int32_t d, int64_t ldx, c
               const int32_t* labels, int32_t k, int32_t dist, float* s_out, float* sa, float* sb,
               int32_t* skstar, int32_t path, void* ws, const WsLayout& L, cudaStream_t st,
               int32_t* np) {
-  if (path == SIL_PATH_TENSOR) return SIL_EUNSUPPORTED;
+  const bool tc_ok = path != SIL_PATH_SIMT && tc_eligible(dtype, n, d, ldx, k, X, labels);
+  if (path == SIL_PATH_TENSOR && !tc_ok) return SIL_EUNSUPPORTED;
   ScoreLaunch s{};
   s.X = X;
   s.dtype = dtype;
@@ -161,6 +162,7 @@ int run_score(const void* X, int32_t dtype, int64_t n, int32_t d, int64_t ldx, c
   s.n_partials = np;
   s.status = at<uint32_t>(ws, L.misc);
   s.stream = st;
+  if (tc_ok) return cu(launch_score_tc(s, at<double>(ws, L.g), at<void>(ws, L.zbf), s.status));
   return cu(launch_score_simt(s));
 }
 

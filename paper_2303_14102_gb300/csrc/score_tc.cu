@@ -1,0 +1,714 @@
+// Pass 2 on the 5th-generation tensor cores (tcgen05 + TMEM + TMA).
+//
+// The K dot products of every point with the centred centroids (the
+// x_i . Y_k term of Eq. 10/11, and x_hat_i . Omega_k of Eq. 17/18) form the
+// GEMM  X (n x d) . Z^T (d x K).  This kernel runs it in BF16 with FP32
+// accumulation in tensor memory, at FP32-level accuracy:
+//   * Z = mu' is split into hi + lo BF16 parts (mu' - hi rounded again), so
+//     B carries ~16 significant bits;
+//   * FP32 X (SPLIT) is split the same way by converter warps inside the
+//     kernel and the GEMM is hi.Zhi + hi.Zlo + lo.Zhi (the lo.lo term is
+//     below FP32 rounding of the result);
+//   * BF16 X is exact in BF16: x.Zhi + x.Zlo.
+// The epilogue reads each point's K accumulators from TMEM, forms
+// d_k = ||x'||^2 + cb_k - 2 inv x.mu'_k (cb_k = bias_k + 2 g.mu'_k folds the
+// centring on the global mean g back in; inv = 1/||x|| for cosine) and keeps
+// the minimum over k != own cluster.  The own-cluster term a_i uses the exact
+// difference form in FP32 on the converter warps.  The n x K matrix never
+// leaves TMEM.
+//
+// One persistent CTA per SM, 14 warps:
+//   warp 0       TMA producer (X tiles, labels; the split centroids once)
+//   warp 1       TMEM allocation + single-thread tcgen05.mma issue
+//   warps 2-9    converters: two threads per tile row (one per half) --
+//                FP32 -> BF16 hi/lo in the 128-byte-swizzled K-major layout,
+//                ||x'||^2 and the exact a_i, with the centroids, the global
+//                centre and the cluster constants staged in shared memory
+//   warps 10-13  epilogue: tcgen05.ld, masked running minimum, s_i, sums
+// Ring buffers: raw X stages (SPLIT), A buffers, and two TMEM accumulators,
+// each guarded by mbarriers.  Every wait is bounded (SIL_ETIMEOUT); on a
+// timeout all roles stop, in-flight copies and MMAs are waited for (bounded)
+// and TMEM is freed before the CTA exits.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cstdlib>
+
+#include "sil_internal.cuh"
+#include "tma.cuh"
+
+namespace sil {
+
+namespace {
+
+constexpr int kTM = 128;           // points per tile = TMEM lanes
+constexpr int kTcThreads = 448;    // 14 warps
+constexpr int kConvWarps = 8;      // warps 2..9
+constexpr int kEpiWarp0 = 2 + kConvWarps;  // warps 10..13
+constexpr int kAtomBytes = kTM * 128;  // one 128-row x 128-byte swizzle column
+
+// ------------------------------------------------------------ tcgen05 PTX
+__device__ __forceinline__ uint64_t umma_desc_sw128(uint32_t saddr) {
+  // K-major, 128-byte swizzle: 8-row groups 1024 bytes apart (SBO), version 1.
+  return uint64_t((saddr >> 4) & 0x3FFF) | (uint64_t(1) << 16) | (uint64_t(1024 >> 4) << 32) |
+         (uint64_t(1) << 46) | (uint64_t(2) << 61);
+}
+
+__host__ __device__ constexpr uint32_t umma_idesc_bf16(int M, int N) {
+  return (1u << 4)                          // D: FP32
+         | (1u << 7)                        // A: BF16
+         | (1u << 10)                       // B: BF16
+         | ((uint32_t(N) >> 3) << 17)       // N / 8
+         | ((uint32_t(M) >> 4) << 24);      // M / 16
+}
+
+__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                          uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+// Byte offset of 16-byte chunk q of row r inside a 128-byte-swizzled block.
+__device__ __forceinline__ int sw128(int r, int q) { return r * 128 + ((q ^ (r & 7)) << 4); }
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo_elem, float hi_elem) {
+  // element with the lower column index goes to the low half
+  __nv_bfloat162 v = __floats2bfloat162_rn(lo_elem, hi_elem);
+  return *reinterpret_cast<uint32_t*>(&v);
+}
+
+// ------------------------------------------------------------ parameters
+struct TcK {
+  int64_t n;
+  int32_t d;
+  int32_t k;
+  int32_t kp;        // MMA N (multiple of 16, >= k)
+  int32_t acc_cols;  // TMEM columns per accumulator (power of two >= kp)
+  int32_t dz;
+  int32_t cosine;
+  float scale;
+  int32_t nxs;  // raw X stages (SPLIT)
+  int32_t nab;  // A buffers
+  int32_t zst;  // stride of the staged centroids (0: not staged)
+  const float* zf;
+  const float4* cl;
+  const float* gf;
+  const float* cb;
+  float* s_out;
+  float* sa;
+  float* sb;
+  int32_t* skstar;
+  double* partials;
+  uint32_t* status;
+};
+
+struct TcMaps {
+  CUtensorMap x, lab, zh, zl;
+};
+
+// Shared-memory plan (byte offsets from a 1024-aligned base).
+struct TcSmem {
+  int zh, zl, abuf, abuf_stride, lo_off, xs, xs_stride, side, side_stride, cb, gsm, clsm, zsm, zst,
+      bars, total;
+};
+
+// zst: row stride (floats) of the staged centroids, 0 = read them from global memory.
+__host__ __device__ inline TcSmem tc_smem(bool split, int dp, int kp, int nxs, int nab, int zst) {
+  const int natom = dp / 64;
+  TcSmem s;
+  int o = 0;
+  s.zh = o; o += natom * kp * 128;
+  o = (o + 1023) & ~1023;
+  s.zl = o; o += natom * kp * 128;
+  o = (o + 1023) & ~1023;
+  s.abuf = o;
+  s.lo_off = natom * kAtomBytes;
+  s.abuf_stride = natom * kAtomBytes * (split ? 2 : 1);
+  o += nab * s.abuf_stride;
+  s.xs = o;
+  s.xs_stride = split ? (dp / 32) * kAtomBytes + 1024 : 0;  // + labels (512 B), keeps 1024 alignment
+  o += split ? nxs * s.xs_stride : 0;
+  s.side = o;
+  s.side_stride = kTM * 16 + 512;  // xn2, aown, inv, own + labels (bf16 mode)
+  o += nab * s.side_stride;
+  s.cb = o; o += kp * 4 + 16;  // + 4 floats of block-reduction scratch
+  o = (o + 15) & ~15;
+  s.gsm = o; o += dp * 4;
+  s.clsm = o; o += kp * 16;
+  s.zst = zst;
+  s.zsm = o; o += kp * zst * 4;
+  o = (o + 15) & ~15;
+  s.bars = o; o += 8 * (2 * nxs + 4 * nab + 4 + 1) + 16;  // + TMEM base, abort flag
+  s.total = o + 1024;  // slack for aligning the dynamic base to 1024
+  return s;
+}
+
+struct TcBars {
+  uint64_t *xfull, *xempty, *afull, *aempty, *pfull, *accfull, *accempty, *zfull;
+  uint32_t* tmem_base;
+  int* abort_flag;
+};
+
+__device__ inline TcBars tc_bars(unsigned char* base, const TcSmem& L, int nxs, int nab) {
+  TcBars b;
+  uint64_t* p = reinterpret_cast<uint64_t*>(base + L.bars);
+  b.xfull = p; p += nxs;
+  b.xempty = p; p += nxs;
+  b.afull = p; p += nab;
+  b.aempty = p; p += nab;
+  b.pfull = p; p += nab;
+  b.accfull = p; p += 2;
+  b.accempty = p; p += 2;
+  b.zfull = p; p += 1;
+  b.tmem_base = reinterpret_cast<uint32_t*>(p);
+  b.abort_flag = reinterpret_cast<int*>(p) + 1;
+  return b;
+}
+
+// Bounded wait that also notices another role's abort.
+__device__ __forceinline__ bool tc_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
+                                        uint32_t* status) {
+  const uint32_t a = smem_u32(bar);
+  if (mbar_try_wait(a, parity)) return true;
+  const uint64_t t0 = globaltimer_ns();
+  while (!mbar_try_wait(a, parity)) {
+    if (*abort_flag) return false;
+    if (globaltimer_ns() - t0 > kWaitTimeoutNs) {
+      *abort_flag = 1;
+      set_status(status, SIL_ETIMEOUT);
+      return false;
+    }
+  }
+  return true;
+}
+
+template <bool SPLIT, int DP, bool SAVE>
+__global__ void __launch_bounds__(kTcThreads, 1) k_score_tc(TcK a, const __grid_constant__ TcMaps maps) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  // 1024-byte alignment for the swizzled tiles, by offsetting the shared array
+  // itself so that every access below stays a shared-space access
+  unsigned char* base = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+  constexpr int natom = DP / 64;
+  const TcSmem L = tc_smem(SPLIT, DP, a.kp, a.nxs, a.nab, a.zst);
+  const TcBars B = tc_bars(base, L, a.nxs, a.nab);
+  volatile int* abort_flag = B.abort_flag;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t ntiles = cdiv(a.n, kTM);
+  // tiles of this CTA: blockIdx.x, blockIdx.x + gridDim.x, ...
+  const int my_tiles = blockIdx.x < ntiles ? int(cdiv(ntiles - blockIdx.x, gridDim.x)) : 0;
+  float* cbs = reinterpret_cast<float*>(base + L.cb);
+
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < a.nxs; ++i) {
+      mbar_init(&B.xfull[i], 1);
+      mbar_init(&B.xempty[i], kConvWarps);
+    }
+    for (int i = 0; i < a.nab; ++i) {
+      mbar_init(&B.afull[i], SPLIT ? kConvWarps : 1);  // converters, or the TMA transaction
+      mbar_init(&B.aempty[i], 1 + 4);         // MMA commit + 4 epilogue warps
+      mbar_init(&B.pfull[i], kConvWarps);              // BF16 mode: prep warps wrote the row terms
+    }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&B.accfull[i], 1);
+      mbar_init(&B.accempty[i], 4);
+    }
+    mbar_init(B.zfull, 1);
+    *B.abort_flag = 0;
+    fence_mbar_init();
+  }
+  for (int i = threadIdx.x; i < a.kp; i += blockDim.x) cbs[i] = a.cb[i];
+  float* gsm = reinterpret_cast<float*>(base + L.gsm);
+  float4* clsm = reinterpret_cast<float4*>(base + L.clsm);
+  float* zsm = reinterpret_cast<float*>(base + L.zsm);
+  for (int i = threadIdx.x; i < DP; i += blockDim.x) gsm[i] = i < a.dz ? a.gf[i] : 0.f;
+  for (int i = threadIdx.x; i < a.k; i += blockDim.x) clsm[i] = a.cl[i];
+  if (a.zst)
+    for (int i = threadIdx.x; i < a.k * a.zst; i += blockDim.x) {
+      const int kk = i / a.zst, c = i - kk * a.zst;
+      zsm[i] = c < a.dz ? a.zf[int64_t(kk) * a.dz + c] : 0.f;
+    }
+  if (warp == 1) {  // TMEM: two accumulators of acc_cols columns
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(B.tmem_base)),
+                 "r"(2 * a.acc_cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    tc_fence_before();
+  }
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *B.tmem_base;
+
+  if (warp == 0) {
+    // ------------------------------------------------------- TMA producer
+    if (lane == 0) {
+      mbar_arrive_expect_tx(B.zfull, uint32_t(2 * natom * a.kp * 128));
+      for (int at = 0; at < natom; ++at) {
+        tma_load_2d(base + L.zh + at * a.kp * 128, &maps.zh, at * 64, 0, B.zfull);
+        tma_load_2d(base + L.zl + at * a.kp * 128, &maps.zl, at * 64, 0, B.zfull);
+      }
+      int t = 0;
+      for (; t < my_tiles; ++t) {
+        const int32_t row0 = int32_t((blockIdx.x + int64_t(t) * gridDim.x) * kTM);
+        if (SPLIT) {
+          const int j = t % a.nxs;
+          if (!tc_wait(&B.xempty[j], ((t / a.nxs) & 1) ^ 1, abort_flag, a.status)) break;
+          unsigned char* xs = base + L.xs + j * L.xs_stride;
+          mbar_arrive_expect_tx(&B.xfull[j], uint32_t((DP / 32) * kAtomBytes + kTM * 4));
+          for (int s32 = 0; s32 < DP / 32; ++s32)
+            tma_load_2d(xs + s32 * kAtomBytes, &maps.x, s32 * 32, row0, &B.xfull[j]);
+          tma_load_1d(xs + (DP / 32) * kAtomBytes, &maps.lab, row0, &B.xfull[j]);
+        } else {
+          const int i = t % a.nab;
+          if (!tc_wait(&B.aempty[i], ((t / a.nab) & 1) ^ 1, abort_flag, a.status)) break;
+          unsigned char* ab = base + L.abuf + i * L.abuf_stride;
+          mbar_arrive_expect_tx(&B.afull[i], uint32_t(natom * kAtomBytes + kTM * 4));
+          for (int at = 0; at < natom; ++at)
+            tma_load_2d(ab + at * kAtomBytes, &maps.x, at * 64, row0, &B.afull[i]);
+          tma_load_1d(base + L.side + i * L.side_stride + kTM * 16, &maps.lab, row0, &B.afull[i]);
+        }
+      }
+      if (*abort_flag) {
+        // wait (bounded) for every copy this thread issued and nobody consumed
+        const int ring = SPLIT ? a.nxs : a.nab;
+        uint64_t* full = SPLIT ? B.xfull : B.afull;
+        const int first = t - ring > 0 ? t - ring : 0;
+        for (int u = first; u < t; ++u) mbar_wait(&full[u % ring], uint32_t((u / ring) & 1));
+        mbar_wait(B.zfull, 0);
+      }
+    }
+  } else if (warp == 1) {
+    // --------------------------------------------------------- MMA issuer
+    if (lane == 0) {
+      const uint32_t idesc = umma_idesc_bf16(kTM, a.kp);
+      int t = 0;
+      bool ok = tc_wait(B.zfull, 0, abort_flag, a.status);
+      for (; ok && t < my_tiles; ++t) {
+        const int i = t % a.nab, bsel = t & 1;
+        if (!tc_wait(&B.afull[i], (t / a.nab) & 1, abort_flag, a.status)) break;
+        if (!tc_wait(&B.accempty[bsel], ((t >> 1) & 1) ^ 1, abort_flag, a.status)) break;
+        tc_fence_after();
+        const uint32_t d_tmem = tmem + uint32_t(bsel * a.acc_cols);
+        const uint32_t ahi = smem_u32(base + L.abuf + i * L.abuf_stride);
+        const uint32_t alo = ahi + uint32_t(L.lo_off);
+        const uint32_t zh = smem_u32(base + L.zh), zl = smem_u32(base + L.zl);
+#pragma unroll
+        for (int at = 0; at < natom; ++at) {
+#pragma unroll
+          for (int ks = 0; ks < 4; ++ks) {
+            const uint32_t ao = uint32_t(at * kAtomBytes + ks * 32);
+            const uint32_t bo = uint32_t(at * a.kp * 128 + ks * 32);
+            umma_bf16(d_tmem, umma_desc_sw128(ahi + ao), umma_desc_sw128(zh + bo), idesc,
+                      (at | ks) != 0);
+            umma_bf16(d_tmem, umma_desc_sw128(ahi + ao), umma_desc_sw128(zl + bo), idesc, 1);
+            if (SPLIT) umma_bf16(d_tmem, umma_desc_sw128(alo + ao), umma_desc_sw128(zh + bo), idesc, 1);
+          }
+        }
+        umma_commit(&B.accfull[bsel]);
+        umma_commit(&B.aempty[i]);
+      }
+      if (*abort_flag && t > 0) {
+        // the last committed accumulator must be complete before TMEM is freed
+        const int u = t - 1;
+        mbar_wait(&B.accfull[u & 1], uint32_t((u >> 1) & 1));
+      }
+    }
+  } else if (warp < kEpiWarp0) {
+    // ------------------------------------------------ converter warps 2..9
+    // lanes 0-15 and 16-31 of a warp hold the two halves of the same 16 rows
+    constexpr int HP = DP / 2;  // columns per half
+    const int h = lane >> 4;
+    const int r = (warp - 2) * 16 + (lane & 15);  // tile row of this thread
+
+    for (int t = 0; t < my_tiles; ++t) {
+      const int i = t % a.nab;
+      const int64_t row = (blockIdx.x + int64_t(t) * gridDim.x) * kTM + r;
+      unsigned char* ab = base + L.abuf + i * L.abuf_stride;
+      float* side = reinterpret_cast<float*>(base + L.side + i * L.side_stride);
+      float x[HP];
+      int own;
+      if (SPLIT) {
+        const int j = t % a.nxs;
+        if (!tc_wait(&B.xfull[j], (t / a.nxs) & 1, abort_flag, a.status)) break;
+        if (!tc_wait(&B.aempty[i], ((t / a.nab) & 1) ^ 1, abort_flag, a.status)) break;
+        const unsigned char* xs = base + L.xs + j * L.xs_stride;
+#pragma unroll
+        for (int c4 = 0; c4 < HP / 4; ++c4) {
+          const int col = h * HP + 4 * c4;
+          const float4 v =
+              *reinterpret_cast<const float4*>(xs + (col / 32) * kAtomBytes + sw128(r, (col % 32) / 4));
+          x[4 * c4 + 0] = v.x;
+          x[4 * c4 + 1] = v.y;
+          x[4 * c4 + 2] = v.z;
+          x[4 * c4 + 3] = v.w;
+        }
+        own = reinterpret_cast<const int32_t*>(xs + (DP / 32) * kAtomBytes)[r];
+      } else {
+        if (!tc_wait(&B.afull[i], (t / a.nab) & 1, abort_flag, a.status)) break;
+#pragma unroll
+        for (int c8 = 0; c8 < HP / 8; ++c8) {
+          const int col = h * HP + 8 * c8;
+          const uint4 u = *reinterpret_cast<const uint4*>(ab + (col / 64) * kAtomBytes + sw128(r, (col % 64) / 8));
+          const uint32_t w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&w[e]));
+            x[8 * c8 + 2 * e] = f.x;
+            x[8 * c8 + 2 * e + 1] = f.y;
+          }
+        }
+        own = reinterpret_cast<const int32_t*>(reinterpret_cast<unsigned char*>(side) + kTM * 16)[r];
+      }
+      bool valid = row < a.n;
+      if (valid && (own < 0 || own >= a.k)) {
+        if (h == 0) set_status(a.status, SIL_ELABEL);
+        valid = false;
+      }
+      float inv = 1.f;
+      if (a.cosine) {
+        float2 ss2 = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int c = 0; c < HP; c += 2) {
+          const float2 xv = make_float2(x[c], x[c + 1]);
+          ss2 = __ffma2_rn(xv, xv, ss2);
+        }
+        float ss = ss2.x + ss2.y;
+        ss += __shfl_xor_sync(0xffffffffu, ss, 16);
+        if (valid && !(ss > 0.f)) {
+          if (h == 0) set_status(a.status, SIL_EZERONORM);
+          valid = false;
+        }
+        inv = ss > 0.f ? rsqrtf(ss) : 0.f;
+      }
+      // ||x'||^2 and the exact own-cluster term (x' = x inv - g), half a row
+      // each, two columns per packed FP32x2 instruction
+      float2 xn2 = make_float2(0.f, 0.f), ae = xn2;
+      const float2 inv2 = make_float2(inv, inv);
+      const int ownc = valid ? own : 0;
+#pragma unroll
+      for (int c4 = 0; c4 < HP / 4; ++c4) {
+        const int col = h * HP + 4 * c4;
+        const float4 g = *reinterpret_cast<const float4*>(gsm + col);
+        float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (col < a.dz) {
+          if (a.zst)  // staged centroids (uniform branch)
+            z = *reinterpret_cast<const float4*>(zsm + ownc * a.zst + col);
+          else
+            z = __ldg(reinterpret_cast<const float4*>(a.zf + int64_t(ownc) * a.dz + col));
+        }
+        const float2 xa = make_float2(x[4 * c4], x[4 * c4 + 1]), xb = make_float2(x[4 * c4 + 2], x[4 * c4 + 3]);
+        const float2 ca = __ffma2_rn(xa, inv2, make_float2(-g.x, -g.y));
+        const float2 cb = __ffma2_rn(xb, inv2, make_float2(-g.z, -g.w));
+        xn2 = __ffma2_rn(ca, ca, xn2);
+        xn2 = __ffma2_rn(cb, cb, xn2);
+        const float2 da = __fadd2_rn(ca, make_float2(-z.x, -z.y));
+        const float2 db = __fadd2_rn(cb, make_float2(-z.z, -z.w));
+        ae = __ffma2_rn(da, da, ae);
+        ae = __ffma2_rn(db, db, ae);
+      }
+      float xn2s = xn2.x + xn2.y, aes = ae.x + ae.y;
+      xn2s += __shfl_xor_sync(0xffffffffu, xn2s, 16);
+      aes += __shfl_xor_sync(0xffffffffu, aes, 16);
+      if (SPLIT) {
+        // hi/lo BF16 split of this half row into the swizzled A buffer
+#pragma unroll
+        for (int c8 = 0; c8 < HP / 8; ++c8) {
+          const int col = h * HP + 8 * c8;
+          uint32_t hw[4], lw[4];
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const float2 xv = make_float2(x[8 * c8 + 2 * e], x[8 * c8 + 2 * e + 1]);
+            const __nv_bfloat162 hv = __floats2bfloat162_rn(xv.x, xv.y);
+            const float2 hf = __bfloat1622float2(hv);
+            const float2 rem = __fadd2_rn(xv, make_float2(-hf.x, -hf.y));
+            hw[e] = *reinterpret_cast<const uint32_t*>(&hv);
+            lw[e] = pack_bf16x2(rem.x, rem.y);
+          }
+          const int off = (col / 64) * kAtomBytes + sw128(r, (col % 64) / 8);
+          *reinterpret_cast<uint4*>(ab + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+          *reinterpret_cast<uint4*>(ab + L.lo_off + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+        }
+        fence_proxy_async_smem();
+      }
+      if (h == 0) {
+        float aown = 0.f;
+        if (valid) {
+          const float4 co = clsm[own];
+          aown = fmaf(co.y, aes, co.z);
+          if (co.w < 1.5f) own = -2 - own;  // singleton: s_i = 0, b_i still reported
+        }
+        side[r] = xn2s;
+        side[kTM + r] = aown;
+        side[2 * kTM + r] = inv;
+        reinterpret_cast<int*>(side)[3 * kTM + r] = valid ? own : -1;
+      }
+      __syncwarp();
+      if (lane == 0) {
+        if (SPLIT) {
+          mbar_arrive(&B.afull[i]);
+          mbar_arrive(&B.xempty[t % a.nxs]);
+        } else {
+          mbar_arrive(&B.pfull[i]);
+        }
+      }
+    }
+  } else {
+    // ---------------------------------------------- epilogue warps 10..13
+    const int q = warp & 3;          // TMEM lane quarter this warp may access
+    const int r = q * 32 + lane;     // tile row = TMEM lane
+    float tsum = 0.f;
+    for (int t = 0; t < my_tiles; ++t) {
+      const int i = t % a.nab, bsel = t & 1;
+      if (!tc_wait(&B.accfull[bsel], (t >> 1) & 1, abort_flag, a.status)) break;
+      if (!tc_wait(SPLIT ? &B.afull[i] : &B.pfull[i], (t / a.nab) & 1, abort_flag, a.status)) break;
+      tc_fence_after();
+      const float* side = reinterpret_cast<const float*>(base + L.side + i * L.side_stride);
+      const int own_raw = reinterpret_cast<const int*>(side)[3 * kTM + r];
+      const int own = own_raw >= 0 ? own_raw : (own_raw <= -2 ? -2 - own_raw : -1);
+      const float sc = -2.f * side[2 * kTM + r];
+      float best = INFINITY;
+      int kb = -1;
+      const uint32_t tbase = tmem + uint32_t(bsel * a.acc_cols) + (uint32_t(q * 32) << 16);
+      const float2 sc2 = make_float2(sc, sc);
+      for (int c0 = 0; c0 < a.kp; c0 += 16) {
+        float v[16];
+        tmem_ld16(tbase + uint32_t(c0), v);
+        const float4* cb4 = reinterpret_cast<const float4*>(cbs + c0);
+#pragma unroll
+        for (int q4 = 0; q4 < 4; ++q4) {
+          const float4 cq = cb4[q4];
+          const float2 va = __ffma2_rn(sc2, make_float2(v[4 * q4], v[4 * q4 + 1]), make_float2(cq.x, cq.y));
+          const float2 vb = __ffma2_rn(sc2, make_float2(v[4 * q4 + 2], v[4 * q4 + 3]), make_float2(cq.z, cq.w));
+          const float vals[4] = {va.x, va.y, vb.x, vb.y};
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const int kk = c0 + 4 * q4 + e;
+            if (SAVE) {
+              if (kk != own && vals[e] < best) {
+                best = vals[e];
+                kb = kk;
+              }
+            } else if (kk != own) {
+              best = fminf(best, vals[e]);
+            }
+          }
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&B.accempty[bsel]);
+      const int64_t row = (blockIdx.x + int64_t(t) * gridDim.x) * kTM + r;
+      if (row < a.n) {
+        float av = 0.f, bv = INFINITY, sv = 0.f;
+        if (own >= 0) {
+          const bool has_b = best < INFINITY;
+          av = fmaxf(0.f, a.scale * side[kTM + r]);
+          bv = has_b ? fmaxf(0.f, a.scale * (side[r] + best)) : INFINITY;
+          if (own_raw >= 0 && has_b) {
+            const float m = fmaxf(av, bv);
+            sv = m > 0.f ? (av <= bv ? 1.f - av / bv : bv / av - 1.f) : 0.f;
+          }
+          if (!SAVE) kb = has_b ? 0 : -1;
+        } else {
+          kb = -1;
+        }
+        if (a.s_out) a.s_out[row] = sv;
+        if (SAVE) {
+          a.sa[row] = av;
+          a.sb[row] = bv;
+          a.skstar[row] = kb;
+        }
+        tsum += sv;
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&B.aempty[i]);
+    }
+    // block partial over the 128 epilogue threads
+    for (int o = 16; o > 0; o >>= 1) tsum += __shfl_xor_sync(0xffffffffu, tsum, o);
+    float* red = cbs + a.kp;  // 4 floats of scratch right after cb (within the plan's padding)
+    if (lane == 0) red[q] = tsum;
+    asm volatile("bar.sync 1, 128;" ::: "memory");
+    if (warp == kEpiWarp0 && lane == 0) a.partials[blockIdx.x] = double(red[0]) + red[1] + red[2] + red[3];
+  }
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * a.acc_cols)
+                 : "memory");
+  }
+}
+
+// Split centroids and per-cluster constants for the tensor-core kernel:
+//   zh/zl (bf16 [kp][dp], zero padded) with zh + zl ~ mu'_k to ~16 bits,
+//   cb[k] = bias_k + 2 g.mu'_k (+inf for empty clusters and padding).
+__global__ void k_tc_pack(const float* zf, const float4* cl, const double* g, int32_t k, int32_t d,
+                          int32_t dz, int32_t kp, int32_t dp, __nv_bfloat16* zh, __nv_bfloat16* zl,
+                          float* cb) {
+  __shared__ double red[32];
+  const int kk = blockIdx.x;
+  double dot = 0.0;
+  for (int c = threadIdx.x; c < dp; c += blockDim.x) {
+    const float z = (kk < k && c < dz) ? zf[int64_t(kk) * dz + c] : 0.f;
+    const __nv_bfloat16 h = __float2bfloat16_rn(z);
+    zh[int64_t(kk) * dp + c] = h;
+    zl[int64_t(kk) * dp + c] = __float2bfloat16_rn(z - __bfloat162float(h));
+    if (c < d) dot += g[c] * double(z);
+  }
+  for (int o = 16; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = dot;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < int(blockDim.x >> 5); ++w) t += red[w];
+    float v = INFINITY;
+    if (kk < k && cl[kk].w > 0.5f) v = float(double(cl[kk].x) + 2.0 * t);
+    cb[kk] = v;
+  }
+}
+
+int pow2_at_least(int v) {
+  int p = 32;
+  while (p < v) p <<= 1;
+  return p;
+}
+
+}  // namespace
+
+bool tc_eligible(int32_t dtype, int64_t n, int32_t d, int64_t ldx, int32_t k, const void* X,
+                 const int32_t* labels) {
+  const char* e = getenv("SIL_TC_DISABLE");
+  if (e && e[0] == '1') return false;
+  if (dtype != SIL_F32 && dtype != SIL_BF16) return false;
+  if (n <= 0 || n >= (int64_t(1) << 31) || k > 256 || d > 128) return false;
+  const int esz = dtype == SIL_F32 ? 4 : 2;
+  if (d < (dtype == SIL_F32 ? 32 : 64)) return false;  // the TMA box must fit inside a row
+  if (reinterpret_cast<uintptr_t>(X) % 16 || reinterpret_cast<uintptr_t>(labels) % 16) return false;
+  if ((ldx * esz) % 16) return false;
+  // the centroids, one A buffer and (FP32) one raw X stage must fit in shared memory
+  const int dp = int(round_up(d, 64)), kp = int(round_up(std::max(k, 16), 16));
+  if (tc_smem(dtype == SIL_F32, dp, kp, 1, 1, 0).total > 227 * 1024) return false;
+  int dev = 0, major = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return false;
+  if (cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev) != cudaSuccess) return false;
+  return major == 10;
+}
+
+size_t tc_pack_bytes(int32_t k, int32_t d) {
+  const size_t kp = size_t(round_up(std::max(k, 16), 16)), dp = size_t(round_up(d, 64));
+  return 2 * kp * dp * 2 + kp * 4 + 256;
+}
+
+cudaError_t launch_score_tc(const ScoreLaunch& s, const double* g, void* pack, uint32_t* status) {
+  const int dp = int(round_up(s.d, 64));
+  const int kp = int(round_up(std::max(s.k, 16), 16));
+  const int dz = int(round_up(s.d, 4));
+  __nv_bfloat16* zh = static_cast<__nv_bfloat16*>(pack);
+  __nv_bfloat16* zl = zh + size_t(kp) * dp;
+  float* cb = reinterpret_cast<float*>(zl + size_t(kp) * dp);
+  k_tc_pack<<<kp, 128, 0, s.stream>>>(s.zf, s.cl, g, s.k, s.d, dz, kp, dp, zh, zl, cb);
+  cudaError_t err = cudaGetLastError();
+  if (err != cudaSuccess) return err;
+
+  const bool split = s.dtype == SIL_F32;
+  TcMaps maps{};
+  const int esz = split ? 4 : 2;
+  const CUtensorMapDataType xt = split ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+  const uint32_t box_inner = split ? 32 : 64;
+  if (!encode_tmap_2d(&maps.x, s.X, xt, esz, uint64_t(s.d), uint64_t(s.n), uint64_t(s.ldx) * esz, box_inner,
+                      kTM, CU_TENSOR_MAP_SWIZZLE_128B))
+    return cudaErrorInvalidValue;
+  if (!encode_tmap_1d(&maps.lab, s.labels, CU_TENSOR_MAP_DATA_TYPE_INT32, uint64_t(s.n), kTM))
+    return cudaErrorInvalidValue;
+  if (!encode_tmap_2d(&maps.zh, zh, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, uint64_t(dp), uint64_t(kp),
+                      uint64_t(dp) * 2, 64, uint32_t(kp), CU_TENSOR_MAP_SWIZZLE_128B) ||
+      !encode_tmap_2d(&maps.zl, zl, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, uint64_t(dp), uint64_t(kp),
+                      uint64_t(dp) * 2, 64, uint32_t(kp), CU_TENSOR_MAP_SWIZZLE_128B))
+    return cudaErrorInvalidValue;
+
+  TcK k{};
+  k.n = s.n;
+  k.d = s.d;
+  k.k = s.k;
+  k.kp = kp;
+  k.acc_cols = pow2_at_least(kp);
+  k.dz = dz;
+  k.cosine = s.dist == SIL_COSINE;
+  k.scale = s.dist == SIL_COSINE ? 0.5f : 1.f;
+  k.zf = s.zf;
+  k.cl = s.cl;
+  k.gf = s.gf;
+  k.cb = cb;
+  k.s_out = s.s_out;
+  k.sa = s.sa;
+  k.sb = s.sb;
+  k.skstar = s.skstar;
+  k.partials = s.partials;
+  k.status = status;
+  // deepest rings that fit: A buffers first (2), then raw X stages
+  const int budget = 227 * 1024;
+  int nab = 2, nxs = split ? 3 : 0;
+  if (!split) nab = 4;
+  // stage the centroids (padded rows: fewer bank conflicts) when 2 A buffers + 2 stages still fit
+  int zst = dz + 4;
+  if (tc_smem(split, dp, kp, split ? 2 : 1, 2, zst).total > budget) zst = 0;
+  while (tc_smem(split, dp, kp, std::max(nxs, 1), nab, zst).total > budget) {
+    if (split && nxs > 2) --nxs;
+    else if (nab > 2) --nab;
+    else if (split && nxs > 1) --nxs;
+    else if (nab > 1) --nab;
+    else return cudaErrorInvalidValue;
+  }
+  k.nxs = std::max(nxs, 1);
+  k.nab = nab;
+  k.zst = zst;
+  const int smem = tc_smem(split, dp, kp, k.nxs, nab, zst).total;
+  const int64_t ntiles = cdiv(s.n, kTM);
+  const int grid = int(std::min<int64_t>(ntiles, kNumSMs));
+  const bool save = s.sa != nullptr;
+  auto launch = [&](auto fn) {
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    fn<<<grid, kTcThreads, smem, s.stream>>>(k, maps);
+    return cudaGetLastError();
+  };
+  *s.n_partials = grid;
+  if (split) {
+    if (dp == 64) return save ? launch(k_score_tc<true, 64, true>) : launch(k_score_tc<true, 64, false>);
+    return save ? launch(k_score_tc<true, 128, true>) : launch(k_score_tc<true, 128, false>);
+  }
+  if (dp == 64) return save ? launch(k_score_tc<false, 64, true>) : launch(k_score_tc<false, 64, false>);
+  return save ? launch(k_score_tc<false, 128, true>) : launch(k_score_tc<false, 128, false>);
+}
+
+}  // namespace sil

@@ -198,6 +198,12 @@ struct ScoreLaunch {
   cudaStream_t stream;
 };
 cudaError_t launch_score_simt(ScoreLaunch& s);
+// Tensor-core pass 2 (tcgen05): eligibility, bytes of its packed centroids
+// (inside the workspace) and the launch (status = workspace status word).
+bool tc_eligible(int32_t dtype, int64_t n, int32_t d, int64_t ldx, int32_t k, const void* X,
+                 const int32_t* labels);
+size_t tc_pack_bytes(int32_t k, int32_t d);
+cudaError_t launch_score_tc(const ScoreLaunch& s, const double* g, void* pack, uint32_t* status);
 // S = sum(partials)/n, NaN when the workspace status word is non-zero; the
 // word is OR-ed into user_status.
 cudaError_t launch_reduce_S(const double* partials, int32_t np, int64_t n, const uint32_t* ws_status,

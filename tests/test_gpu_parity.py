@@ -199,3 +199,23 @@ def test_batched_matches_oracle_per_labeling(metric):
     for b, k in enumerate(ks):
         ref = oracle.linear(X.astype(np.float64), labs[b], k, metric)
         assert abs(S[b] - ref["S"]) <= TOL_S, (b, S[b], ref["S"])
+
+
+# ------------------------------------------- pass-1 kernel variants agree
+@pytest.mark.parametrize("metric", METRICS)
+@pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16])
+@pytest.mark.parametrize("N,D,K", [(100003, 64, 100), (7777, 24, 6), (50001, 128, 1000), (3001, 256, 40)])
+def test_tma_and_generic_pass1_agree(metric, dtype, N, D, K, monkeypatch):
+    X, lab = case(600 + N + D, N, D, K, metric)
+    Xt, lt = to_dev(X, lab, dtype)
+    fast = sil.aggregate(Xt, lt, K, metric)
+    monkeypatch.setenv("SIL_AGG_GENERIC", "1")
+    slow = sil.aggregate(Xt, lt, K, metric)
+    torch.cuda.synchronize()
+    assert torch.equal(fast[0], slow[0])
+    torch.testing.assert_close(fast[1], slow[1], rtol=1e-6, atol=1e-6 * float(slow[1].abs().max()))
+    torch.testing.assert_close(fast[2], slow[2], rtol=1e-6, atol=0.0)
+    rc, r1, r2 = oracle.aggregate(dequant(Xt), lab, K, metric)
+    np.testing.assert_array_equal(fast[0].cpu().numpy(), rc)
+    np.testing.assert_allclose(fast[1].cpu().numpy(), r1, rtol=1e-6, atol=1e-6 * np.abs(r1).max())
+
