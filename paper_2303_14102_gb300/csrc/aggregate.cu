@@ -143,8 +143,11 @@ struct AggMaps {
 
 // Byte offsets of the per-CTA shared state (the part both kernels share).
 struct AggSmem {
-  int acc, acc2, macc, mint, cnt, slot, ebk, epos, ew, order, nel, bstart, bsize, inv, wtot, nne, total;
+  int acc, acc2, macc, mint, cnt, slot, ebk, epos, ew, order, nel, bstart, bsize, segq, inv, wtot, nne,
+      total;
 };
+
+constexpr int kSeg = 8;  // rows per accumulation segment
 
 __host__ __device__ inline AggSmem agg_smem(int dsp, int kbs, bool dual, bool weighted) {
   const int R = kAggRows, E = dual ? 2 * R : R, c4 = dsp / 4;
@@ -163,6 +166,7 @@ __host__ __device__ inline AggSmem agg_smem(int dsp, int kbs, bool dual, bool we
   s.nel = o; o += E * 4;
   s.bstart = o; o += (E + 1) * 4;
   s.bsize = o; o += E * 4;
+  s.segq = o; o += (E + E / kSeg + 1) * 4;
   s.inv = o; o += R * 4;
   s.wtot = o; o += 32 * 4;
   s.nne = o; o += 16;
@@ -185,6 +189,7 @@ struct AggState {
   int* nel;
   int* bstart;
   int* bsize;
+  int* segq;  // segment -> (bucket position << 8 | segment index)
   float* inv;
   int* wtot;
   int* nne;  // [0] = non-empty bucket count (being built), [1] = abort flag, [2] = count of this tile
@@ -206,6 +211,7 @@ __device__ inline AggState agg_state(unsigned char* smem, const AggSmem& L) {
   S.nel = reinterpret_cast<int*>(smem + L.nel);
   S.bstart = reinterpret_cast<int*>(smem + L.bstart);
   S.bsize = reinterpret_cast<int*>(smem + L.bsize);
+  S.segq = reinterpret_cast<int*>(smem + L.segq);
   S.inv = reinterpret_cast<float*>(smem + L.inv);
   S.wtot = reinterpret_cast<int*>(smem + L.wtot);
   S.nne = reinterpret_cast<int*>(smem + L.nne);
@@ -313,8 +319,8 @@ struct SrcTma {
 // Counters are reset inside; the caller syncs before the next tile (and
 // before its staging buffer is refilled).
 template <bool DUAL, bool WEIGHTED, class Src>
-__device__ void agg_tile(const AggK& a, const AggState& S, const AggItem& it, const Src& src,
-                         int rows, int64_t r0) {
+__device__ int agg_sort(const AggK& a, const AggState& S, const AggItem& it, const Src& src,
+                        int rows, int64_t r0) {
   constexpr int R = kAggRows, T = kAggThreads, E = DUAL ? 2 * R : R;
   const int tid = threadIdx.x;
   const bool in_cta_norm = a.cosine && a.invnorm == nullptr;  // full rows are in this tile
@@ -374,46 +380,60 @@ __device__ void agg_tile(const AggK& a, const AggState& S, const AggItem& it, co
     }
   }
   __syncthreads();
-  // (c) warp 0: exclusive scan of the bucket sizes over the non-empty list;
-  // it also resets the counters, so no barrier is needed after the tile
-  if (tid < 32) {
-    const int lane = tid;
-    const int m = S.nne[0];
-    const int per = (m + 31) / 32;  // consecutive entries per lane
-    const int q0 = lane * per, q1 = min(m, q0 + per);
-    int local = 0;
-    for (int q = q0; q < q1; ++q) local += S.cnt[S.nel[q]];
-    int incl = local;
+  // (c) block-wide exclusive scan over the non-empty buckets (one thread per
+  // bucket, m <= E <= T), of the packed pair (rows << 16 | segments of kSeg
+  // rows); it also writes the segment -> bucket table and resets the counters
+  const int m = S.nne[0];
+  {
+    const int warp = tid >> 5, lane = tid & 31;
+    const int c = tid < m ? S.cnt[S.nel[tid]] : 0;
+    const int v = (c << 16) | ((c + kSeg - 1) / kSeg);
+    int incl = v;
     for (int o = 1; o < 32; o <<= 1) {
       const int t = __shfl_up_sync(0xffffffffu, incl, o);
       if (lane >= o) incl += t;
     }
-    int run = incl - local;
-    for (int q = q0; q < q1; ++q) {
-      const int lb = S.nel[q];
-      const int c = S.cnt[lb];
-      S.bstart[q] = run;
-      S.bsize[q] = c;
-      run += c;
+    if (lane == 31) S.wtot[warp] = incl;
+    __syncthreads();
+    int off = 0;
+    for (int w = 0; w < warp; ++w) off += S.wtot[w];
+    const int ex = off + incl - v;
+    if (tid < m) {
+      const int lb = S.nel[tid];
+      S.bstart[tid] = ex >> 16;
+      S.bsize[tid] = c;
       S.cnt[lb] = 0;
+      const int s0 = ex & 0xFFFF, ns = v & 0xFFFF;
+      for (int sg = 0; sg < ns; ++sg) S.segq[s0 + sg] = (tid << 8) | sg;
     }
-    __syncwarp();
-    if (lane == 0) {
-      S.nne[2] = m;
-      S.nne[0] = 0;
-    }
+    if (tid == T - 1) S.nne[2] = (off + incl) & 0xFFFF;  // total number of segments
   }
   __syncthreads();
-  const int m = S.nne[2];
+  if (tid == 0) S.nne[0] = 0;  // everybody has read m
   // (d) scatter entries into bucket order
   for (int e = tid; e < E; e += T) {
     const int lb = S.ebk[e];
     if (lb >= 0) S.order[S.bstart[S.slot[lb]] + S.epos[e]] = e;
   }
   __syncthreads();
-  // (e) one thread per (non-empty bucket, 4-column chunk of this slice)
-  for (int p = tid; p < m * it.c4e; p += T) {
-    const int q = p / it.c4e, c = p - q * it.c4e;
+  return S.nne[2];  // segments of at most kSeg rows over the non-empty buckets
+}
+
+// Accumulation into the per-CTA shared accumulators: one thread per
+// (non-empty bucket, 4-column chunk of this slice).
+template <bool DUAL, bool WEIGHTED, class Src>
+__device__ void agg_tile(const AggK& a, const AggState& S, const AggItem& it, const Src& src,
+                         int rows, int64_t r0) {
+  constexpr int R = kAggRows, T = kAggThreads;
+  const int tid = threadIdx.x;
+  const int nseg = agg_sort<DUAL, WEIGHTED>(a, S, it, src, rows, r0);
+  // one thread per (segment of at most kSeg rows of one bucket, 4-column
+  // chunk): short independent chains; the segments of a bucket longer than
+  // kSeg rows meet in shared memory through float atomics
+  for (int p = tid; p < nseg * it.c4e; p += T) {
+    const int sidx = p / it.c4e, c = p - sidx * it.c4e;
+    const int sq_ = S.segq[sidx];
+    const int q = sq_ >> 8, sg = sq_ & 255;
     const int lb = S.nel[q];
     const int bg = it.kb0 + lb;
     const int kc = bg < a.k ? bg : bg - a.k;  // cluster whose reference point shifts this bucket
@@ -421,10 +441,16 @@ __device__ void agg_tile(const AggK& a, const AggState& S, const AggItem& it, co
         *reinterpret_cast<const float4*>(a.rs + int64_t(kc) * a.dz + it.col0 + 4 * c);
     float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
     float sq = 0.f, wsum = 0.f;
-    const int jb = S.bstart[q], je = jb + S.bsize[q];
-#pragma unroll 4
-    for (int j = jb; j < je; ++j) {
-      const int e = S.order[j];
+    const int size = S.bsize[q];
+    const int jb = S.bstart[q] + sg * kSeg;
+    const int je = min(S.bstart[q] + size, jb + kSeg);
+    int eidx[kSeg];
+#pragma unroll
+    for (int u = 0; u < kSeg; ++u) eidx[u] = S.order[min(jb + u, je - 1)];
+#pragma unroll
+    for (int u = 0; u < kSeg; ++u) {
+      if (jb + u >= je) break;
+      const int e = eidx[u];
       const int r = DUAL ? (e < R ? e : e - R) : e;
       const float4 x = src.chunk(r, c);
       const float sc = a.cosine ? S.inv[r] : 1.f;
@@ -442,16 +468,28 @@ __device__ void agg_tile(const AggK& a, const AggState& S, const AggItem& it, co
       }
       s.x += v.x; s.y += v.y; s.z += v.z; s.w += v.w;
     }
-    float4 t = S.acc4[lb * it.c4 + c];
-    t.x += s.x; t.y += s.y; t.z += s.z; t.w += s.w;
-    S.acc4[lb * it.c4 + c] = t;
-    if (!WEIGHTED) S.acc2[lb * it.c4 + c] += sq;
-    if (c == 0) {
-      S.mint[lb] += je - jb;
-      if (WEIGHTED) S.macc[lb] += wsum;
+    float* accp = S.acc + (lb * it.c4 + c) * 4;
+    if (size <= kSeg) {  // the only segment of its bucket: plain read-modify-write
+      float4 t = S.acc4[lb * it.c4 + c];
+      t.x += s.x; t.y += s.y; t.z += s.z; t.w += s.w;
+      S.acc4[lb * it.c4 + c] = t;
+      if (!WEIGHTED) S.acc2[lb * it.c4 + c] += sq;
+      if (c == 0) {
+        S.mint[lb] += size;
+        if (WEIGHTED) S.macc[lb] += wsum;
+      }
+    } else {
+      atomicAdd(accp + 0, s.x);
+      atomicAdd(accp + 1, s.y);
+      atomicAdd(accp + 2, s.z);
+      atomicAdd(accp + 3, s.w);
+      if (!WEIGHTED) atomicAdd(S.acc2 + lb * it.c4 + c, sq);
+      if (c == 0) {
+        if (sg == 0) S.mint[lb] += size;
+        if (WEIGHTED) atomicAdd(S.macc + lb, wsum);
+      }
     }
   }
-  // the caller's barrier after this tile orders (e) before the next tile's (b)
 }
 
 // Un-shift in FP64 and add the CTA's sums into the outputs.
