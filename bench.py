@@ -46,11 +46,6 @@ def peaks():
             "sm_max_mhz": 2070.0, "source": "fallback"}
 
 
-# FP32 FFMA peak of a GB300: 152 SMs x 128 FP32 lanes x 2 flop x SM clock.
-def ffma_peak_tflops(sm_mhz: float) -> float:
-    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
-
-
 class ClockSampler:
     """nvidia-smi samples (every 200 ms) while the timed region runs."""
 
@@ -196,7 +191,7 @@ def timed(fn, steps, stream):
     return ev0.elapsed_time(ev1) / 1e3
 
 
-def variant_lines(dev, steps, budget_s):
+def variant_lines(dev, steps, budget_s, pk_sustained):
     """Secondary measurements, each bounded in time."""
     import torch
     from paper_2303_14102_gb300 import sil, synth
@@ -207,6 +202,53 @@ def variant_lines(dev, steps, budget_s):
     def left():
         return budget_s - (time.time() - t_start)
 
+    # precision workload (N=1e8, D=128, K=1000, centres at radius 1e3): the
+    # same blobs stored in BF16, FP8-E4M3 with column scales, and FP32
+    if left() > 0:
+        w = synth.workload_precision(device=dev)
+        lab, K = w.labels, w.K
+        N = lab.shape[0]
+        forms = {"bf16": (synth.to_bf16(w.X), None)}
+        q, cs = synth.to_fp8_e4m3(w.X)
+        forms["fp8_e4m3"] = (q, cs)
+        forms["fp32"] = (w.X, None)
+        del w
+        torch.cuda.empty_cache()
+        stream = torch.cuda.current_stream()
+        res = {}
+        for name, (Xs, sc) in forms.items():
+            if left() <= 0:
+                break
+            st = sil.new_status(dev)
+            agg = sil.aggregate(Xs, lab, K, col_scale=sc, status=st)
+            sil.score(Xs, lab, K, agg, col_scale=sc, status=st)
+            n = max(1, min(steps, 3))
+            t1 = timed(lambda: sil.aggregate(Xs, lab, K, col_scale=sc, out=agg, status=st), n, stream) / n
+            t2 = timed(lambda: sil.score(Xs, lab, K, agg, col_scale=sc, status=st), n, stream) / n
+            r = sil.score(Xs, lab, K, agg, col_scale=sc, status=st)
+            torch.cuda.synchronize()
+            sil.check_status(st, "precision " + name)
+            plan = sil.tensor_plan(Xs.dtype, Xs.shape[1], K)
+            entry = {"points_per_s": N / (t1 + t2), "ms": (t1 + t2) * 1e3, "pass1_ms": t1 * 1e3,
+                     "pass2_ms": t2 * 1e3, "S": float(r.S.item()),
+                     "pass1_hbm_gbs": Xs.numel() * Xs.element_size() / t1 / 1e9 + N * 4 / t1 / 1e9,
+                     "pass2_useful_tflops": 2.0 * N * K * Xs.shape[1] / t2 / 1e12}
+            if plan is not None:
+                bk, nb = plan
+                mmas = 3 if Xs.dtype == torch.float32 else 2  # BF16 hi/lo products per k-step
+                mma_flops = 2.0 * N * bk * nb * 128 * mmas
+                entry.update({"tensor_plan": {"block_k": bk, "blocks": nb, "mma_per_kstep": mmas},
+                              "pass2_mma_tflops": mma_flops / t2 / 1e12,
+                              "pass2_tensor_frac_of_measured_bf16": mma_flops / t2 / 1e12
+                              / pk_sustained})
+            res[name] = entry
+        if "fp32" in res:
+            for name in ("bf16", "fp8_e4m3"):
+                if name in res:
+                    res[name]["dS_vs_fp32_storage"] = abs(res[name]["S"] - res["fp32"]["S"])
+        out["precision"] = dict(res, N=N, D=128, K=K)
+        del forms, q, cs, lab
+        torch.cuda.empty_cache()
     # fwd+bwd on the differentiation workload (N=1e6, D=256, K=1000 unit-normalised)
     if left() > 0:
         w = synth.workload_grad(device=dev)
@@ -309,24 +351,25 @@ def main():
     ms_pass1 = statistics.mean(s[0] for s in split)
     ms_pass2 = statistics.mean(s[1] for s in split)
 
-    # roofline of the dominant kernel (the longer pass)
+    # roofline of the dominant kernel (the longer pass); both passes read X and
+    # the labels once, so both are HBM-bound at this K (2K flop per 4 bytes of
+    # X on the tensor cores is far below the tensor ridge)
     bytes_pass1 = N * D * 4 + N * 4          # one read of X and labels
     bytes_pass2 = N * D * 4 + N * 4          # one read of X and labels
     flops_pass2 = 2.0 * N * K * D            # the K dot products per point
-    sm_mhz = clocks["sm_mhz"] or pk["sm_max_mhz"]
+    plan = sil.tensor_plan(X.dtype, D, K)
+    p2_kernel = "k_score_tc (pass 2, tcgen05)" if plan is not None else "k_score_simt (pass 2)"
     if ms_pass2 >= ms_pass1:
-        achieved = flops_pass2 / (ms_pass2 / 1e3) / 1e12
-        peak = ffma_peak_tflops(pk["sm_max_mhz"])
-        roof = {"kernel": "k_score_simt (pass 2)", "bound": "alu", "achieved": achieved, "peak": peak,
-                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
-                "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x max SM clock (derived)",
-                "algorithmic": f"2*N*K*D = {flops_pass2:.3e} flop per launch"}
+        kname, kbytes, kms = p2_kernel, bytes_pass2, ms_pass2
     else:
-        achieved = bytes_pass1 / (ms_pass1 / 1e3) / 1e9
-        roof = {"kernel": "k_aggregate (pass 1)", "bound": "hbm", "achieved": achieved,
-                "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": achieved / pk["hbm_gbs"], "traffic": None,
-                "peak_source": f"{pk['source']} copy bandwidth",
-                "algorithmic": f"N*(4D+4) = {bytes_pass1:.3e} B per launch"}
+        kname, kbytes, kms = "k_aggregate_tma (pass 1)", bytes_pass1, ms_pass1
+    achieved = kbytes / (kms / 1e3) / 1e9
+    roof = {"kernel": kname, "bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+            "frac": achieved / pk["hbm_gbs"], "traffic": None,
+            "peak_source": f"{pk['source']} copy bandwidth (burst)",
+            "algorithmic": f"N*(4D+4) = {kbytes:.3e} B per launch",
+            "timing": "CUDA events around the pass on the launching stream, mean over steps "
+                      "(pass 1 includes its small reference-point and finalisation launches)"}
     pass_info = {"pass1_ms": ms_pass1, "pass1_hbm_gbs": bytes_pass1 / (ms_pass1 / 1e3) / 1e9,
                  "pass2_ms": ms_pass2, "pass2_hbm_gbs": bytes_pass2 / (ms_pass2 / 1e3) / 1e9,
                  "pass2_tflops": flops_pass2 / (ms_pass2 / 1e3) / 1e12}
@@ -368,15 +411,17 @@ def main():
                                         "dS_vs_fp32": abs(float(rb.S.item()) - S_val)}
         del Xb
         torch.cuda.empty_cache()
-        variants.update(variant_lines(dev, args.steps, budget_s=120.0))
+        variants.update(variant_lines(dev, args.steps, budget_s=150.0,
+                                      pk_sustained=pk["bf16_tflops_sustained"]))
 
     cpu = None
     if rank == 0 and world >= 1 and not args.no_cpu_baseline and args.gpus == 1:
         cpu = cpu_oracle_sample(X.cpu().numpy(), lab.cpu().numpy(), K)
 
     if rank == 0:
-        launches_per_step = 9  # pass 1: rep_init, rep_find, shift_build, aggregate, publish;
-        #                        pass 2: fin_global, fin_clusters, score, reduce_S
+        # pass 1: rep_init, rep_find, shift_build, aggregate, publish_status;
+        # pass 2: fin_global, fin_clusters, (tc_pack,) score, reduce_S
+        launches_per_step = 5 + (5 if plan is not None else 4)
         line = {"metric": METRIC, "value": value, "unit": "points/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": t / args.steps * 1e3,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",

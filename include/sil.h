@@ -188,6 +188,20 @@ int sil_score_noalloc(const void* X, int32_t dtype, int64_t n, int32_t d, int64_
                       const int64_t* count, const double* s1, const double* s2, float* s_out,
                       double* S_out, void* saved, uint32_t* dev_status, void* stream);
 
+/*
+ * The cluster-block plan of the tensor-core pass 2 (sil_score with
+ * SIL_PATH_TENSOR or AUTO) for this storage type and shape: *block_k =
+ * clusters per block (the MMA N, a multiple of 16, at most 256) and
+ * *n_blocks = blocks covering the k clusters.  With more than one block every
+ * block is scored by its own CTAs and a combine kernel takes the minimum over
+ * blocks (Eq. 3: b_i is a minimum over clusters, so it splits over any
+ * partition of them).  Host-only arithmetic: no device is touched and the
+ * answer does not say whether the current device can run the path.  Returns
+ * SIL_OK, SIL_EINVAL (null outputs, bad dtype, d or k <= 0) or
+ * SIL_EUNSUPPORTED (no plan fits in shared memory, e.g. d > 128).
+ */
+int sil_tensor_plan(int32_t dtype, int32_t d, int32_t k, int32_t* block_k, int32_t* n_blocks);
+
 /* Human-readable name of a return code or of one status flag. */
 const char* sil_status_string(int32_t status);
 

@@ -9,7 +9,6 @@
 namespace sil {
 
 WsLayout ws_layout(int64_t n, int32_t d, int32_t k, int32_t dtype, int32_t dist, int32_t batch) {
-  (void)dtype;
   (void)dist;
   const size_t dz = size_t(round_up(d, 4));
   const size_t K = size_t(k), N = size_t(n);
@@ -34,7 +33,8 @@ WsLayout ws_layout(int64_t n, int32_t d, int32_t k, int32_t dtype, int32_t dist,
   L.bw_ab = take(2 * N * 4);
   L.bw_f = take((K * dz + K) * 4);
   L.saved = take(N * 12);
-  L.zbf = take(2 * size_t(round_up(k, 256)) * size_t(round_up(d, 64)) * 2 + size_t(round_up(k, 256)) * 16);
+  L.zbf = take(tc_pack_bytes(k, d));
+  L.tcp = take(tc_partial_bytes(n, d, k, dtype));
   L.batch = take(K * (size_t(d) + 2) * 8);
   L.total = o;
   return L;
@@ -162,7 +162,9 @@ int run_score(const void* X, int32_t dtype, int64_t n, int32_t d, int64_t ldx, c
   s.n_partials = np;
   s.status = at<uint32_t>(ws, L.misc);
   s.stream = st;
-  if (tc_ok) return cu(launch_score_tc(s, at<double>(ws, L.g), at<void>(ws, L.zbf), s.status));
+  if (tc_ok)
+    return cu(launch_score_tc(s, at<double>(ws, L.g), at<void>(ws, L.zbf), at<void>(ws, L.tcp),
+                              L.batch - L.tcp, s.status));
   return cu(launch_score_simt(s));
 }
 
@@ -346,6 +348,12 @@ int sil_score_batched(const void* X, int32_t dtype, int64_t n, int32_t d, int64_
     SIL_TRY(cu(launch_reduce_S(at<double>(ws, L.partials), np, n, wst, dev_status, S_out + b, st)));
   }
   return SIL_OK;
+}
+
+int sil_tensor_plan(int32_t dtype, int32_t d, int32_t k, int32_t* block_k, int32_t* n_blocks) {
+  if (!block_k || !n_blocks || d <= 0 || k <= 0) return SIL_EINVAL;
+  if (dtype < SIL_F32 || dtype > SIL_FP8_E4M3) return SIL_EINVAL;
+  return tc_plan_query(dtype, d, k, block_k, n_blocks) ? SIL_OK : SIL_EUNSUPPORTED;
 }
 
 const char* sil_status_string(int32_t status) {

@@ -6,30 +6,47 @@
 // accumulation in tensor memory, at FP32-level accuracy:
 //   * Z = mu' is split into hi + lo BF16 parts (mu' - hi rounded again), so
 //     B carries ~16 significant bits;
-//   * FP32 X (SPLIT) is split the same way by converter warps inside the
+//   * FP32 X (MODE 0) is split the same way by converter warps inside the
 //     kernel and the GEMM is hi.Zhi + hi.Zlo + lo.Zhi (the lo.lo term is
 //     below FP32 rounding of the result);
-//   * BF16 X is exact in BF16: x.Zhi + x.Zlo.
-// The epilogue reads each point's K accumulators from TMEM, forms
+//   * BF16 X (MODE 1) is exact in BF16 and TMA writes it straight into the
+//     operand layout: x.Zhi + x.Zlo;
+//   * FP8-E4M3 X (MODE 2) with per-column scales s: the codes q are exact in
+//     BF16 (converter warps widen them) and the scales are folded into the
+//     centroids, x.mu' = q.(s * mu'): q.Zhi + q.Zlo.
+// The epilogue reads each point's accumulators from TMEM, forms
 // d_k = ||x'||^2 + cb_k - 2 inv x.mu'_k (cb_k = bias_k + 2 g.mu'_k folds the
 // centring on the global mean g back in; inv = 1/||x|| for cosine) and keeps
 // the minimum over k != own cluster.  The own-cluster term a_i uses the exact
 // difference form in FP32 on the converter warps.  The n x K matrix never
 // leaves TMEM.
 //
+// Clusters are processed in blocks of at most 256 (the MMA N).  With one
+// block the epilogue finishes s_i and the per-CTA sums itself.  With G > 1
+// blocks the grid is (point ranges) x (G blocks): each CTA keeps its block's
+// split centroids resident in shared memory and streams the X tiles of its
+// point range -- the G CTAs of a range read the same tiles at about the same
+// time, so the repeats are served by L2 -- and writes, per point, the minimum
+// over its block (and the argmin when the backward record is wanted).  The
+// CTA whose block holds the point's own cluster also writes a_i and ||x'||^2.
+// k_tc_combine then takes the minimum over the blocks and finishes s_i.
+//
 // One persistent CTA per SM, 14 warps:
 //   warp 0       TMA producer (X tiles, labels; the split centroids once)
 //   warp 1       TMEM allocation + single-thread tcgen05.mma issue
 //   warps 2-9    converters: two threads per tile row (one per half) --
-//                FP32 -> BF16 hi/lo in the 128-byte-swizzled K-major layout,
-//                ||x'||^2 and the exact a_i, with the centroids, the global
-//                centre and the cluster constants staged in shared memory
+//                FP32 -> BF16 hi/lo or FP8 -> BF16 in the 128-byte-swizzled
+//                K-major layout, ||x'||^2 and the exact a_i, with the block's
+//                centroids, the global centre and the cluster constants staged
+//                in shared memory
 //   warps 10-13  epilogue: tcgen05.ld, masked running minimum, s_i, sums
-// Ring buffers: raw X stages (SPLIT), A buffers, and two TMEM accumulators,
-// each guarded by mbarriers.  Every wait is bounded (SIL_ETIMEOUT); on a
-// timeout all roles stop, in-flight copies and MMAs are waited for (bounded)
-// and TMEM is freed before the CTA exits.
+// Ring buffers: raw X stages (MODE 0 and 2), A buffers, and two TMEM
+// accumulators, each guarded by mbarriers.  Every wait is bounded
+// (SIL_ETIMEOUT); on a timeout all roles stop, in-flight copies and MMAs are
+// waited for (bounded) and TMEM is freed before the CTA exits.
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_fp8.h>
 
 #include <algorithm>
 #include <cstdlib>
@@ -41,11 +58,22 @@ namespace sil {
 
 namespace {
 
-constexpr int kTM = 128;           // points per tile = TMEM lanes
-constexpr int kTcThreads = 448;    // 14 warps
-constexpr int kConvWarps = 8;      // warps 2..9
+constexpr int kTM = 128;                   // points per tile = TMEM lanes
+constexpr int kTcThreads = 448;            // 14 warps
+constexpr int kConvWarps = 8;              // warps 2..9
 constexpr int kEpiWarp0 = 2 + kConvWarps;  // warps 10..13
-constexpr int kAtomBytes = kTM * 128;  // one 128-row x 128-byte swizzle column
+constexpr int kAtomBytes = kTM * 128;      // one 128-row x 128-byte swizzle column
+constexpr int kMaxBlockN = 256;            // clusters per block (MMA N)
+constexpr int kSmemMax = 227 * 1024;
+
+enum TcMode { kModeF32 = 0, kModeBF16 = 1, kModeFP8 = 2 };
+
+// Per-row code handed from the converters to the epilogue: the own cluster's
+// index within this CTA's block (>= 0), -2 - index for a singleton own
+// cluster, kOwnElsewhere when the own cluster is in another block, and
+// kRowInvalid for rows past n, bad labels and zero-norm rows (cosine).
+constexpr int kOwnElsewhere = -1;
+constexpr int kRowInvalid = -0x7fffffff - 1;
 
 // ------------------------------------------------------------ tcgen05 PTX
 __device__ __forceinline__ uint64_t umma_desc_sw128(uint32_t saddr) {
@@ -55,11 +83,11 @@ __device__ __forceinline__ uint64_t umma_desc_sw128(uint32_t saddr) {
 }
 
 __host__ __device__ constexpr uint32_t umma_idesc_bf16(int M, int N) {
-  return (1u << 4)                          // D: FP32
-         | (1u << 7)                        // A: BF16
-         | (1u << 10)                       // B: BF16
-         | ((uint32_t(N) >> 3) << 17)       // N / 8
-         | ((uint32_t(M) >> 4) << 24);      // M / 16
+  return (1u << 4)                     // D: FP32
+         | (1u << 7)                   // A: BF16
+         | (1u << 10)                  // B: BF16
+         | ((uint32_t(N) >> 3) << 17)  // N / 8
+         | ((uint32_t(M) >> 4) << 24); // M / 16
 }
 
 __device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
@@ -108,28 +136,39 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float lo_elem, float hi_elem) {
   return *reinterpret_cast<uint32_t*>(&v);
 }
 
+// Two E4M3 codes (low byte first) widened exactly to FP32.
+__device__ __forceinline__ float2 fp8x2_to_float2(uint32_t two_codes) {
+  const __half2_raw h = __nv_cvt_fp8x2_to_halfraw2(__nv_fp8x2_storage_t(two_codes & 0xFFFFu), __NV_E4M3);
+  return __half22float2(__half2(h));
+}
+
 // ------------------------------------------------------------ parameters
 struct TcK {
   int64_t n;
   int32_t d;
   int32_t k;
-  int32_t kp;        // MMA N (multiple of 16, >= k)
+  int32_t kp;        // MMA N = clusters per block (multiple of 16)
+  int32_t nblk;      // cluster blocks G (= gridDim.y)
   int32_t acc_cols;  // TMEM columns per accumulator (power of two >= kp)
   int32_t dz;
   int32_t cosine;
   float scale;
-  int32_t nxs;  // raw X stages (SPLIT)
+  int32_t nxs;  // raw X stages (MODE 0, 2)
   int32_t nab;  // A buffers
   int32_t zst;  // stride of the staged centroids (0: not staged)
   const float* zf;
   const float4* cl;
   const float* gf;
-  const float* cb;
+  const float* cb;  // [nblk * kp]
+  const float* cs;  // FP8 column scales
   float* s_out;
   float* sa;
   float* sb;
   int32_t* skstar;
   double* partials;
+  float* pmin;    // [nblk][n] block minimum of (cb - 2 inv x.mu'), NaN for an invalid row
+  int32_t* parg;  // [nblk][n] its argmin (backward record)
+  float2* pown;   // [n]       (a_i before scaling, ||x'||^2), from the own cluster's block
   uint32_t* status;
 };
 
@@ -139,13 +178,18 @@ struct TcMaps {
 
 // Shared-memory plan (byte offsets from a 1024-aligned base).
 struct TcSmem {
-  int zh, zl, abuf, abuf_stride, lo_off, xs, xs_stride, side, side_stride, cb, gsm, clsm, zsm, zst,
-      bars, total;
+  int zh, zl, abuf, abuf_stride, lo_off, xs, xs_stride, side, side_stride, cb, gsm, csm, clsm, zsm,
+      zst, bars, total;
 };
 
+__host__ __device__ constexpr int raw_tile_bytes(int mode, int dp) {
+  return mode == kModeF32 ? (dp / 32) * kAtomBytes : mode == kModeFP8 ? (dp / 128) * kAtomBytes : 0;
+}
+
 // zst: row stride (floats) of the staged centroids, 0 = read them from global memory.
-__host__ __device__ inline TcSmem tc_smem(bool split, int dp, int kp, int nxs, int nab, int zst) {
+__host__ __device__ inline TcSmem tc_smem(int mode, int dp, int kp, int nxs, int nab, int zst) {
   const int natom = dp / 64;
+  const bool staged = mode != kModeBF16;
   TcSmem s;
   int o = 0;
   s.zh = o; o += natom * kp * 128;
@@ -154,17 +198,18 @@ __host__ __device__ inline TcSmem tc_smem(bool split, int dp, int kp, int nxs, i
   o = (o + 1023) & ~1023;
   s.abuf = o;
   s.lo_off = natom * kAtomBytes;
-  s.abuf_stride = natom * kAtomBytes * (split ? 2 : 1);
+  s.abuf_stride = natom * kAtomBytes * (mode == kModeF32 ? 2 : 1);
   o += nab * s.abuf_stride;
   s.xs = o;
-  s.xs_stride = split ? (dp / 32) * kAtomBytes + 1024 : 0;  // + labels (512 B), keeps 1024 alignment
-  o += split ? nxs * s.xs_stride : 0;
+  s.xs_stride = staged ? raw_tile_bytes(mode, dp) + 1024 : 0;  // + labels (512 B), keeps 1024 alignment
+  o += staged ? nxs * s.xs_stride : 0;
   s.side = o;
-  s.side_stride = kTM * 16 + 512;  // xn2, aown, inv, own + labels (bf16 mode)
+  s.side_stride = kTM * 16 + 512;  // xn2, aown, inv, code + labels (BF16 mode)
   o += nab * s.side_stride;
   s.cb = o; o += kp * 4 + 16;  // + 4 floats of block-reduction scratch
   o = (o + 15) & ~15;
   s.gsm = o; o += dp * 4;
+  s.csm = o; o += mode == kModeFP8 ? dp * 4 : 0;
   s.clsm = o; o += kp * 16;
   s.zst = zst;
   s.zsm = o; o += kp * zst * 4;
@@ -213,20 +258,24 @@ __device__ __forceinline__ bool tc_wait(uint64_t* bar, uint32_t parity, volatile
   return true;
 }
 
-template <bool SPLIT, int DP, bool SAVE>
+template <int MODE, int DP, bool SAVE>
 __global__ void __launch_bounds__(kTcThreads, 1) k_score_tc(TcK a, const __grid_constant__ TcMaps maps) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   // 1024-byte alignment for the swizzled tiles, by offsetting the shared array
   // itself so that every access below stays a shared-space access
   unsigned char* base = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
   constexpr int natom = DP / 64;
-  const TcSmem L = tc_smem(SPLIT, DP, a.kp, a.nxs, a.nab, a.zst);
+  constexpr bool STAGED = MODE != kModeBF16;  // converters build the A operand
+  const TcSmem L = tc_smem(MODE, DP, a.kp, a.nxs, a.nab, a.zst);
   const TcBars B = tc_bars(base, L, a.nxs, a.nab);
   volatile int* abort_flag = B.abort_flag;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t ntiles = cdiv(a.n, kTM);
-  // tiles of this CTA: blockIdx.x, blockIdx.x + gridDim.x, ...
+  // tiles of this CTA: blockIdx.x, blockIdx.x + gridDim.x, ...; cluster block blockIdx.y
   const int my_tiles = blockIdx.x < ntiles ? int(cdiv(ntiles - blockIdx.x, gridDim.x)) : 0;
+  const int kb0 = int(blockIdx.y) * a.kp;  // first cluster of this block
+  const int kblk = min(a.kp, a.k - kb0);   // clusters of this block (>= 1)
+  const bool fused = a.nblk == 1;
   float* cbs = reinterpret_cast<float*>(base + L.cb);
 
   if (threadIdx.x == 0) {
@@ -235,9 +284,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_score_tc(TcK a, const __grid_
       mbar_init(&B.xempty[i], kConvWarps);
     }
     for (int i = 0; i < a.nab; ++i) {
-      mbar_init(&B.afull[i], SPLIT ? kConvWarps : 1);  // converters, or the TMA transaction
-      mbar_init(&B.aempty[i], 1 + 4);         // MMA commit + 4 epilogue warps
-      mbar_init(&B.pfull[i], kConvWarps);              // BF16 mode: prep warps wrote the row terms
+      mbar_init(&B.afull[i], STAGED ? kConvWarps : 1);  // converters, or the TMA transaction
+      mbar_init(&B.aempty[i], 1 + 4);                   // MMA commit + 4 epilogue warps
+      mbar_init(&B.pfull[i], kConvWarps);               // BF16 mode: the row terms are written
     }
     for (int i = 0; i < 2; ++i) {
       mbar_init(&B.accfull[i], 1);
@@ -247,16 +296,19 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_score_tc(TcK a, const __grid_
     *B.abort_flag = 0;
     fence_mbar_init();
   }
-  for (int i = threadIdx.x; i < a.kp; i += blockDim.x) cbs[i] = a.cb[i];
+  for (int i = threadIdx.x; i < a.kp; i += blockDim.x) cbs[i] = a.cb[kb0 + i];
   float* gsm = reinterpret_cast<float*>(base + L.gsm);
+  float* csm = reinterpret_cast<float*>(base + L.csm);
   float4* clsm = reinterpret_cast<float4*>(base + L.clsm);
   float* zsm = reinterpret_cast<float*>(base + L.zsm);
   for (int i = threadIdx.x; i < DP; i += blockDim.x) gsm[i] = i < a.dz ? a.gf[i] : 0.f;
-  for (int i = threadIdx.x; i < a.k; i += blockDim.x) clsm[i] = a.cl[i];
+  if (MODE == kModeFP8)
+    for (int i = threadIdx.x; i < DP; i += blockDim.x) csm[i] = i < a.d ? a.cs[i] : 0.f;
+  for (int i = threadIdx.x; i < kblk; i += blockDim.x) clsm[i] = a.cl[kb0 + i];
   if (a.zst)
-    for (int i = threadIdx.x; i < a.k * a.zst; i += blockDim.x) {
+    for (int i = threadIdx.x; i < kblk * a.zst; i += blockDim.x) {
       const int kk = i / a.zst, c = i - kk * a.zst;
-      zsm[i] = c < a.dz ? a.zf[int64_t(kk) * a.dz + c] : 0.f;
+      zsm[i] = c < a.dz ? a.zf[int64_t(kb0 + kk) * a.dz + c] : 0.f;
     }
   if (warp == 1) {  // TMEM: two accumulators of acc_cols columns
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -275,20 +327,26 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_score_tc(TcK a, const __grid_
     if (lane == 0) {
       mbar_arrive_expect_tx(B.zfull, uint32_t(2 * natom * a.kp * 128));
       for (int at = 0; at < natom; ++at) {
-        tma_load_2d(base + L.zh + at * a.kp * 128, &maps.zh, at * 64, 0, B.zfull);
-        tma_load_2d(base + L.zl + at * a.kp * 128, &maps.zl, at * 64, 0, B.zfull);
+        tma_load_2d(base + L.zh + at * a.kp * 128, &maps.zh, at * 64, kb0, B.zfull);
+        tma_load_2d(base + L.zl + at * a.kp * 128, &maps.zl, at * 64, kb0, B.zfull);
       }
       int t = 0;
       for (; t < my_tiles; ++t) {
         const int32_t row0 = int32_t((blockIdx.x + int64_t(t) * gridDim.x) * kTM);
-        if (SPLIT) {
+        if (STAGED) {
           const int j = t % a.nxs;
           if (!tc_wait(&B.xempty[j], ((t / a.nxs) & 1) ^ 1, abort_flag, a.status)) break;
           unsigned char* xs = base + L.xs + j * L.xs_stride;
-          mbar_arrive_expect_tx(&B.xfull[j], uint32_t((DP / 32) * kAtomBytes + kTM * 4));
-          for (int s32 = 0; s32 < DP / 32; ++s32)
-            tma_load_2d(xs + s32 * kAtomBytes, &maps.x, s32 * 32, row0, &B.xfull[j]);
-          tma_load_1d(xs + (DP / 32) * kAtomBytes, &maps.lab, row0, &B.xfull[j]);
+          constexpr int raw = raw_tile_bytes(MODE, DP);
+          mbar_arrive_expect_tx(&B.xfull[j], uint32_t(raw + kTM * 4));
+          if (MODE == kModeF32) {
+            for (int s32 = 0; s32 < DP / 32; ++s32)
+              tma_load_2d(xs + s32 * kAtomBytes, &maps.x, s32 * 32, row0, &B.xfull[j]);
+          } else {
+            for (int s128 = 0; s128 < DP / 128; ++s128)
+              tma_load_2d(xs + s128 * kAtomBytes, &maps.x, s128 * 128, row0, &B.xfull[j]);
+          }
+          tma_load_1d(xs + raw, &maps.lab, row0, &B.xfull[j]);
         } else {
           const int i = t % a.nab;
           if (!tc_wait(&B.aempty[i], ((t / a.nab) & 1) ^ 1, abort_flag, a.status)) break;
@@ -301,8 +359,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_score_tc(TcK a, const __grid_
       }
       if (*abort_flag) {
         // wait (bounded) for every copy this thread issued and nobody consumed
-        const int ring = SPLIT ? a.nxs : a.nab;
-        uint64_t* full = SPLIT ? B.xfull : B.afull;
+        const int ring = STAGED ? a.nxs : a.nab;
+        uint64_t* full = STAGED ? B.xfull : B.afull;
         const int first = t - ring > 0 ? t - ring : 0;
         for (int u = first; u < t; ++u) mbar_wait(&full[u % ring], uint32_t((u / ring) & 1));
         mbar_wait(B.zfull, 0);
@@ -332,7 +390,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_score_tc(TcK a, const __grid_
             umma_bf16(d_tmem, umma_desc_sw128(ahi + ao), umma_desc_sw128(zh + bo), idesc,
                       (at | ks) != 0);
             umma_bf16(d_tmem, umma_desc_sw128(ahi + ao), umma_desc_sw128(zl + bo), idesc, 1);
-            if (SPLIT) umma_bf16(d_tmem, umma_desc_sw128(alo + ao), umma_desc_sw128(zh + bo), idesc, 1);
+            if (MODE == kModeF32)
+              umma_bf16(d_tmem, umma_desc_sw128(alo + ao), umma_desc_sw128(zh + bo), idesc, 1);
           }
         }
         umma_commit(&B.accfull[bsel]);
@@ -350,7 +409,6 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_score_tc(TcK a, const __grid_
     constexpr int HP = DP / 2;  // columns per half
     const int h = lane >> 4;
     const int r = (warp - 2) * 16 + (lane & 15);  // tile row of this thread
-
     for (int t = 0; t < my_tiles; ++t) {
       const int i = t % a.nab;
       const int64_t row = (blockIdx.x + int64_t(t) * gridDim.x) * kTM + r;
@@ -358,22 +416,62 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_score_tc(TcK a, const __grid_
       float* side = reinterpret_cast<float*>(base + L.side + i * L.side_stride);
       float x[HP];
       int own;
-      if (SPLIT) {
+      if (STAGED) {
         const int j = t % a.nxs;
         if (!tc_wait(&B.xfull[j], (t / a.nxs) & 1, abort_flag, a.status)) break;
         if (!tc_wait(&B.aempty[i], ((t / a.nab) & 1) ^ 1, abort_flag, a.status)) break;
         const unsigned char* xs = base + L.xs + j * L.xs_stride;
+        if (MODE == kModeF32) {
 #pragma unroll
-        for (int c4 = 0; c4 < HP / 4; ++c4) {
-          const int col = h * HP + 4 * c4;
-          const float4 v =
-              *reinterpret_cast<const float4*>(xs + (col / 32) * kAtomBytes + sw128(r, (col % 32) / 4));
-          x[4 * c4 + 0] = v.x;
-          x[4 * c4 + 1] = v.y;
-          x[4 * c4 + 2] = v.z;
-          x[4 * c4 + 3] = v.w;
+          for (int c4 = 0; c4 < HP / 4; ++c4) {
+            const int col = h * HP + 4 * c4;
+            const float4 v =
+                *reinterpret_cast<const float4*>(xs + (col / 32) * kAtomBytes + sw128(r, (col % 32) / 4));
+            x[4 * c4 + 0] = v.x;
+            x[4 * c4 + 1] = v.y;
+            x[4 * c4 + 2] = v.z;
+            x[4 * c4 + 3] = v.w;
+          }
+        } else {
+          // FP8 codes, 16 per 16-byte chunk; the A operand takes the codes
+          // themselves (exact in BF16), the per-point terms below the scaled values
+#pragma unroll
+          for (int c16 = 0; c16 < HP / 16; ++c16) {
+            const int col = h * HP + 16 * c16;
+            const uint4 u =
+                *reinterpret_cast<const uint4*>(xs + (col / 128) * kAtomBytes + sw128(r, (col % 128) / 16));
+            const uint32_t w[4] = {u.x, u.y, u.z, u.w};
+            uint32_t hw[8];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              const float2 f0 = fp8x2_to_float2(w[e]);
+              const float2 f1 = fp8x2_to_float2(w[e] >> 16);
+              x[16 * c16 + 4 * e + 0] = f0.x;
+              x[16 * c16 + 4 * e + 1] = f0.y;
+              x[16 * c16 + 4 * e + 2] = f1.x;
+              x[16 * c16 + 4 * e + 3] = f1.y;
+              hw[2 * e] = pack_bf16x2(f0.x, f0.y);
+              hw[2 * e + 1] = pack_bf16x2(f1.x, f1.y);
+            }
+            // 16 columns = two 16-byte chunks of the BF16 operand
+            *reinterpret_cast<uint4*>(ab + (col / 64) * kAtomBytes + sw128(r, (col % 64) / 8)) =
+                make_uint4(hw[0], hw[1], hw[2], hw[3]);
+            *reinterpret_cast<uint4*>(ab + ((col + 8) / 64) * kAtomBytes + sw128(r, ((col + 8) % 64) / 8)) =
+                make_uint4(hw[4], hw[5], hw[6], hw[7]);
+          }
+          fence_proxy_async_smem();
+#pragma unroll
+          for (int c4 = 0; c4 < HP / 4; ++c4) {
+            const float4 s4 = *reinterpret_cast<const float4*>(csm + h * HP + 4 * c4);
+            const float2 xa = __fmul2_rn(make_float2(x[4 * c4], x[4 * c4 + 1]), make_float2(s4.x, s4.y));
+            const float2 xb = __fmul2_rn(make_float2(x[4 * c4 + 2], x[4 * c4 + 3]), make_float2(s4.z, s4.w));
+            x[4 * c4 + 0] = xa.x;
+            x[4 * c4 + 1] = xa.y;
+            x[4 * c4 + 2] = xb.x;
+            x[4 * c4 + 3] = xb.y;
+          }
         }
-        own = reinterpret_cast<const int32_t*>(xs + (DP / 32) * kAtomBytes)[r];
+        own = reinterpret_cast<const int32_t*>(xs + raw_tile_bytes(MODE, DP))[r];
       } else {
         if (!tc_wait(&B.afull[i], (t / a.nab) & 1, abort_flag, a.status)) break;
 #pragma unroll
@@ -411,11 +509,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_score_tc(TcK a, const __grid_
         }
         inv = ss > 0.f ? rsqrtf(ss) : 0.f;
       }
+      // is the point's own cluster in this block?
+      const int ol = own - kb0;
+      const bool in_blk = valid && ol >= 0 && ol < kblk;
+      const int olc = in_blk ? ol : 0;
       // ||x'||^2 and the exact own-cluster term (x' = x inv - g), half a row
       // each, two columns per packed FP32x2 instruction
       float2 xn2 = make_float2(0.f, 0.f), ae = xn2;
       const float2 inv2 = make_float2(inv, inv);
-      const int ownc = valid ? own : 0;
 #pragma unroll
       for (int c4 = 0; c4 < HP / 4; ++c4) {
         const int col = h * HP + 4 * c4;
@@ -423,9 +524,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_score_tc(TcK a, const __grid_
         float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
         if (col < a.dz) {
           if (a.zst)  // staged centroids (uniform branch)
-            z = *reinterpret_cast<const float4*>(zsm + ownc * a.zst + col);
+            z = *reinterpret_cast<const float4*>(zsm + olc * a.zst + col);
           else
-            z = __ldg(reinterpret_cast<const float4*>(a.zf + int64_t(ownc) * a.dz + col));
+            z = __ldg(reinterpret_cast<const float4*>(a.zf + int64_t(kb0 + olc) * a.dz + col));
         }
         const float2 xa = make_float2(x[4 * c4], x[4 * c4 + 1]), xb = make_float2(x[4 * c4 + 2], x[4 * c4 + 3]);
         const float2 ca = __ffma2_rn(xa, inv2, make_float2(-g.x, -g.y));
@@ -440,7 +541,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_score_tc(TcK a, const __grid_
       float xn2s = xn2.x + xn2.y, aes = ae.x + ae.y;
       xn2s += __shfl_xor_sync(0xffffffffu, xn2s, 16);
       aes += __shfl_xor_sync(0xffffffffu, aes, 16);
-      if (SPLIT) {
+      if (MODE == kModeF32) {
         // hi/lo BF16 split of this half row into the swizzled A buffer
 #pragma unroll
         for (int c8 = 0; c8 < HP / 8; ++c8) {
@@ -463,19 +564,20 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_score_tc(TcK a, const __grid_
       }
       if (h == 0) {
         float aown = 0.f;
-        if (valid) {
-          const float4 co = clsm[own];
+        int code = valid ? kOwnElsewhere : kRowInvalid;
+        if (in_blk) {
+          const float4 co = clsm[ol];
           aown = fmaf(co.y, aes, co.z);
-          if (co.w < 1.5f) own = -2 - own;  // singleton: s_i = 0, b_i still reported
+          code = co.w < 1.5f ? -2 - ol : ol;  // singleton: s_i = 0, b_i still reported
         }
         side[r] = xn2s;
         side[kTM + r] = aown;
         side[2 * kTM + r] = inv;
-        reinterpret_cast<int*>(side)[3 * kTM + r] = valid ? own : -1;
+        reinterpret_cast<int*>(side)[3 * kTM + r] = code;
       }
       __syncwarp();
       if (lane == 0) {
-        if (SPLIT) {
+        if (STAGED) {
           mbar_arrive(&B.afull[i]);
           mbar_arrive(&B.xempty[t % a.nxs]);
         } else {
@@ -485,17 +587,18 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_score_tc(TcK a, const __grid_
     }
   } else {
     // ---------------------------------------------- epilogue warps 10..13
-    const int q = warp & 3;          // TMEM lane quarter this warp may access
-    const int r = q * 32 + lane;     // tile row = TMEM lane
+    const int q = warp & 3;       // TMEM lane quarter this warp may access
+    const int r = q * 32 + lane;  // tile row = TMEM lane
     float tsum = 0.f;
     for (int t = 0; t < my_tiles; ++t) {
       const int i = t % a.nab, bsel = t & 1;
       if (!tc_wait(&B.accfull[bsel], (t >> 1) & 1, abort_flag, a.status)) break;
-      if (!tc_wait(SPLIT ? &B.afull[i] : &B.pfull[i], (t / a.nab) & 1, abort_flag, a.status)) break;
+      if (!tc_wait(STAGED ? &B.afull[i] : &B.pfull[i], (t / a.nab) & 1, abort_flag, a.status)) break;
       tc_fence_after();
       const float* side = reinterpret_cast<const float*>(base + L.side + i * L.side_stride);
-      const int own_raw = reinterpret_cast<const int*>(side)[3 * kTM + r];
-      const int own = own_raw >= 0 ? own_raw : (own_raw <= -2 ? -2 - own_raw : -1);
+      const int code = reinterpret_cast<const int*>(side)[3 * kTM + r];
+      const bool row_ok = code != kRowInvalid;
+      const int own = code >= 0 ? code : (row_ok && code <= -2 ? -2 - code : -1);  // in-block index
       const float sc = -2.f * side[2 * kTM + r];
       float best = INFINITY;
       int kb = -1;
@@ -530,36 +633,45 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_score_tc(TcK a, const __grid_
       if (lane == 0) mbar_arrive(&B.accempty[bsel]);
       const int64_t row = (blockIdx.x + int64_t(t) * gridDim.x) * kTM + r;
       if (row < a.n) {
-        float av = 0.f, bv = INFINITY, sv = 0.f;
-        if (own >= 0) {
-          const bool has_b = best < INFINITY;
-          av = fmaxf(0.f, a.scale * side[kTM + r]);
-          bv = has_b ? fmaxf(0.f, a.scale * (side[r] + best)) : INFINITY;
-          if (own_raw >= 0 && has_b) {
-            const float m = fmaxf(av, bv);
-            sv = m > 0.f ? (av <= bv ? 1.f - av / bv : bv / av - 1.f) : 0.f;
+        if (fused) {
+          float av = 0.f, bv = INFINITY, sv = 0.f;
+          if (row_ok) {
+            const bool has_b = best < INFINITY;
+            av = fmaxf(0.f, a.scale * side[kTM + r]);
+            bv = has_b ? fmaxf(0.f, a.scale * (side[r] + best)) : INFINITY;
+            if (code >= 0 && has_b) {
+              const float m = fmaxf(av, bv);
+              sv = m > 0.f ? (av <= bv ? 1.f - av / bv : bv / av - 1.f) : 0.f;
+            }
+            if (!has_b) kb = -1;
+          } else {
+            kb = -1;
           }
-          if (!SAVE) kb = has_b ? 0 : -1;
+          if (a.s_out) a.s_out[row] = sv;
+          if (SAVE) {
+            a.sa[row] = av;
+            a.sb[row] = bv;
+            a.skstar[row] = kb;
+          }
+          tsum += sv;
         } else {
-          kb = -1;
+          const int64_t o = int64_t(blockIdx.y) * a.n + row;
+          a.pmin[o] = row_ok ? best : __int_as_float(0x7fc00000);
+          if (SAVE) a.parg[o] = (row_ok && kb >= 0) ? kb0 + kb : -1;
+          if (own >= 0) a.pown[row] = make_float2(side[kTM + r], side[r]);
         }
-        if (a.s_out) a.s_out[row] = sv;
-        if (SAVE) {
-          a.sa[row] = av;
-          a.sb[row] = bv;
-          a.skstar[row] = kb;
-        }
-        tsum += sv;
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(&B.aempty[i]);
     }
-    // block partial over the 128 epilogue threads
-    for (int o = 16; o > 0; o >>= 1) tsum += __shfl_xor_sync(0xffffffffu, tsum, o);
-    float* red = cbs + a.kp;  // 4 floats of scratch right after cb (within the plan's padding)
-    if (lane == 0) red[q] = tsum;
-    asm volatile("bar.sync 1, 128;" ::: "memory");
-    if (warp == kEpiWarp0 && lane == 0) a.partials[blockIdx.x] = double(red[0]) + red[1] + red[2] + red[3];
+    if (fused) {
+      // block partial over the 128 epilogue threads
+      for (int o = 16; o > 0; o >>= 1) tsum += __shfl_xor_sync(0xffffffffu, tsum, o);
+      float* red = cbs + a.kp;  // 4 floats of scratch right after cb (within the plan's padding)
+      if (lane == 0) red[q] = tsum;
+      asm volatile("bar.sync 1, 128;" ::: "memory");
+      if (warp == kEpiWarp0 && lane == 0) a.partials[blockIdx.x] = double(red[0]) + red[1] + red[2] + red[3];
+    }
   }
   __syncthreads();
   if (warp == 1) {
@@ -569,20 +681,77 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_score_tc(TcK a, const __grid_
   }
 }
 
+// s_i from the per-block results when the clusters span several blocks: the
+// minimum over the blocks (lowest cluster index on ties: blocks are visited
+// in order and only a strictly smaller value replaces the best), then Eq. 2
+// with the singleton and max(a, b) = 0 rules, and one partial sum per CTA.
+__global__ void k_tc_combine(int64_t n, int32_t k, int32_t nblk, const int32_t* labels, const float4* cl,
+                             float scale, const float* pmin, const int32_t* parg, const float2* pown,
+                             float* s_out, float* sa, float* sb, int32_t* skstar, double* partials) {
+  float tsum = 0.f;
+  for (int64_t row = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; row < n;
+       row += int64_t(gridDim.x) * blockDim.x) {
+    const int own = labels[row];
+    float best = INFINITY, av = 0.f, bv = INFINITY, sv = 0.f;
+    int kb = -1;
+    bool bad = own < 0 || own >= k;
+    for (int g = 0; g < nblk && !bad; ++g) {
+      const float v = pmin[int64_t(g) * n + row];
+      if (v != v) {
+        bad = true;  // NaN marks a row the scoring kernel rejected (zero norm)
+      } else if (v < best) {
+        best = v;
+        if (parg) kb = parg[int64_t(g) * n + row];
+      }
+    }
+    if (!bad) {
+      const float2 pw = pown[row];
+      const bool has_b = best < INFINITY;
+      av = fmaxf(0.f, scale * pw.x);
+      bv = has_b ? fmaxf(0.f, scale * (pw.y + best)) : INFINITY;
+      if (has_b && cl[own].w > 1.5f) {
+        const float m = fmaxf(av, bv);
+        sv = m > 0.f ? (av <= bv ? 1.f - av / bv : bv / av - 1.f) : 0.f;
+      }
+      if (!has_b) kb = -1;
+    } else {
+      kb = -1;
+    }
+    if (s_out) s_out[row] = sv;
+    if (sa) {
+      sa[row] = av;
+      sb[row] = bv;
+      skstar[row] = kb;
+    }
+    tsum += sv;
+  }
+  __shared__ float red[32];
+  for (int o = 16; o > 0; o >>= 1) tsum += __shfl_xor_sync(0xffffffffu, tsum, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = tsum;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < int(blockDim.x >> 5); ++w) t += double(red[w]);
+    partials[blockIdx.x] = t;
+  }
+}
+
 // Split centroids and per-cluster constants for the tensor-core kernel:
-//   zh/zl (bf16 [kp][dp], zero padded) with zh + zl ~ mu'_k to ~16 bits,
+//   zh/zl (bf16 [kpad][dp], zero padded) with zh + zl ~ (cs *) mu'_k to ~16 bits,
 //   cb[k] = bias_k + 2 g.mu'_k (+inf for empty clusters and padding).
-__global__ void k_tc_pack(const float* zf, const float4* cl, const double* g, int32_t k, int32_t d,
-                          int32_t dz, int32_t kp, int32_t dp, __nv_bfloat16* zh, __nv_bfloat16* zl,
+// With FP8 storage the column scales cs are folded into the split values.
+__global__ void k_tc_pack(const float* zf, const float4* cl, const double* g, const float* cs, int32_t k,
+                          int32_t d, int32_t dz, int32_t dp, __nv_bfloat16* zh, __nv_bfloat16* zl,
                           float* cb) {
   __shared__ double red[32];
   const int kk = blockIdx.x;
   double dot = 0.0;
   for (int c = threadIdx.x; c < dp; c += blockDim.x) {
     const float z = (kk < k && c < dz) ? zf[int64_t(kk) * dz + c] : 0.f;
-    const __nv_bfloat16 h = __float2bfloat16_rn(z);
-    zh[int64_t(kk) * dp + c] = h;
-    zl[int64_t(kk) * dp + c] = __float2bfloat16_rn(z - __bfloat162float(h));
+    const float zs = cs ? (c < d ? z * cs[c] : 0.f) : z;
+    const __nv_bfloat16 hh = __float2bfloat16_rn(zs);
+    zh[int64_t(kk) * dp + c] = hh;
+    zl[int64_t(kk) * dp + c] = __float2bfloat16_rn(zs - __bfloat162float(hh));
     if (c < d) dot += g[c] * double(z);
   }
   for (int o = 16; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
@@ -603,56 +772,132 @@ int pow2_at_least(int v) {
   return p;
 }
 
+int mode_of(int32_t dtype) { return dtype == SIL_F32 ? kModeF32 : dtype == SIL_BF16 ? kModeBF16 : kModeFP8; }
+
+// Launch plan: cluster-block width kp, ring depths and whether the centroids
+// are staged for the own-cluster term.  Candidates are ranked by a small cost
+// model -- work per point over the G blocks times penalties for shallow rings
+// (a single A buffer serialises conversion and MMA; a single raw stage
+// exposes the TMA latency) and for unstaged centroids -- and the cheapest
+// plan whose shared memory fits is taken.
+struct TcPlan {
+  int kp, nblk, nxs, nab, zst, smem;
+};
+
+bool tc_plan(int32_t dtype, int32_t k, int32_t d, TcPlan* out) {
+  const int mode = mode_of(dtype);
+  const bool staged = mode != kModeBF16;
+  const int dp = int(round_up(d, 64));
+  const int dz = int(round_up(d, 4));
+  const int kmax = int(std::min<int64_t>(round_up(std::max(k, 16), 16), kMaxBlockN));
+  double best_cost = 0.0;
+  bool found = false;
+  for (int kp = kmax; kp >= 16; kp -= 16) {
+    const int nblk = int(cdiv(k, kp));
+    for (int nab = 1; nab <= 4; ++nab) {
+      for (int nxs = 1; nxs <= (staged ? 3 : 1); ++nxs) {
+        for (int zs = 0; zs < 2; ++zs) {
+          const int zst = zs ? dz + 4 : 0;  // padded rows: fewer bank conflicts
+          const int smem = tc_smem(mode, dp, kp, nxs, nab, zst).total;
+          if (smem > kSmemMax) continue;
+          // per block and tile: MMA + epilogue ~ kp columns (the MMA is bound by
+          // its A-operand reads below ~64), plus a fixed share for conversion,
+          // row terms and the per-block results
+          double cost = double(nblk) * (std::max(kp, 64) + 64);
+          if (nab < 2) cost *= 1.4;
+          if (staged && nxs < 2) cost *= 1.2;
+          if (staged && nxs == 2) cost *= 1.02;
+          if (!staged && nab == 2) cost *= 1.02;
+          if (!zst) cost *= 1.05;
+          if (!found || cost < best_cost) {
+            found = true;
+            best_cost = cost;
+            *out = TcPlan{kp, nblk, nxs, nab, zst, smem};
+          }
+        }
+      }
+    }
+  }
+  return found;
+}
+
 }  // namespace
 
 bool tc_eligible(int32_t dtype, int64_t n, int32_t d, int64_t ldx, int32_t k, const void* X,
                  const int32_t* labels) {
   const char* e = getenv("SIL_TC_DISABLE");
   if (e && e[0] == '1') return false;
-  if (dtype != SIL_F32 && dtype != SIL_BF16) return false;
-  if (n <= 0 || n >= (int64_t(1) << 31) || k > 256 || d > 128) return false;
-  const int esz = dtype == SIL_F32 ? 4 : 2;
-  if (d < (dtype == SIL_F32 ? 32 : 64)) return false;  // the TMA box must fit inside a row
+  if (n <= 0 || n >= (int64_t(1) << 31) || d > 128) return false;
   if (reinterpret_cast<uintptr_t>(X) % 16 || reinterpret_cast<uintptr_t>(labels) % 16) return false;
+  const int esz = dtype == SIL_F32 ? 4 : dtype == SIL_BF16 ? 2 : 1;
   if ((ldx * esz) % 16) return false;
-  // the centroids, one A buffer and (FP32) one raw X stage must fit in shared memory
-  const int dp = int(round_up(d, 64)), kp = int(round_up(std::max(k, 16), 16));
-  if (tc_smem(dtype == SIL_F32, dp, kp, 1, 1, 0).total > 227 * 1024) return false;
+  // the TMA box of a row must fit inside the row
+  if (dtype == SIL_F32 && d < 32) return false;
+  if (dtype == SIL_BF16 && d < 64) return false;
+  if (dtype == SIL_FP8_E4M3 && d != 128) return false;
+  TcPlan p;
+  if (!tc_plan(dtype, k, d, &p)) return false;
   int dev = 0, major = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return false;
   if (cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev) != cudaSuccess) return false;
   return major == 10;
 }
 
-size_t tc_pack_bytes(int32_t k, int32_t d) {
-  const size_t kp = size_t(round_up(std::max(k, 16), 16)), dp = size_t(round_up(d, 64));
-  return 2 * kp * dp * 2 + kp * 4 + 256;
+bool tc_plan_query(int32_t dtype, int32_t d, int32_t k, int32_t* block_k, int32_t* n_blocks) {
+  if (d > 128 || d <= 0 || k <= 0) return false;
+  TcPlan p;
+  if (!tc_plan(dtype, k, d, &p)) return false;
+  *block_k = p.kp;
+  *n_blocks = p.nblk;
+  return true;
 }
 
-cudaError_t launch_score_tc(const ScoreLaunch& s, const double* g, void* pack, uint32_t* status) {
+size_t tc_pack_bytes(int32_t k, int32_t d) {
+  // nblk * kp < k + kp <= k + 256
+  const size_t kpad = size_t(round_up(std::max(k, 16), 16)) + kMaxBlockN, dp = size_t(round_up(d, 64));
+  return 2 * kpad * dp * 2 + kpad * 4 + 256;
+}
+
+size_t tc_partial_bytes(int64_t n, int32_t d, int32_t k, int32_t dtype) {
+  if (n <= 0 || d > 128 || dtype < SIL_F32 || dtype > SIL_FP8_E4M3) return 0;
+  TcPlan p;
+  if (!tc_plan(dtype, k, d, &p) || p.nblk == 1) return 0;
+  const size_t N = size_t(n), G = size_t(p.nblk);
+  return align256(G * N * 4) + align256(G * N * 4) + align256(N * 8);
+}
+
+cudaError_t launch_score_tc(const ScoreLaunch& s, const double* g, void* pack, void* partial_ws,
+                            size_t partial_bytes, uint32_t* status) {
+  TcPlan plan;
+  if (!tc_plan(s.dtype, s.k, s.d, &plan)) return cudaErrorInvalidValue;
+  if (plan.nblk > 1 && partial_bytes < tc_partial_bytes(s.n, s.d, s.k, s.dtype)) return cudaErrorInvalidValue;
+  const int mode = mode_of(s.dtype);
   const int dp = int(round_up(s.d, 64));
-  const int kp = int(round_up(std::max(s.k, 16), 16));
+  const int kp = plan.kp;
+  const int kpad = plan.nblk * kp;
   const int dz = int(round_up(s.d, 4));
   __nv_bfloat16* zh = static_cast<__nv_bfloat16*>(pack);
-  __nv_bfloat16* zl = zh + size_t(kp) * dp;
-  float* cb = reinterpret_cast<float*>(zl + size_t(kp) * dp);
-  k_tc_pack<<<kp, 128, 0, s.stream>>>(s.zf, s.cl, g, s.k, s.d, dz, kp, dp, zh, zl, cb);
+  __nv_bfloat16* zl = zh + size_t(kpad) * dp;
+  float* cb = reinterpret_cast<float*>(zl + size_t(kpad) * dp);
+  k_tc_pack<<<kpad, 128, 0, s.stream>>>(s.zf, s.cl, g, mode == kModeFP8 ? s.cs : nullptr, s.k, s.d, dz, dp,
+                                         zh, zl, cb);
   cudaError_t err = cudaGetLastError();
   if (err != cudaSuccess) return err;
 
-  const bool split = s.dtype == SIL_F32;
   TcMaps maps{};
-  const int esz = split ? 4 : 2;
-  const CUtensorMapDataType xt = split ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
-  const uint32_t box_inner = split ? 32 : 64;
+  const int esz = mode == kModeF32 ? 4 : mode == kModeBF16 ? 2 : 1;
+  const CUtensorMapDataType xt = mode == kModeF32    ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                 : mode == kModeBF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                                     : CU_TENSOR_MAP_DATA_TYPE_UINT8;
+  const uint32_t box_inner = mode == kModeF32 ? 32 : mode == kModeBF16 ? 64 : 128;
   if (!encode_tmap_2d(&maps.x, s.X, xt, esz, uint64_t(s.d), uint64_t(s.n), uint64_t(s.ldx) * esz, box_inner,
                       kTM, CU_TENSOR_MAP_SWIZZLE_128B))
     return cudaErrorInvalidValue;
   if (!encode_tmap_1d(&maps.lab, s.labels, CU_TENSOR_MAP_DATA_TYPE_INT32, uint64_t(s.n), kTM))
     return cudaErrorInvalidValue;
-  if (!encode_tmap_2d(&maps.zh, zh, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, uint64_t(dp), uint64_t(kp),
+  if (!encode_tmap_2d(&maps.zh, zh, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, uint64_t(dp), uint64_t(kpad),
                       uint64_t(dp) * 2, 64, uint32_t(kp), CU_TENSOR_MAP_SWIZZLE_128B) ||
-      !encode_tmap_2d(&maps.zl, zl, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, uint64_t(dp), uint64_t(kp),
+      !encode_tmap_2d(&maps.zl, zl, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, uint64_t(dp), uint64_t(kpad),
                       uint64_t(dp) * 2, 64, uint32_t(kp), CU_TENSOR_MAP_SWIZZLE_128B))
     return cudaErrorInvalidValue;
 
@@ -661,54 +906,63 @@ cudaError_t launch_score_tc(const ScoreLaunch& s, const double* g, void* pack, u
   k.d = s.d;
   k.k = s.k;
   k.kp = kp;
+  k.nblk = plan.nblk;
   k.acc_cols = pow2_at_least(kp);
   k.dz = dz;
   k.cosine = s.dist == SIL_COSINE;
   k.scale = s.dist == SIL_COSINE ? 0.5f : 1.f;
+  k.nxs = plan.nxs;
+  k.nab = plan.nab;
+  k.zst = plan.zst;
   k.zf = s.zf;
   k.cl = s.cl;
   k.gf = s.gf;
   k.cb = cb;
+  k.cs = s.cs;
   k.s_out = s.s_out;
   k.sa = s.sa;
   k.sb = s.sb;
   k.skstar = s.skstar;
   k.partials = s.partials;
   k.status = status;
-  // deepest rings that fit: A buffers first (2), then raw X stages
-  const int budget = 227 * 1024;
-  int nab = 2, nxs = split ? 3 : 0;
-  if (!split) nab = 4;
-  // stage the centroids (padded rows: fewer bank conflicts) when 2 A buffers + 2 stages still fit
-  int zst = dz + 4;
-  if (tc_smem(split, dp, kp, split ? 2 : 1, 2, zst).total > budget) zst = 0;
-  while (tc_smem(split, dp, kp, std::max(nxs, 1), nab, zst).total > budget) {
-    if (split && nxs > 2) --nxs;
-    else if (nab > 2) --nab;
-    else if (split && nxs > 1) --nxs;
-    else if (nab > 1) --nab;
-    else return cudaErrorInvalidValue;
-  }
-  k.nxs = std::max(nxs, 1);
-  k.nab = nab;
-  k.zst = zst;
-  const int smem = tc_smem(split, dp, kp, k.nxs, nab, zst).total;
-  const int64_t ntiles = cdiv(s.n, kTM);
-  const int grid = int(std::min<int64_t>(ntiles, kNumSMs));
   const bool save = s.sa != nullptr;
+  if (plan.nblk > 1) {
+    const size_t N = size_t(s.n), G = size_t(plan.nblk);
+    char* p = static_cast<char*>(partial_ws);
+    k.pmin = reinterpret_cast<float*>(p);
+    k.parg = reinterpret_cast<int32_t*>(p + align256(G * N * 4));
+    k.pown = reinterpret_cast<float2*>(p + 2 * align256(G * N * 4));
+  }
+  const int64_t ntiles = cdiv(s.n, kTM);
+  const int per_block = std::max(1, kNumSMs / plan.nblk);
+  const dim3 grid(unsigned(std::min<int64_t>(ntiles, per_block)), unsigned(plan.nblk));
   auto launch = [&](auto fn) {
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, plan.smem);
     if (e != cudaSuccess) return e;
-    fn<<<grid, kTcThreads, smem, s.stream>>>(k, maps);
+    fn<<<grid, kTcThreads, plan.smem, s.stream>>>(k, maps);
     return cudaGetLastError();
   };
-  *s.n_partials = grid;
-  if (split) {
-    if (dp == 64) return save ? launch(k_score_tc<true, 64, true>) : launch(k_score_tc<true, 64, false>);
-    return save ? launch(k_score_tc<true, 128, true>) : launch(k_score_tc<true, 128, false>);
+  cudaError_t e;
+  if (mode == kModeF32) {
+    if (dp == 64) e = save ? launch(k_score_tc<kModeF32, 64, true>) : launch(k_score_tc<kModeF32, 64, false>);
+    else e = save ? launch(k_score_tc<kModeF32, 128, true>) : launch(k_score_tc<kModeF32, 128, false>);
+  } else if (mode == kModeBF16) {
+    if (dp == 64) e = save ? launch(k_score_tc<kModeBF16, 64, true>) : launch(k_score_tc<kModeBF16, 64, false>);
+    else e = save ? launch(k_score_tc<kModeBF16, 128, true>) : launch(k_score_tc<kModeBF16, 128, false>);
+  } else {
+    e = save ? launch(k_score_tc<kModeFP8, 128, true>) : launch(k_score_tc<kModeFP8, 128, false>);
   }
-  if (dp == 64) return save ? launch(k_score_tc<false, 64, true>) : launch(k_score_tc<false, 64, false>);
-  return save ? launch(k_score_tc<false, 128, true>) : launch(k_score_tc<false, 128, false>);
+  if (e != cudaSuccess) return e;
+  if (plan.nblk == 1) {
+    *s.n_partials = int(grid.x);
+    return cudaSuccess;
+  }
+  const int cgrid = int(std::max<int64_t>(1, std::min<int64_t>(cdiv(s.n, 256), int64_t(kNumSMs) * 4)));
+  k_tc_combine<<<cgrid, 256, 0, s.stream>>>(s.n, s.k, plan.nblk, s.labels, s.cl, k.scale, k.pmin,
+                                            save ? k.parg : nullptr, k.pown, s.s_out, s.sa, s.sb, s.skstar,
+                                            s.partials);
+  *s.n_partials = cgrid;
+  return cudaGetLastError();
 }
 
 }  // namespace sil

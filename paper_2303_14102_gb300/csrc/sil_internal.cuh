@@ -54,6 +54,7 @@ struct WsLayout {
   size_t bw_f;      // float[k*dz + k]   backward: W_c rows then C_c
   size_t saved;     // 12 bytes * n      recomputed forward record
   size_t zbf;       // bf16 centroid tiles for the tensor path
+  size_t tcp;       // tensor path with several cluster blocks: per-block minima
   size_t batch;     // batched aggregates
   size_t total;
 };
@@ -203,7 +204,12 @@ cudaError_t launch_score_simt(ScoreLaunch& s);
 bool tc_eligible(int32_t dtype, int64_t n, int32_t d, int64_t ldx, int32_t k, const void* X,
                  const int32_t* labels);
 size_t tc_pack_bytes(int32_t k, int32_t d);
-cudaError_t launch_score_tc(const ScoreLaunch& s, const double* g, void* pack, uint32_t* status);
+// Host-only: the cluster-block plan (false when none fits).
+bool tc_plan_query(int32_t dtype, int32_t d, int32_t k, int32_t* block_k, int32_t* n_blocks);
+// Bytes of the per-block results when k needs several cluster blocks (else 0).
+size_t tc_partial_bytes(int64_t n, int32_t d, int32_t k, int32_t dtype);
+cudaError_t launch_score_tc(const ScoreLaunch& s, const double* g, void* pack, void* partial_ws,
+                            size_t partial_bytes, uint32_t* status);
 // S = sum(partials)/n, NaN when the workspace status word is non-zero; the
 // word is OR-ed into user_status.
 cudaError_t launch_reduce_S(const double* partials, int32_t np, int64_t n, const uint32_t* ws_status,

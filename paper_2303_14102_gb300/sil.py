@@ -31,7 +31,8 @@ SIL_AGG_ACCUMULATE = 1
 METRICS = {"sqeuclidean": 0, "cosine": 1}
 PATHS = {"auto": 0, "simt": 1, "tensor": 2}
 EXPORTED = ("sil_workspace_size", "sil_saved_size", "sil_aggregate", "sil_score",
-            "sil_score_backward", "sil_score_batched", "sil_status_string", "sil_version")
+            "sil_score_backward", "sil_score_batched", "sil_tensor_plan", "sil_status_string",
+            "sil_version")
 
 _lock = threading.Lock()
 _lib = None
@@ -76,6 +77,8 @@ def load(build_if_stale: bool = True) -> ctypes.CDLL:
             lib.sil_score_noalloc.argtypes = [vp, i32, i64, i32, i64, vp, vp, i32, i32, vp, vp, vp,
                                               vp, vp, vp, vp, vp]
             lib.sil_score_noalloc.restype = ctypes.c_int
+            lib.sil_tensor_plan.argtypes = [i32, i32, i32, vp, vp]
+            lib.sil_tensor_plan.restype = ctypes.c_int
             lib.sil_status_string.argtypes = [i32]
             lib.sil_status_string.restype = ctypes.c_char_p
             lib.sil_version.restype = i32
@@ -281,6 +284,18 @@ def score_batched(X: torch.Tensor, labels: torch.Tensor, ks, metric: str = "sqeu
                                _ptr(ws), need, _ptr(status), _stream_handle(X.device))
     _rc(rc, "sil_score_batched")
     return S
+
+
+def tensor_plan(dtype: torch.dtype, D: int, K: int):
+    """(clusters per block, number of blocks) of the tensor-core pass 2, or None."""
+    lib = load()
+    bk, nb = ctypes.c_int32(0), ctypes.c_int32(0)
+    code = {torch.float32: 0, torch.bfloat16: 1, torch.float8_e4m3fn: 2}[dtype]
+    rc = lib.sil_tensor_plan(code, D, K, ctypes.byref(bk), ctypes.byref(nb))
+    if rc == SIL_EUNSUPPORTED:
+        return None
+    _rc(rc, "sil_tensor_plan")
+    return bk.value, nb.value
 
 
 def silhouette(X: torch.Tensor, labels: torch.Tensor, K: int, metric: str = "sqeuclidean",

@@ -103,3 +103,24 @@ def test_binding_refuses_cpu_tensors():
     X = torch.zeros(4, 2)
     with pytest.raises(RuntimeError, match="CUDA"):
         sil.aggregate(X, torch.zeros(4, dtype=torch.int32), 2)
+
+
+def test_tensor_plan_is_host_arithmetic():
+    import torch
+    # one block covers k <= 256 when it fits; k = 1000 in BF16 at d = 128 takes
+    # four blocks of 256 (two A buffers beside the resident split centroids)
+    assert sil.tensor_plan(torch.float32, 64, 100) == (112, 1)
+    assert sil.tensor_plan(torch.bfloat16, 128, 1000) == (256, 4)
+    for dt, d, k in [(torch.float32, 128, 256), (torch.float8_e4m3fn, 128, 1000),
+                     (torch.float32, 32, 513), (torch.bfloat16, 64, 4096)]:
+        bk, nb = sil.tensor_plan(dt, d, k)
+        assert bk % 16 == 0 and 16 <= bk <= 256
+        assert (nb - 1) * bk < k <= nb * bk
+    assert sil.tensor_plan(torch.float32, 256, 100) is None  # d > 128: SIMT only
+
+
+def test_tensor_plan_rejects_bad_arguments(lib):
+    out = ctypes.c_int32(0)
+    assert lib.sil_tensor_plan(0, 64, 100, None, ctypes.byref(out)) == sil.SIL_EINVAL
+    assert lib.sil_tensor_plan(7, 64, 100, ctypes.byref(out), ctypes.byref(out)) == sil.SIL_EINVAL
+    assert lib.sil_tensor_plan(0, 64, 0, ctypes.byref(out), ctypes.byref(out)) == sil.SIL_EINVAL

@@ -1,9 +1,11 @@
 """Parity of the tcgen05 tensor-core pass 2 with the FP64 oracle.
 
 FP32 storage runs the in-kernel BF16 hi/lo split (three MMAs per k-step),
-BF16 storage runs two; both must meet the FP32 tolerances of the SIMT path.
-Sizes cover one and two 64-wide K atoms, padded D, K from 2 to 256 (MMA N up
-to 256, both TMEM accumulators), ragged last tiles and multi-tile CTAs.
+BF16 storage runs two, FP8 storage (d = 128, per-column scales folded into
+the centroids) runs two on the widened codes; all must meet the FP32
+tolerances of the SIMT path.  Sizes cover one and two 64-wide K atoms, padded
+D, K from 2 to 1000 (one cluster block of up to 256, and several blocks whose
+per-block minima are combined), ragged last tiles and multi-tile CTAs.
 """
 import numpy as np
 import pytest
@@ -17,10 +19,10 @@ pytestmark = pytest.mark.gpu
 METRICS = ["sqeuclidean", "cosine"]
 
 
-def run(Xt, lt, K, metric, path, save=True):
+def run(Xt, lt, K, metric, path, save=True, cs=None):
     st = sil.new_status(Xt.device)
-    agg = sil.aggregate(Xt, lt, K, metric, status=st)
-    r = sil.score(Xt, lt, K, agg, metric, want_s=True, save=save, path=path, status=st)
+    agg = sil.aggregate(Xt, lt, K, metric, col_scale=cs, status=st)
+    r = sil.score(Xt, lt, K, agg, metric, col_scale=cs, want_s=True, save=save, path=path, status=st)
     torch.cuda.synchronize()
     return r, int(st.item())
 
@@ -29,7 +31,8 @@ def run(Xt, lt, K, metric, path, save=True):
 @pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16])
 @pytest.mark.parametrize("N,D,K", [(1000, 64, 2), (4097, 64, 7), (20000, 64, 100), (3001, 128, 17),
                                    (5000, 100, 33), (2000, 40, 5), (300, 64, 256), (129, 64, 3),
-                                   (700, 128, 128)])
+                                   (700, 128, 128), (700, 128, 256), (3000, 64, 300),
+                                   (2500, 128, 700), (1500, 64, 1000)])
 def test_tensor_path_against_bruteforce(metric, dtype, N, D, K):
     if dtype == torch.bfloat16 and (D < 64 or (2 * D) % 16):
         pytest.skip("BF16 tensor path needs d >= 64 and 16-byte rows (TMA)")
@@ -78,16 +81,98 @@ def test_auto_picks_tensor_when_eligible():
     assert torch.equal(ra.s, rt.s)  # same aggregates, same kernel: bit-identical
 
 
-def test_tensor_refuses_shapes_beyond_shared_memory():
-    # FP32, d = 128, k = 256: split centroids + one A buffer + one raw stage > 227 KB
-    X, lab = case(7, 300, 128, 256)
+@pytest.mark.parametrize("metric", METRICS)
+@pytest.mark.parametrize("N,K", [(1000, 5), (4097, 100), (3000, 300), (2000, 1000)])
+def test_fp8_tensor_path_against_bruteforce(metric, N, K):
+    X, lab = case(900 + N + K, N, 128, K, metric)
+    q, scale = synth.to_fp8_e4m3(torch.as_tensor(X))
+    Xt, lt, cs = q.cuda(), torch.as_tensor(lab).cuda(), scale.cuda()
+    r, st = run(Xt, lt, K, metric, "tensor", cs=cs)
+    ref = oracle.bruteforce(dequant(Xt, cs), lab, K, metric)
+    assert st == 0
+    assert_scores(r.s, r.S, ref, what=f"fp8 tensor {metric} N={N} K={K}")
+    a, b, ks = sil.unpack_saved(r.saved, N)
+    ok = ref["s"] != 0
+    np.testing.assert_allclose(b.cpu().double().numpy()[ok], ref["b"][ok], rtol=1e-4, atol=1e-4)
+    assert np.mean(ks.cpu().numpy()[ok] == ref["kstar"][ok]) > 0.995
+
+
+@pytest.mark.parametrize("storage", ["bf16", "fp8"])
+def test_precision_recipe_subsample(storage):
+    # the precision workload's recipe (centres at radius 1e3, d = 128,
+    # k = 1000) at reduced n; s_i of 20,000 seeded rows against the FP64
+    # linear form with full-n FP64 aggregates of the stored values
+    w = synth.workload_precision(device="cuda", N=200_000)
+    cs = None
+    if storage == "bf16":
+        Xt = synth.to_bf16(w.X)
+    else:
+        Xt, cs = synth.to_fp8_e4m3(w.X)
+    lt = w.labels
+    r, st = run(Xt, lt, w.K, "sqeuclidean", "tensor", save=False, cs=cs)
+    assert st == 0
+    X64, lab = dequant(Xt, cs), lt.cpu().numpy()
+    full = oracle.linear(X64, lab, w.K)
+    idx = np.sort(np.random.default_rng(2026).choice(Xt.shape[0], 20_000, replace=False))
+    sub = oracle.linear(X64, lab, w.K, agg=full["agg"], idx=idx)
+    s = r.s.cpu().double().numpy()
+    assert float(np.abs(s[idx] - sub["s"]).max()) <= TOL_SI
+    assert float(np.abs(s - full["s"]).max()) <= TOL_SI
+    # the bound stated for the low-precision storage forms
+    assert abs(float(r.S) - full["S"]) <= 1e-4
+
+
+@pytest.mark.parametrize("storage", ["bf16", "fp8"])
+def test_precision_workload_full_size_sampled(storage):
+    # the full precision workload (n = 1e8, d = 128, k = 1000, radius 1e3) in
+    # the launch configuration the benchmark times; s_i of 20,000 seeded rows
+    # against the FP64 linear form with FP64 aggregates of all 1e8 stored rows
+    w = synth.workload_precision(device="cuda")
+    if storage == "bf16":
+        Xt, cs = synth.to_bf16(w.X), None
+    else:
+        Xt, cs = synth.to_fp8_e4m3(w.X)
+    lt, K, N = w.labels, w.K, Xt.shape[0]
+    del w  # the FP32 copy (51 GB) is no longer needed
+    torch.cuda.empty_cache()
+    r, st = run(Xt, lt, K, "sqeuclidean", "auto", save=False, cs=cs)
+    assert st == 0
+    s_gpu, S_gpu = r.s.cpu().double().numpy(), float(r.S)
+    del r
+    count = np.zeros(K, np.int64)
+    s1 = np.zeros((K, 128), np.float64)
+    s2 = np.zeros(K, np.float64)
+    step = 4_000_000
+    for lo in range(0, N, step):
+        hi = min(N, lo + step)
+        part = oracle.aggregate(dequant(Xt[lo:hi], cs), lt[lo:hi].cpu().numpy(), K)
+        count += part[0]
+        s1 += part[1]
+        s2 += part[2]
+    idx = np.sort(np.random.default_rng(2027).choice(N, 20_000, replace=False))
+    it = torch.as_tensor(idx, device="cuda")
+    sub = oracle.linear(dequant(Xt[it], cs), lt[it].cpu().numpy(), K, agg=(count, s1, s2),
+                        idx=np.arange(idx.shape[0]))
+    assert sub["status"] == oracle.OK
+    assert float(np.abs(s_gpu[idx] - sub["s"]).max()) <= TOL_SI
+    # S is the FP64 mean of the s_i the kernel wrote ...
+    assert abs(S_gpu - float(np.mean(s_gpu))) <= 1e-6
+    # ... and the oracle's sample mean estimates it to within its standard error
+    se = float(np.std(sub["s"])) / np.sqrt(idx.shape[0])
+    assert abs(S_gpu - sub["S"]) <= 1e-4 + 5 * se
+
+
+def test_fp32_d128_k256_uses_two_cluster_blocks():
+    # split centroids for 256 clusters, two A buffers and a raw stage exceed
+    # shared memory, so the tensor path runs two blocks of 128 clusters
+    X, lab = case(7, 3000, 128, 256)
     Xt, lt = to_dev(X, lab)
     agg = sil.aggregate(Xt, lt, 256)
-    with pytest.raises(sil.SilError):
-        sil.score(Xt, lt, 256, agg, path="tensor")
-    r = sil.score(Xt, lt, 256, agg, want_s=True, path="auto")  # falls back to SIMT
+    rt = sil.score(Xt, lt, 256, agg, want_s=True, path="tensor")
+    rs = sil.score(Xt, lt, 256, agg, want_s=True, path="simt")
     torch.cuda.synchronize()
-    assert np.isfinite(float(r.S))
+    assert float((rt.s - rs.s).abs().max()) <= TOL_SI
+    assert abs(float(rt.S) - float(rs.S)) <= TOL_S
 
 
 def test_tensor_refuses_ineligible_shapes():
