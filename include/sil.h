@@ -45,6 +45,8 @@
  *     trap or assert.
  *   - ws is a device workspace of at least sil_workspace_size(...) bytes,
  *     256-byte aligned.  Its contents are scratch between calls.
+ *   - n < 2^31 (pass 1 sorts 32-bit row indices); larger n returns
+ *     SIL_EUNSUPPORTED.
  */
 #ifndef SIL_H_
 #define SIL_H_
@@ -108,8 +110,10 @@ size_t sil_saved_size(int64_t n);
  * several calls on disjoint row ranges can be merged by adding them (the
  * per-worker partial sums of the paper's distributed form); with
  * SIL_AGG_ACCUMULATE the call adds into the outputs instead of overwriting
- * them.  Inside a kernel, partial sums are formed in FP32 on values shifted
- * by a per-cluster reference point and folded into FP64 once per block.
+ * them.  The rows are first counting-sorted by label (inside the
+ * workspace); each warp then sums a run of one cluster's rows in FP32 on
+ * values shifted by a per-cluster reference point and folds the run into
+ * FP64 once.
  */
 int sil_aggregate(const void* X, int32_t dtype, int64_t n, int32_t d, int64_t ldx,
                   const float* col_scale, const int32_t* labels, int32_t k, int32_t dist,

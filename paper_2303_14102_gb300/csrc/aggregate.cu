@@ -1,32 +1,46 @@
 // Pass 1: the segmented per-cluster reduction (Sec. III-A Eq. 5-9 with the
 // footnote that Y and Psi come from one joint pass; Sec. III-B Eq. 15-16).
 //
-// Design (GB300): the reduction is HBM-bound -- one read of X and labels --
-// so the kernel is SIMT, with no tensor-core reshaping.  A CTA owns a
-// contiguous row range and a column slice (and, for very many clusters, a
-// bucket slice).  Rows are staged in shared memory one tile of 128 rows at a
-// time -- by TMA (cp.async.bulk.tensor) into a ring of stages that runs ahead
-// of the computation, or, when the layout does not allow a tensor map, by
-// synchronous coalesced 128-bit loads; the tile's labels are counting-sorted in
-// shared memory (integer shared atomics only) so that every (cluster, 4-column
-// chunk) pair present in the tile is summed by ONE thread in registers and
-// added once into a per-CTA FP32 accumulator in shared memory -- no float
-// atomics, no warp-divergent scatter.  Values are accumulated shifted by a
-// per-cluster reference point r_k (a point of that cluster), which keeps the
-// FP32 partials well conditioned even when clusters sit far from the origin;
-// the partials are un-shifted and folded into the FP64 outputs once per CTA:
+// Design (GB300): the reduction is HBM-bound -- one read of X and the labels
+// -- so it is SIMT work whose only job is to stream X at full bandwidth with
+// as few instructions per byte as possible.  A per-tile sort of the labels
+// costs the same whatever K is, and with many clusters almost every row of a
+// tile is its own segment; so the rows are counting-sorted by cluster ONCE,
+// on the labels alone (4 bytes a row), and the reduction then walks the
+// sorted order:
+//   1. k_bucket_count    histogram of the labels (privatised in shared memory)
+//   2. k_bucket_scan     exclusive scan -> bucket starts; the int64 counts
+//   3. k_bucket_scatter  row indices (and weights) in bucket order; each CTA
+//                        reserves one contiguous range per bucket it touches
+//   4. k_gather_reduce   every warp takes a contiguous run of the sorted
+//                        order; its lanes read whole rows with 16-byte loads
+//                        (a row is one contiguous burst, so DRAM sees full
+//                        sectors whatever the order of the rows), sum x - r_k
+//                        in FP32 registers while the bucket stays the same,
+//                        and add into the FP64 outputs once per run.
+// Values are accumulated shifted by a per-cluster reference point r_k (the
+// first row of cluster k among the first 65,536 rows), which keeps the FP32
+// partials well conditioned when clusters sit far from the origin; a run's
+// sums are un-shifted in FP64 when they are added:
 //   s1 += sum(x - r) + m r,   s2 += sum||x - r||^2 + 2 r.sum(x - r) + m ||r||^2.
-// The same kernel, with per-row weights and two bucket entries per row, forms
-// the segmented sums of the backward pass.
+// The same kernels, with per-row weights and two bucket entries per row
+// (bucket c_i and bucket k + k*_i), form the segmented sums of the backward
+// pass; those are left shifted (sum w (x - r_c), with the shift of cluster c
+// for both of its buckets) and come with sum w per bucket.
 #include <climits>
 #include <cstdlib>
 
 #include "sil_internal.cuh"
-#include "tma.cuh"
 
 namespace sil {
 
 namespace {
+
+constexpr int kHistSmem = 12288;    // buckets privatised in shared memory by the count kernel
+constexpr int kScatterSmem = 4096;  // buckets privatised by the scatter kernel
+constexpr int kScatterIPT = 16;     // entries per thread of the scatter kernel
+constexpr int kScanThreads = 1024;
+constexpr int kGatherThreads = 256;
 
 __global__ void k_rep_init(int32_t* rep, int32_t k) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -106,599 +120,413 @@ __global__ void k_invnorm(const void* X, int64_t n, int32_t d, int64_t ldx, cons
   }
 }
 
-struct AggK {
-  const void* X;
+// ------------------------------------------------------------ bucket sort
+// Entry e < n is row e in bucket labels[e]; in dual mode entry n + i is row i
+// in bucket k + labels2[i] (labels2[i] = -1: no second entry).
+struct Entries {
   int64_t n;
-  int32_t d;
-  int64_t ldx;
-  const float* cs;
+  int32_t k;
   const int32_t* lab1;
   const int32_t* lab2;
   const float* w1;
   const float* w2;
+  uint32_t* status;
+  __device__ __forceinline__ int bucket(int64_t e, bool report) const {
+    if (e < n) {
+      const int l = lab1[e];
+      if (l >= 0 && l < k) return l;
+      if (report) set_status(status, SIL_ELABEL);
+      return -1;
+    }
+    const int l = lab2[e - n];
+    if (l >= 0 && l < k) return k + l;
+    if (report && l != -1) set_status(status, SIL_ELABEL);
+    return -1;
+  }
+  __device__ __forceinline__ uint32_t row(int64_t e) const { return uint32_t(e < n ? e : e - n); }
+  __device__ __forceinline__ float weight(int64_t e) const { return e < n ? w1[e] : w2[e - n]; }
+};
+
+// Lanes with the same bucket reserve consecutive slots with one atomic on
+// that bucket's counter; returns this lane's slot (the counter's old value
+// plus the lane's rank among its peers).  b < 0: no slot.
+__device__ __forceinline__ unsigned warp_reserve(int b, unsigned* counter_of_b) {
+  const int lane = threadIdx.x & 31;
+  const unsigned peers = __match_any_sync(0xffffffffu, b);
+  const int leader = __ffs(peers) - 1;
+  unsigned old = 0;
+  if (b >= 0 && lane == leader) old = atomicAdd(counter_of_b, unsigned(__popc(peers)));
+  old = __shfl_sync(0xffffffffu, old, leader);
+  return old + unsigned(__popc(peers & ((1u << lane) - 1u)));
+}
+
+__global__ void __launch_bounds__(256) k_bucket_count(Entries en, int64_t E, int32_t nb, uint32_t* bcount) {
+  extern __shared__ uint32_t hist[];
+  const bool priv = nb <= kHistSmem;
+  if (priv)
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) hist[b] = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  // the loop bound is uniform per warp, so every lane reaches the warp collectives
+  for (int64_t base = int64_t(blockIdx.x) * blockDim.x + threadIdx.x - lane; base < E; base += stride) {
+    const int64_t e = base + lane;
+    const int b = e < E ? en.bucket(e, true) : -1;
+    unsigned* ctr = b >= 0 ? (priv ? &hist[b] : &bcount[b]) : nullptr;
+    warp_reserve(b, ctr);
+  }
+  if (priv) {
+    __syncthreads();
+    for (int b = threadIdx.x; b < nb; b += blockDim.x)
+      if (hist[b]) atomicAdd(&bcount[b], hist[b]);
+  }
+}
+
+// One CTA: bstart[b] = sum of bcount[< b], bstart[nb] = total, cursor = bstart;
+// count_out[b] += bcount[b] for the first k buckets when count_out is given.
+__global__ void __launch_bounds__(kScanThreads) k_bucket_scan(const uint32_t* bcount, int32_t nb, int32_t k,
+                                                              uint32_t* bstart, uint32_t* cursor,
+                                                              unsigned long long* count_out) {
+  __shared__ uint32_t wsum[kScanThreads / 32];
+  __shared__ uint32_t carry;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid == 0) carry = 0;
+  __syncthreads();
+  for (int b0 = 0; b0 < nb; b0 += kScanThreads) {
+    const int b = b0 + tid;
+    const uint32_t c = b < nb ? bcount[b] : 0u;
+    if (count_out && b < k) count_out[b] += c;
+    uint32_t incl = c;
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += t;
+    }
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    uint32_t off = carry;
+    for (int w = 0; w < warp; ++w) off += wsum[w];
+    if (b < nb) {
+      bstart[b] = off + incl - c;
+      cursor[b] = off + incl - c;
+    }
+    __syncthreads();
+    if (tid == kScanThreads - 1) carry = off + incl;
+    __syncthreads();
+  }
+  if (tid == 0) bstart[nb] = carry;
+}
+
+// Each CTA places kScatterIPT * 256 consecutive entries.  With few buckets it
+// counts them in shared memory first and reserves one range per bucket with
+// a single global atomic (the hot buckets of skewed size distributions would
+// otherwise serialise on their cursor).
+__global__ void __launch_bounds__(256) k_bucket_scatter(Entries en, int64_t E, int32_t nb, uint32_t* cursor,
+                                                         uint32_t* idx, float* widx) {
+  __shared__ uint32_t lh[kScatterSmem];
+  __shared__ uint32_t lbase[kScatterSmem];
+  const bool priv = nb <= kScatterSmem;
+  const int tid = threadIdx.x;
+  const int64_t c0 = int64_t(blockIdx.x) * (256 * kScatterIPT);
+  if (!priv) {
+    for (int i = 0; i < kScatterIPT; ++i) {
+      const int64_t e = c0 + int64_t(i) * 256 + tid;
+      const int b = e < E ? en.bucket(e, false) : -1;
+      const unsigned pos = warp_reserve(b, b >= 0 ? &cursor[b] : nullptr);
+      if (b >= 0) {
+        idx[pos] = en.row(e);
+        if (widx) widx[pos] = en.weight(e);
+      }
+    }
+    return;
+  }
+  for (int b = tid; b < nb; b += 256) lh[b] = 0;
+  __syncthreads();
+  int bk[kScatterIPT];
+  unsigned rk[kScatterIPT];
+#pragma unroll
+  for (int i = 0; i < kScatterIPT; ++i) {
+    const int64_t e = c0 + int64_t(i) * 256 + tid;
+    bk[i] = e < E ? en.bucket(e, false) : -1;
+    rk[i] = warp_reserve(bk[i], bk[i] >= 0 ? &lh[bk[i]] : nullptr);
+  }
+  __syncthreads();
+  for (int b = tid; b < nb; b += 256) {
+    const uint32_t c = lh[b];
+    if (c) lbase[b] = atomicAdd(&cursor[b], c);
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < kScatterIPT; ++i) {
+    if (bk[i] < 0) continue;
+    const int64_t e = c0 + int64_t(i) * 256 + tid;
+    const uint32_t pos = lbase[bk[i]] + rk[i];
+    idx[pos] = en.row(e);
+    if (widx) widx[pos] = en.weight(e);
+  }
+}
+
+// --------------------------------------------------------- gather-reduce
+struct GatherK {
+  const unsigned char* X;
+  int64_t n;
+  int32_t d;
+  int64_t ldx_bytes;
+  const float* cs;
   int32_t k;
-  int32_t kb;  // total buckets: k, or 2k in dual mode
-  int32_t cosine;
-  int32_t vec;
-  const float* rs;
+  int32_t nb;
   int32_t dz;
-  const float* invnorm;
-  int32_t dsp;    // columns per slice (multiple of 4)
-  int32_t nslc;   // column slices
-  int32_t kbs;    // buckets per bucket slice
-  int64_t rows_per_cta;
-  int32_t stages;      // TMA kernel: pipeline depth
-  int32_t stage_bytes; // TMA kernel: bytes of one stage
-  unsigned long long* count;
+  const uint32_t* idx;
+  const float* widx;  // weights in sorted order (weighted mode), else null
+  const uint32_t* bstart;
+  const float* rs;
+  const float* invnorm;  // 1/||x|| per row (cosine with column slices), else null
+  int32_t cosine;
+  int32_t vec;  // 16-byte loads allowed (X and the row stride 16-byte aligned)
+  int32_t G;    // lanes per row (power of two)
+  int32_t lgG;
+  int32_t nch;       // 16-byte chunks in a row (whole row)
+  int32_t ch_slice;  // chunks per column slice (= G * CPL, or fewer in the last)
+  int64_t wchunk;    // sorted entries per warp work item
+  int64_t nitems;
   double* s1;
   double* s2;
   double* wsum;
   uint32_t* status;
 };
 
-// Tensor maps of the TMA-fed kernel (X tile, labels, second labels, weights).
-struct AggMaps {
-  CUtensorMap x, lab1, lab2, w1, w2;
-};
-
-// Byte offsets of the per-CTA shared state (the part both kernels share).
-struct AggSmem {
-  int acc, acc2, macc, mint, cnt, slot, ebk, epos, ew, order, nel, bstart, bsize, segq, inv, wtot, nne,
-      total;
-};
-
-constexpr int kSeg = 8;  // rows per accumulation segment
-
-__host__ __device__ inline AggSmem agg_smem(int dsp, int kbs, bool dual, bool weighted) {
-  const int R = kAggRows, E = dual ? 2 * R : R, c4 = dsp / 4;
-  AggSmem s;
-  int o = 0;
-  s.acc = o; o += kbs * dsp * 4;
-  s.acc2 = o; o += weighted ? 0 : kbs * c4 * 4;
-  s.macc = o; o += kbs * 4;
-  s.mint = o; o += kbs * 4;
-  s.cnt = o; o += kbs * 4;
-  s.slot = o; o += kbs * 4;
-  s.ebk = o; o += E * 4;
-  s.epos = o; o += E * 4;
-  s.ew = o; o += E * 4;
-  s.order = o; o += E * 4;
-  s.nel = o; o += E * 4;
-  s.bstart = o; o += (E + 1) * 4;
-  s.bsize = o; o += E * 4;
-  s.segq = o; o += (E + E / kSeg + 1) * 4;
-  s.inv = o; o += R * 4;
-  s.wtot = o; o += 32 * 4;
-  s.nne = o; o += 16;
-  s.total = (o + 127) & ~127;
-  return s;
-}
-
-struct AggState {
-  float* acc;
-  float4* acc4;
-  float* acc2;
-  float* macc;
-  int* mint;
-  int* cnt;
-  int* slot;
-  int* ebk;
-  int* epos;
-  float* ew;
-  int* order;
-  int* nel;
-  int* bstart;
-  int* bsize;
-  int* segq;  // segment -> (bucket position << 8 | segment index)
-  float* inv;
-  int* wtot;
-  int* nne;  // [0] = non-empty bucket count (being built), [1] = abort flag, [2] = count of this tile
-};
-
-__device__ inline AggState agg_state(unsigned char* smem, const AggSmem& L) {
-  AggState S;
-  S.acc = reinterpret_cast<float*>(smem + L.acc);
-  S.acc4 = reinterpret_cast<float4*>(smem + L.acc);
-  S.acc2 = reinterpret_cast<float*>(smem + L.acc2);
-  S.macc = reinterpret_cast<float*>(smem + L.macc);
-  S.mint = reinterpret_cast<int*>(smem + L.mint);
-  S.cnt = reinterpret_cast<int*>(smem + L.cnt);
-  S.slot = reinterpret_cast<int*>(smem + L.slot);
-  S.ebk = reinterpret_cast<int*>(smem + L.ebk);
-  S.epos = reinterpret_cast<int*>(smem + L.epos);
-  S.ew = reinterpret_cast<float*>(smem + L.ew);
-  S.order = reinterpret_cast<int*>(smem + L.order);
-  S.nel = reinterpret_cast<int*>(smem + L.nel);
-  S.bstart = reinterpret_cast<int*>(smem + L.bstart);
-  S.bsize = reinterpret_cast<int*>(smem + L.bsize);
-  S.segq = reinterpret_cast<int*>(smem + L.segq);
-  S.inv = reinterpret_cast<float*>(smem + L.inv);
-  S.wtot = reinterpret_cast<int*>(smem + L.wtot);
-  S.nne = reinterpret_cast<int*>(smem + L.nne);
-  return S;
-}
-
-// Geometry of one CTA's work item.
-struct AggItem {
-  int cslice, col0, dlim, c4, c4e, kb0, kbn;
-  int64_t row_begin, row_end;
-};
-
-__device__ inline AggItem agg_item(const AggK& a) {
-  AggItem it;
-  it.cslice = blockIdx.x % a.nslc;
-  const int kslice = blockIdx.x / a.nslc;
-  it.col0 = it.cslice * a.dsp;
-  it.dlim = min(a.d, it.col0 + a.dsp);  // columns of this slice are [col0, dlim)
-  it.c4 = a.dsp / 4;
-  it.c4e = int(cdiv(it.dlim - it.col0, 4));  // chunks holding columns < dlim
-  it.kb0 = kslice * a.kbs;
-  it.kbn = min(a.kbs, a.kb - it.kb0);  // buckets of this slice
-  it.row_begin = int64_t(blockIdx.y) * a.rows_per_cta;
-  it.row_end = min(a.n, it.row_begin + a.rows_per_cta);
-  return it;
-}
-
-__device__ inline void agg_zero(const AggState& S, const AggItem& it, int dsp, bool weighted) {
-  const int tid = threadIdx.x, T = blockDim.x;
-  for (int i = tid; i < it.kbn * dsp; i += T) S.acc[i] = 0.f;
-  if (!weighted)
-    for (int i = tid; i < it.kbn * it.c4; i += T) S.acc2[i] = 0.f;
-  for (int i = tid; i < it.kbn; i += T) {
-    S.macc[i] = 0.f;
-    S.mint[i] = 0;
-    S.cnt[i] = 0;
-  }
-  if (tid == 0) {
-    S.nne[0] = 0;
-    S.nne[1] = 0;
-  }
-}
-
-// Tile source of the generic kernel: FP32 rows already in shared memory,
-// labels and weights read from global memory.
-struct SrcGeneric {
-  const float4* xs4;
-  int c4;
-  const int32_t* lab1;
-  const int32_t* lab2;
-  const float* w1;
-  const float* w2;
-  int64_t r0;
-  __device__ float4 chunk(int r, int c) const { return xs4[r * c4 + c]; }
-  __device__ int label1(int r) const { return lab1[r0 + r]; }
-  __device__ int label2(int r) const { return lab2[r0 + r]; }
-  __device__ float weight1(int r) const { return w1[r0 + r]; }
-  __device__ float weight2(int r) const { return w2[r0 + r]; }
-};
-
-// Tile source of the TMA kernel: raw storage rows, labels and weights all in
-// one pipeline stage of shared memory.
 template <int DT>
-struct SrcTma {
-  using T = typename Elem<DT>::T;
-  const T* xs;
-  int dsp;
-  const int32_t* lab1;
-  const int32_t* lab2;
-  const float* w1;
-  const float* w2;
-  const float* cs;
-  int col0, dlim;
-  __device__ float4 chunk(int r, int c) const {
-    const T* p = xs + r * dsp + 4 * c;
-    float4 v;
-    if constexpr (DT == SIL_F32) {
-      v = *reinterpret_cast<const float4*>(p);
-    } else if constexpr (DT == SIL_BF16) {
-      const uint2 u = *reinterpret_cast<const uint2*>(p);
-      const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u.x));
-      const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u.y));
-      v = make_float4(a.x, a.y, b.x, b.y);
-    } else {
-      const uint32_t u = *reinterpret_cast<const uint32_t*>(p);
-      const __nv_fp8_e4m3* q = reinterpret_cast<const __nv_fp8_e4m3*>(&u);
-      v = make_float4(float(q[0]), float(q[1]), float(q[2]), float(q[3]));
-      const int col = col0 + 4 * c;
-      v.x *= col + 0 < dlim ? __ldg(cs + col + 0) : 0.f;
-      v.y *= col + 1 < dlim ? __ldg(cs + col + 1) : 0.f;
-      v.z *= col + 2 < dlim ? __ldg(cs + col + 2) : 0.f;
-      v.w *= col + 3 < dlim ? __ldg(cs + col + 3) : 0.f;
-    }
-    return v;
+struct Chunk;
+template <>
+struct Chunk<SIL_F32> {
+  static constexpr int Q = 4;
+  static __device__ __forceinline__ void cvt(const uint4& u, float* v) {
+    v[0] = __uint_as_float(u.x);
+    v[1] = __uint_as_float(u.y);
+    v[2] = __uint_as_float(u.z);
+    v[3] = __uint_as_float(u.w);
   }
-  __device__ int label1(int r) const { return lab1[r]; }
-  __device__ int label2(int r) const { return lab2[r]; }
-  __device__ float weight1(int r) const { return w1[r]; }
-  __device__ float weight2(int r) const { return w2[r]; }
+};
+template <>
+struct Chunk<SIL_BF16> {
+  static constexpr int Q = 8;
+  static __device__ __forceinline__ void cvt(const uint4& u, float* v) {
+    const uint32_t w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&w[i]));
+      v[2 * i] = f.x;
+      v[2 * i + 1] = f.y;
+    }
+  }
+};
+template <>
+struct Chunk<SIL_FP8_E4M3> {
+  static constexpr int Q = 16;
+  static __device__ __forceinline__ void cvt(const uint4& u, float* v) {
+    const uint32_t w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const __half2_raw hr =
+            __nv_cvt_fp8x2_to_halfraw2(__nv_fp8x2_storage_t((w[i] >> (16 * h)) & 0xFFFFu), __NV_E4M3);
+        const float2 f = __half22float2(__half2(hr));
+        v[4 * i + 2 * h] = f.x;
+        v[4 * i + 2 * h + 1] = f.y;
+      }
+    }
+  }
 };
 
-// One 128-row tile: bucket the rows by label (counting sort in shared memory),
-// then one thread per (non-empty bucket, 4-column chunk) sums the bucket's
-// rows in registers and adds the result once into the CTA accumulator.
-// Counters are reset inside; the caller syncs before the next tile (and
-// before its staging buffer is refilled).
-template <bool DUAL, bool WEIGHTED, class Src>
-__device__ int agg_sort(const AggK& a, const AggState& S, const AggItem& it, const Src& src,
-                        int rows, int64_t r0) {
-  constexpr int R = kAggRows, T = kAggThreads, E = DUAL ? 2 * R : R;
-  const int tid = threadIdx.x;
-  const bool in_cta_norm = a.cosine && a.invnorm == nullptr;  // full rows are in this tile
-  // (b) bucket entries and row scales
-  for (int e = tid; e < E; e += T) {
-    const int r = e < R ? e : e - R;
-    int lb = -1;
-    float w = 1.f;
-    if (r < rows) {
-      const int lab = (e < R) ? src.label1(r) : src.label2(r);
-      if (lab >= 0 && lab < a.k) {
-        const int bucket = (e < R) ? lab : a.k + lab;
-        if (bucket >= it.kb0 && bucket < it.kb0 + it.kbn) lb = bucket - it.kb0;
-        if (WEIGHTED) w = (e < R) ? src.weight1(r) : src.weight2(r);
-      } else if (e < R || lab != -1) {
-        // a label outside [0, k); -1 marks "no neighbour" in the second entry
-        set_status(a.status, SIL_ELABEL);
-      }
-    }
-    // one shared atomic per distinct bucket per warp: lanes with the same
-    // bucket rank themselves inside the warp and the lowest one reserves
-    // positions for all of them
-    const unsigned peers = __match_any_sync(0xffffffffu, lb);
-    const int leader = __ffs(peers) - 1;
-    const int lane = tid & 31;
-    int p = 0;
-    if (lb >= 0 && lane == leader) {
-      p = atomicAdd(&S.cnt[lb], __popc(peers));
-      if (p == 0) {
-        const int q = atomicAdd(&S.nne[0], 1);
-        S.nel[q] = lb;
-        S.slot[lb] = q;
-      }
-    }
-    p = __shfl_sync(0xffffffffu, p, leader);
-    if (lb >= 0) S.epos[e] = p + __popc(peers & ((1u << lane) - 1u));
-    S.ebk[e] = lb;
-    S.ew[e] = w;
-  }
-  if (a.cosine) {
-    if (in_cta_norm) {
-      const int warp = tid >> 5, lane = tid & 31;
-      for (int r = warp; r < R; r += T / 32) {
-        float ss = 0.f;
-        for (int c = lane; c < it.c4e; c += 32) {
-          const float4 v = src.chunk(r, c);
-          ss += v.x * v.x + v.y * v.y + v.z * v.z + v.w * v.w;
-        }
-        for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
-        if (lane == 0) {
-          if (r < rows && !(ss > 0.f)) set_status(a.status, SIL_EZERONORM);
-          S.inv[r] = ss > 0.f ? rsqrtf(ss) : 0.f;
-        }
-      }
-    } else {
-      for (int r = tid; r < R; r += T) S.inv[r] = r < rows ? a.invnorm[r0 + r] : 0.f;
-    }
-  }
-  __syncthreads();
-  // (c) block-wide exclusive scan over the non-empty buckets (one thread per
-  // bucket, m <= E <= T), of the packed pair (rows << 16 | segments of kSeg
-  // rows); it also writes the segment -> bucket table and resets the counters
-  const int m = S.nne[0];
-  {
-    const int warp = tid >> 5, lane = tid & 31;
-    const int c = tid < m ? S.cnt[S.nel[tid]] : 0;
-    const int v = (c << 16) | ((c + kSeg - 1) / kSeg);
-    int incl = v;
-    for (int o = 1; o < 32; o <<= 1) {
-      const int t = __shfl_up_sync(0xffffffffu, incl, o);
-      if (lane >= o) incl += t;
-    }
-    if (lane == 31) S.wtot[warp] = incl;
-    __syncthreads();
-    int off = 0;
-    for (int w = 0; w < warp; ++w) off += S.wtot[w];
-    const int ex = off + incl - v;
-    if (tid < m) {
-      const int lb = S.nel[tid];
-      S.bstart[tid] = ex >> 16;
-      S.bsize[tid] = c;
-      S.cnt[lb] = 0;
-      const int s0 = ex & 0xFFFF, ns = v & 0xFFFF;
-      for (int sg = 0; sg < ns; ++sg) S.segq[s0 + sg] = (tid << 8) | sg;
-    }
-    if (tid == T - 1) S.nne[2] = (off + incl) & 0xFFFF;  // total number of segments
-  }
-  __syncthreads();
-  if (tid == 0) S.nne[0] = 0;  // everybody has read m
-  // (d) scatter entries into bucket order
-  for (int e = tid; e < E; e += T) {
-    const int lb = S.ebk[e];
-    if (lb >= 0) S.order[S.bstart[S.slot[lb]] + S.epos[e]] = e;
-  }
-  __syncthreads();
-  return S.nne[2];  // segments of at most kSeg rows over the non-empty buckets
-}
-
-// Accumulation into the per-CTA shared accumulators: one thread per
-// (non-empty bucket, 4-column chunk of this slice).
-template <bool DUAL, bool WEIGHTED, class Src>
-__device__ void agg_tile(const AggK& a, const AggState& S, const AggItem& it, const Src& src,
-                         int rows, int64_t r0) {
-  constexpr int R = kAggRows, T = kAggThreads;
-  const int tid = threadIdx.x;
-  const int nseg = agg_sort<DUAL, WEIGHTED>(a, S, it, src, rows, r0);
-  // one thread per (segment of at most kSeg rows of one bucket, 4-column
-  // chunk): short independent chains; the segments of a bucket longer than
-  // kSeg rows meet in shared memory through float atomics
-  for (int p = tid; p < nseg * it.c4e; p += T) {
-    const int sidx = p / it.c4e, c = p - sidx * it.c4e;
-    const int sq_ = S.segq[sidx];
-    const int q = sq_ >> 8, sg = sq_ & 255;
-    const int lb = S.nel[q];
-    const int bg = it.kb0 + lb;
-    const int kc = bg < a.k ? bg : bg - a.k;  // cluster whose reference point shifts this bucket
-    const float4 rr =
-        *reinterpret_cast<const float4*>(a.rs + int64_t(kc) * a.dz + it.col0 + 4 * c);
-    float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
-    float sq = 0.f, wsum = 0.f;
-    const int size = S.bsize[q];
-    const int jb = S.bstart[q] + sg * kSeg;
-    const int je = min(S.bstart[q] + size, jb + kSeg);
-    int eidx[kSeg];
-#pragma unroll
-    for (int u = 0; u < kSeg; ++u) eidx[u] = S.order[min(jb + u, je - 1)];
-#pragma unroll
-    for (int u = 0; u < kSeg; ++u) {
-      if (jb + u >= je) break;
-      const int e = eidx[u];
-      const int r = DUAL ? (e < R ? e : e - R) : e;
-      const float4 x = src.chunk(r, c);
-      const float sc = a.cosine ? S.inv[r] : 1.f;
-      float4 v;
-      v.x = fmaf(sc, x.x, -rr.x);
-      v.y = fmaf(sc, x.y, -rr.y);
-      v.z = fmaf(sc, x.z, -rr.z);
-      v.w = fmaf(sc, x.w, -rr.w);
-      if (WEIGHTED) {
-        const float w = S.ew[e];
-        v.x *= w; v.y *= w; v.z *= w; v.w *= w;
-        wsum += w;
-      } else {
-        sq = fmaf(v.x, v.x, fmaf(v.y, v.y, fmaf(v.z, v.z, fmaf(v.w, v.w, sq))));
-      }
-      s.x += v.x; s.y += v.y; s.z += v.z; s.w += v.w;
-    }
-    float* accp = S.acc + (lb * it.c4 + c) * 4;
-    if (size <= kSeg) {  // the only segment of its bucket: plain read-modify-write
-      float4 t = S.acc4[lb * it.c4 + c];
-      t.x += s.x; t.y += s.y; t.z += s.z; t.w += s.w;
-      S.acc4[lb * it.c4 + c] = t;
-      if (!WEIGHTED) S.acc2[lb * it.c4 + c] += sq;
-      if (c == 0) {
-        S.mint[lb] += size;
-        if (WEIGHTED) S.macc[lb] += wsum;
-      }
-    } else {
-      atomicAdd(accp + 0, s.x);
-      atomicAdd(accp + 1, s.y);
-      atomicAdd(accp + 2, s.z);
-      atomicAdd(accp + 3, s.w);
-      if (!WEIGHTED) atomicAdd(S.acc2 + lb * it.c4 + c, sq);
-      if (c == 0) {
-        if (sg == 0) S.mint[lb] += size;
-        if (WEIGHTED) atomicAdd(S.macc + lb, wsum);
-      }
-    }
-  }
-}
-
-// Un-shift in FP64 and add the CTA's sums into the outputs.
-template <bool WEIGHTED>
-__device__ void agg_flush(const AggK& a, const AggState& S, const AggItem& it) {
-  const int tid = threadIdx.x, T = blockDim.x;
-  const int dsl = it.dlim - it.col0;
-  for (int i = tid; i < it.kbn * dsl; i += T) {
-    const int lb = i / dsl, col = i - lb * dsl;
-    const int mm = S.mint[lb];
-    if (mm == 0) continue;
-    const int kg = it.kb0 + lb;
-    double v = double(S.acc[lb * a.dsp + col]);
-    if (!WEIGHTED) v += double(mm) * double(a.rs[int64_t(kg) * a.dz + it.col0 + col]);
-    atomicAdd(a.s1 + int64_t(kg) * a.d + it.col0 + col, v);
-  }
-  for (int lb = tid; lb < it.kbn; lb += T) {
-    const int mm = S.mint[lb];
-    if (mm == 0) continue;
-    const int kg = it.kb0 + lb;
-    if (WEIGHTED) {
-      if (it.cslice == 0) atomicAdd(a.wsum + kg, double(S.macc[lb]));
-    } else {
-      double t = 0.0;
-      for (int c = 0; c < it.c4e; ++c) t += double(S.acc2[lb * it.c4 + c]);
-      for (int col = 0; col < dsl; ++col) {
-        const double r = a.rs[int64_t(kg) * a.dz + it.col0 + col];
-        t += 2.0 * r * double(S.acc[lb * a.dsp + col]) + double(mm) * r * r;
-      }
-      atomicAdd(a.s2 + kg, t);
-      if (it.cslice == 0) atomicAdd(a.count + kg, (unsigned long long)mm);
-    }
-  }
-}
-
-// Generic pass 1: synchronous coalesced loads (any alignment, any ldx).
-template <int DT, bool DUAL, bool WEIGHTED>
-__global__ void __launch_bounds__(kAggThreads) k_aggregate(AggK a) {
-  extern __shared__ __align__(128) unsigned char smem[];
-  constexpr int R = kAggRows, T = kAggThreads;
-  const int tid = threadIdx.x;
-  const AggSmem L = agg_smem(a.dsp, a.kbs, DUAL, WEIGHTED);
-  const AggState S = agg_state(smem, L);
-  float4* xs4 = reinterpret_cast<float4*>(smem + L.total);  // [R][dsp] FP32 tile
-  const AggItem it = agg_item(a);
-  agg_zero(S, it, a.dsp, WEIGHTED);
-  __syncthreads();
-  for (int64_t r0 = it.row_begin; r0 < it.row_end; r0 += R) {
-    const int rows = int((it.row_end - r0) < int64_t(R) ? (it.row_end - r0) : int64_t(R));
-    for (int q = tid; q < R * it.c4; q += T) {
-      const int r = q / it.c4, c = q - r * it.c4;
-      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (r < rows) v = load4<DT>(a.X, r0 + r, it.col0 + 4 * c, it.dlim, a.ldx, a.cs, a.vec);
-      xs4[q] = v;
-    }
-    __syncthreads();
-    const SrcGeneric src{xs4, it.c4, a.lab1, a.lab2, a.w1, a.w2, r0};
-    agg_tile<DUAL, WEIGHTED>(a, S, it, src, rows, r0);
-    __syncthreads();
-  }
-  agg_flush<WEIGHTED>(a, S, it);
-}
-
-// TMA-fed pass 1: a ring of `stages` shared-memory buffers filled by
-// cp.async.bulk.tensor (X tile, labels, weights) while earlier tiles are
-// processed.  Thread 0 refills a buffer as soon as every thread is done with
-// it.  Waits are bounded: on a timeout the CTA flags SIL_ETIMEOUT, waits
-// (bounded) for its own copies in flight and returns without flushing.
-template <int DT, bool DUAL, bool WEIGHTED>
-__global__ void __launch_bounds__(kAggThreads) k_aggregate_tma(AggK a, const __grid_constant__ AggMaps maps) {
-  extern __shared__ __align__(128) unsigned char smem[];
+// 16 bytes of row `row` starting at element `col` (chunk aligned); elements
+// at or past d read as 0.
+template <int DT>
+__device__ __forceinline__ uint4 load_chunk(const GatherK& a, uint32_t row, int col) {
   using T = typename Elem<DT>::T;
-  constexpr int R = kAggRows;
-  constexpr int esz = sizeof(T);
-  const int tid = threadIdx.x;
-  const AggSmem L = agg_smem(a.dsp, a.kbs, DUAL, WEIGHTED);
-  const AggState S = agg_state(smem, L);
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L.total);
-  unsigned char* stage0 = smem + L.total + 128;  // stage buffers, 128-byte aligned
-  const AggItem it = agg_item(a);
-  const int64_t nrows = it.row_end > it.row_begin ? it.row_end - it.row_begin : 0;
-  const int ntiles = int(cdiv(nrows, R));
-  const int xbytes = R * a.dsp * esz;
-  const int nvec = 1 + (DUAL ? 1 : 0) + (WEIGHTED ? (DUAL ? 2 : 1) : 0);
-  const uint32_t tx = uint32_t(xbytes + nvec * R * 4);
-
-  if (tid == 0) {
-    for (int s = 0; s < a.stages; ++s) mbar_init(&bars[s], 1);
-    fence_mbar_init();
-  }
-  agg_zero(S, it, a.dsp, WEIGHTED);
-  __syncthreads();
-
-  auto issue = [&](int t) {
-    const int s = t % a.stages;
-    unsigned char* buf = stage0 + s * a.stage_bytes;
-    const int32_t row = int32_t(it.row_begin + int64_t(t) * R);
-    mbar_arrive_expect_tx(&bars[s], tx);
-    tma_load_2d(buf, &maps.x, it.col0, row, &bars[s]);
-    unsigned char* v = buf + xbytes;
-    tma_load_1d(v, &maps.lab1, row, &bars[s]);
-    v += R * 4;
-    if (DUAL) {
-      tma_load_1d(v, &maps.lab2, row, &bars[s]);
-      v += R * 4;
-    }
-    if (WEIGHTED) {
-      tma_load_1d(v, &maps.w1, row, &bars[s]);
-      v += R * 4;
-      if (DUAL) tma_load_1d(v, &maps.w2, row, &bars[s]);
-    }
-  };
-  if (tid == 0) {
-    fence_proxy_async_smem();
-    for (int t = 0; t < ntiles && t < a.stages; ++t) issue(t);
-  }
-
-  int t = 0;
-  bool aborted = false;
-  for (; t < ntiles; ++t) {
-    const int s = t % a.stages;
-    if (!mbar_wait(&bars[s], uint32_t((t / a.stages) & 1))) {
-      // This thread gave up.  It still runs the tile (on whatever the buffer
-      // holds; every index stays in bounds) so that all threads meet the same
-      // barriers, and the whole CTA stops uniformly after the tile.
-      S.nne[1] = 1;
-      set_status(a.status, SIL_ETIMEOUT);
-    }
-    const int64_t r0 = it.row_begin + int64_t(t) * R;
-    const int rows = int((it.row_end - r0) < int64_t(R) ? (it.row_end - r0) : int64_t(R));
-    const unsigned char* buf = stage0 + s * a.stage_bytes;
-    const int32_t* v = reinterpret_cast<const int32_t*>(buf + xbytes);
-    SrcTma<DT> src;
-    src.xs = reinterpret_cast<const T*>(buf);
-    src.dsp = a.dsp;
-    src.lab1 = v;
-    src.lab2 = DUAL ? v + R : nullptr;
-    src.w1 = WEIGHTED ? reinterpret_cast<const float*>(v + (DUAL ? 2 : 1) * R) : nullptr;
-    src.w2 = (WEIGHTED && DUAL) ? reinterpret_cast<const float*>(v + 3 * R) : nullptr;
-    src.cs = a.cs;
-    src.col0 = it.col0;
-    src.dlim = it.dlim;
-    agg_tile<DUAL, WEIGHTED>(a, S, it, src, rows, r0);
-    __syncthreads();
-    if (S.nne[1]) {  // a thread timed out on this tile's barrier
-      aborted = true;
-      ++t;
-      break;
-    }
-    if (tid == 0 && t + a.stages < ntiles) {
-      fence_proxy_async_smem();
-      issue(t + a.stages);
+  constexpr int Q = Chunk<DT>::Q;
+  const unsigned char* p = a.X + int64_t(row) * a.ldx_bytes + int64_t(col) * int64_t(sizeof(T));
+  if (a.vec && col + Q <= a.d) return __ldg(reinterpret_cast<const uint4*>(p));
+  // ragged last chunk or unaligned layout: element by element, packed into
+  // the same little-endian words a 16-byte load would give
+  constexpr int esz = int(sizeof(T));
+  uint32_t w[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+  for (int t = 0; t < Q; ++t) {
+    if (col + t < a.d) {
+      uint32_t bits;
+      if constexpr (esz == 4) bits = *reinterpret_cast<const uint32_t*>(p + 4 * t);
+      else if constexpr (esz == 2) bits = *reinterpret_cast<const uint16_t*>(p + 2 * t);
+      else bits = p[t];
+      w[(t * esz) / 4] |= bits << (8 * ((t * esz) % 4));
     }
   }
-  if (aborted) {
-    // every thread stops; thread 0 waits (bounded) for this CTA's copies in flight
-    __syncthreads();
-    if (tid == 0) {
-      // tiles t-1 .. t-2+stages were issued and not consumed: one per stage
-      const int first = t - 1;
-      const int end = ntiles < first + a.stages ? ntiles : first + a.stages;
-      for (int u = first; u < end; ++u) mbar_wait(&bars[u % a.stages], uint32_t((u / a.stages) & 1));
-    }
-    __syncthreads();
-    return;
-  }
-  agg_flush<WEIGHTED>(a, S, it);
+  return make_uint4(w[0], w[1], w[2], w[3]);
 }
 
-// Column slices of at least 32 columns keep each row read a whole number of
-// 32-byte DRAM sectors (bf16/fp32); a CTA may use up to 200 KB to get there.
-void agg_plan(int32_t d, int32_t kb, bool dual, bool weighted, int* dsp_out, int* kbs_out) {
-  const int dz = int(round_up(d, 4));
-  const int dmax = dz < 256 ? dz : 256;  // the accumulation phase covers at most 64 chunks
-  const int budgets[2] = {kSmemBudget, 200 * 1024};
-  const int min_dsp = dz < 32 ? dz : 32;
-  auto total = [&](int dsp, int kbs) {  // generic kernel: shared state + one FP32 tile
-    return agg_smem(dsp, kbs, dual, weighted).total + kAggRows * dsp * 4;
-  };
-  for (int budget : budgets) {
-    int dsp = dmax;
-    while (dsp > min_dsp && total(dsp, kb) > budget) dsp = std::max(min_dsp, int(round_up(dsp / 2, 4)));
-    if (total(dsp, kb) <= budget) {
-      *dsp_out = dsp;
-      *kbs_out = kb;
-      return;
+// One warp walks its work items of the sorted order.  Lane layout: G lanes
+// per row (lane % G = 16-byte chunk, CPL chunks per lane), 32/G rows side by
+// side, U rows per lane group in flight.  Per run of one bucket the lanes
+// keep FP32 sums of the shifted values in registers; at the end of the run
+// the row groups are folded with shuffles and the run is added to the FP64
+// outputs.
+template <int DT, int CPL>
+__global__ void __launch_bounds__(kGatherThreads, 3) k_gather_reduce(GatherK a) {
+  constexpr int Q = Chunk<DT>::Q;
+  constexpr int EL = CPL * Q;  // elements per lane
+  constexpr int U = EL >= 16 ? (CPL >= 4 ? 1 : 2) : (EL == 8 ? 2 : 4);  // rows in flight per lane group
+  const int lane = threadIdx.x & 31;
+  const int G = a.G, R = 32 >> a.lgG;
+  const int rg = lane >> a.lgG, cl = lane & (G - 1);
+  const int ch0 = int(blockIdx.y) * a.ch_slice;  // first chunk of this column slice
+  const int chn = min(a.ch_slice, a.nch - ch0);  // chunks of this slice
+  const bool weighted = a.widx != nullptr;
+  const uint32_t total = a.bstart[a.nb];
+  // column of element t of this lane's chunk j: colb[j] + t, valid while < colend[j]
+  int colb[CPL], colend[CPL];
+#pragma unroll
+  for (int j = 0; j < CPL; ++j) {
+    const int ch = cl + G * j;
+    colb[j] = (ch0 + ch) * Q;
+    colend[j] = ch < chn ? min(a.d, colb[j] + Q) : colb[j];
+  }
+  float csc[EL];
+#pragma unroll
+  for (int j = 0; j < CPL; ++j)
+#pragma unroll
+    for (int t = 0; t < Q; ++t)
+      csc[j * Q + t] = (DT == SIL_FP8_E4M3 && colb[j] + t < colend[j]) ? __ldg(a.cs + colb[j] + t) : 1.f;
+
+  const int64_t gw = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
+  for (int64_t item = gw; item < a.nitems; item += nw) {
+    const int64_t e0 = item * a.wchunk;
+    const int64_t e1 = min(int64_t(total), e0 + a.wchunk);
+    if (e0 >= e1) break;
+    // bucket holding e0: the last b with bstart[b] <= e0
+    int lo = 0, hi = a.nb - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (__ldg(a.bstart + mid) <= uint32_t(e0)) lo = mid;
+      else hi = mid - 1;
+    }
+    int b = lo;
+    int64_t cur = e0;
+    while (cur < e1) {
+      while (__ldg(a.bstart + b + 1) <= uint32_t(cur)) ++b;  // skip empty buckets
+      const int64_t se = min(e1, int64_t(__ldg(a.bstart + b + 1)));
+      const int kc = b < a.k ? b : b - a.k;  // cluster whose reference point shifts this bucket
+      float rsh[EL], acc[EL];
+#pragma unroll
+      for (int j = 0; j < CPL; ++j)
+#pragma unroll
+        for (int t = 0; t < Q; ++t) {
+          const int col = colb[j] + t;
+          rsh[j * Q + t] = col < colend[j] ? __ldg(a.rs + int64_t(kc) * a.dz + col) : 0.f;
+          acc[j * Q + t] = 0.f;
+        }
+      float sq = 0.f, wacc = 0.f;
+      for (int64_t base = cur; base < se; base += int64_t(R) * U) {
+        uint4 raw[U][CPL];
+        uint32_t rowv[U];
+        float wv[U];
+        bool ok[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int64_t en = base + int64_t(u) * R + rg;
+          ok[u] = en < se;
+          rowv[u] = ok[u] ? __ldg(a.idx + en) : 0u;
+          wv[u] = (weighted && ok[u]) ? __ldg(a.widx + en) : 0.f;
+#pragma unroll
+          for (int j = 0; j < CPL; ++j) {
+            const int ch = cl + G * j;
+            raw[u][j] = (ok[u] && ch < chn) ? load_chunk<DT>(a, rowv[u], (ch0 + ch) * Q) : make_uint4(0, 0, 0, 0);
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          float v[EL];
+#pragma unroll
+          for (int j = 0; j < CPL; ++j) Chunk<DT>::cvt(raw[u][j], v + j * Q);
+#pragma unroll
+          for (int i = 0; i < EL; ++i) v[i] *= csc[i];
+          float sc = 1.f;
+          if (a.cosine) {
+            if (a.invnorm) {
+              sc = ok[u] ? __ldg(a.invnorm + rowv[u]) : 0.f;
+            } else {
+              float ss = 0.f;
+#pragma unroll
+              for (int i = 0; i < EL; ++i) ss = fmaf(v[i], v[i], ss);
+              for (int o = 1; o < G; o <<= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+              if (ok[u] && !(ss > 0.f) && cl == 0) set_status(a.status, SIL_EZERONORM);
+              sc = ss > 0.f ? rsqrtf(ss) : 0.f;
+            }
+          }
+          if (ok[u]) {
+            const float w = wv[u];
+#pragma unroll
+            for (int i = 0; i < EL; ++i) {
+              float t = fmaf(sc, v[i], -rsh[i]);
+              if (weighted) {
+                t *= w;
+              } else {
+                sq = fmaf(t, t, sq);
+              }
+              acc[i] += t;
+            }
+            wacc += w;
+          }
+        }
+      }
+      // fold the row groups: lanes with the same chunk position hold the same columns
+      for (int o = G; o < 32; o <<= 1) {
+#pragma unroll
+        for (int i = 0; i < EL; ++i) acc[i] += __shfl_xor_sync(0xffffffffu, acc[i], o);
+        wacc += __shfl_xor_sync(0xffffffffu, wacc, o);
+      }
+      // every lane now holds the run's total weight in wacc
+      const double m = weighted ? double(wacc) : double(se - cur);
+      double s2p = weighted ? 0.0 : double(sq);
+      if (rg == 0) {
+#pragma unroll
+        for (int j = 0; j < CPL; ++j)
+#pragma unroll
+          for (int t = 0; t < Q; ++t) {
+            const int col = colb[j] + t;
+            if (col >= colend[j]) continue;
+            const double r = rsh[j * Q + t], sv = acc[j * Q + t];
+            // weighted (backward) sums stay shifted: the gradient kernel
+            // works with sum w (x - r) and sum w directly
+            atomicAdd(a.s1 + int64_t(b) * a.d + col, weighted ? sv : sv + m * r);
+            if (!weighted) s2p += 2.0 * r * sv + m * r * r;
+          }
+      }
+      if (!weighted) {
+        for (int o = 16; o > 0; o >>= 1) s2p += __shfl_xor_sync(0xffffffffu, s2p, o);
+        if (lane == 0) atomicAdd(a.s2 + b, s2p);
+      } else if (lane == 0 && blockIdx.y == 0) {
+        atomicAdd(a.wsum + b, m);
+      }
+      cur = se;
     }
   }
-  // very many buckets: narrowest slice, then split the buckets
-  int dsp = min_dsp;
-  int kbs = kb;
-  while (kbs > 1 && total(dsp, kbs) > 200 * 1024) kbs = (kbs + 1) / 2;
-  *dsp_out = dsp;
-  *kbs_out = kbs;
 }
 
-bool vec_ok(const void* X, int32_t dtype, int64_t ldx) {
-  const int esz = dtype == SIL_F32 ? 4 : dtype == SIL_BF16 ? 2 : 1;
-  return (reinterpret_cast<uintptr_t>(X) % (4 * esz) == 0) && (ldx % 4 == 0);
+template <int DT, int CPL>
+cudaError_t launch_gather_t(const GatherK& g, dim3 grid, cudaStream_t st) {
+  k_gather_reduce<DT, CPL><<<grid, kGatherThreads, 0, st>>>(g);
+  return cudaGetLastError();
 }
 
-inline bool aligned16(const void* p) { return p == nullptr || reinterpret_cast<uintptr_t>(p) % 16 == 0; }
+// Largest number of 16-byte chunks one lane handles (16 elements per lane).
+int max_cpl(int32_t dtype) { return dtype == SIL_F32 ? 4 : dtype == SIL_BF16 ? 2 : 1; }
+int elem_bytes(int32_t dtype) { return dtype == SIL_F32 ? 4 : dtype == SIL_BF16 ? 2 : 1; }
 
 }  // namespace
 
-bool agg_needs_invnorm(int32_t d, int32_t k, bool dual) {
-  int dsp, kbs;
-  agg_plan(d, dual ? 2 * k : k, dual, dual, &dsp, &kbs);
-  return dsp < round_up(d, 4);
+bool agg_needs_invnorm(int32_t dtype, int32_t d) {
+  const int q = 16 / elem_bytes(dtype);
+  return cdiv(d, q) > 32 * max_cpl(dtype);
 }
 
 cudaError_t launch_shift(const void* X, int32_t dtype, int64_t n, int32_t d, int64_t ldx,
@@ -720,7 +548,8 @@ cudaError_t launch_shift(const void* X, int32_t dtype, int64_t n, int32_t d, int
 cudaError_t launch_invnorm(const void* X, int32_t dtype, int64_t n, int32_t d, int64_t ldx,
                            const float* cs, float* invnorm, uint32_t* status, cudaStream_t stream) {
   if (n == 0) return cudaSuccess;
-  const bool vec = vec_ok(X, dtype, ldx);
+  const int esz = elem_bytes(dtype);
+  const bool vec = (reinterpret_cast<uintptr_t>(X) % (4 * esz) == 0) && (ldx % 4 == 0);
   const unsigned grid = unsigned(std::min<int64_t>(cdiv(n, 8), int64_t(kNumSMs) * 16));
   switch (dtype) {
     case SIL_F32: k_invnorm<SIL_F32><<<grid, 256, 0, stream>>>(X, n, d, ldx, cs, vec, invnorm, status); break;
@@ -730,142 +559,81 @@ cudaError_t launch_invnorm(const void* X, int32_t dtype, int64_t n, int32_t d, i
   return cudaGetLastError();
 }
 
-namespace {
-
-template <int DT, bool DUAL, bool WEIGHTED>
-cudaError_t launch_generic_t(const AggK& k, dim3 grid, int smem, cudaStream_t stream) {
-  auto fn = k_aggregate<DT, DUAL, WEIGHTED>;
-  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  if (e != cudaSuccess) return e;
-  fn<<<grid, kAggThreads, smem, stream>>>(k);
-  return cudaGetLastError();
-}
-
-template <int DT, bool DUAL, bool WEIGHTED>
-cudaError_t launch_tma_t(const AggK& k, const AggMaps& maps, dim3 grid, int smem, cudaStream_t stream) {
-  auto fn = k_aggregate_tma<DT, DUAL, WEIGHTED>;
-  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  if (e != cudaSuccess) return e;
-  fn<<<grid, kAggThreads, smem, stream>>>(k, maps);
-  return cudaGetLastError();
-}
-
-template <bool DUAL, bool WEIGHTED>
-cudaError_t dispatch(int dtype, bool tma, const AggK& k, const AggMaps& maps, dim3 grid, int smem,
-                     cudaStream_t st) {
-  switch (dtype) {
-    case SIL_F32:
-      return tma ? launch_tma_t<SIL_F32, DUAL, WEIGHTED>(k, maps, grid, smem, st)
-                 : launch_generic_t<SIL_F32, DUAL, WEIGHTED>(k, grid, smem, st);
-    case SIL_BF16:
-      return tma ? launch_tma_t<SIL_BF16, DUAL, WEIGHTED>(k, maps, grid, smem, st)
-                 : launch_generic_t<SIL_BF16, DUAL, WEIGHTED>(k, grid, smem, st);
-    default:
-      return tma ? launch_tma_t<SIL_FP8_E4M3, DUAL, WEIGHTED>(k, maps, grid, smem, st)
-                 : launch_generic_t<SIL_FP8_E4M3, DUAL, WEIGHTED>(k, grid, smem, st);
-  }
-}
-
-// Tensor maps for the TMA kernel; false when the layout does not allow them.
-bool make_maps(const AggLaunch& L, const AggK& k, AggMaps* maps) {
-  const int esz = L.dtype == SIL_F32 ? 4 : L.dtype == SIL_BF16 ? 2 : 1;
-  const CUtensorMapDataType xt = L.dtype == SIL_F32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
-                                 : L.dtype == SIL_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
-                                                       : CU_TENSOR_MAP_DATA_TYPE_UINT8;
-  if ((k.dsp * esz) % 16 != 0 || k.dsp > 256 || k.dsp > L.d) return false;
-  if (!aligned16(L.labels) || !aligned16(L.labels2) || !aligned16(L.w1) || !aligned16(L.w2)) return false;
-  if (!encode_tmap_2d(&maps->x, L.X, xt, esz, uint64_t(L.d), uint64_t(L.n), uint64_t(L.ldx) * esz,
-                      uint32_t(k.dsp), uint32_t(kAggRows), CU_TENSOR_MAP_SWIZZLE_NONE))
-    return false;
-  if (!encode_tmap_1d(&maps->lab1, L.labels, CU_TENSOR_MAP_DATA_TYPE_INT32, uint64_t(L.n), kAggRows))
-    return false;
-  maps->lab2 = maps->lab1;
-  maps->w1 = maps->lab1;
-  maps->w2 = maps->lab1;
-  if (L.labels2 &&
-      !encode_tmap_1d(&maps->lab2, L.labels2, CU_TENSOR_MAP_DATA_TYPE_INT32, uint64_t(L.n), kAggRows))
-    return false;
-  if (L.w1 && !encode_tmap_1d(&maps->w1, L.w1, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, uint64_t(L.n), kAggRows))
-    return false;
-  if (L.w2 && !encode_tmap_1d(&maps->w2, L.w2, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, uint64_t(L.n), kAggRows))
-    return false;
-  return true;
-}
-
-}  // namespace
-
-// Selects the TMA kernel when the layout allows (set SIL_AGG_GENERIC=1 in the
-// environment to force the generic kernel).
 cudaError_t launch_aggregate(const AggLaunch& L) {
   if (L.n == 0) return cudaSuccess;
   const bool dual = L.labels2 != nullptr;
-  const bool weighted = L.w1 != nullptr;
-  AggK k{};
-  k.X = L.X;
-  k.n = L.n;
-  k.d = L.d;
-  k.ldx = L.ldx;
-  k.cs = L.cs;
-  k.lab1 = L.labels;
-  k.lab2 = L.labels2;
-  k.w1 = L.w1;
-  k.w2 = L.w2;
-  k.k = L.k;
-  k.kb = dual ? 2 * L.k : L.k;
-  k.cosine = L.dist == SIL_COSINE;
-  k.vec = vec_ok(L.X, L.dtype, L.ldx);
-  k.rs = L.rs;
-  k.dz = int(round_up(L.d, 4));
-  k.invnorm = L.invnorm;
-  int dsp, kbs;
-  agg_plan(L.d, k.kb, dual, weighted, &dsp, &kbs);
-  const int esz = L.dtype == SIL_F32 ? 4 : L.dtype == SIL_BF16 ? 2 : 1;
-  const int box_mult = 16 / esz;  // TMA box rows must be whole 16-byte units
-  if (dsp % box_mult != 0 && round_up(dsp, box_mult) <= 256) dsp = int(round_up(dsp, box_mult));
-  k.dsp = dsp;
-  k.kbs = kbs;
-  k.nslc = int(cdiv(L.d, dsp));
-  const int nkslc = int(cdiv(k.kb, kbs));
-  if (k.cosine && k.nslc > 1 && L.invnorm == nullptr) return cudaErrorInvalidValue;
-  k.count = L.count;
-  k.s1 = L.s1;
-  k.s2 = L.s2;
-  k.wsum = L.wsum;
-  k.status = L.status;
+  const int64_t E = dual ? 2 * L.n : L.n;
+  const int nb = dual ? 2 * L.k : L.k;
+  if (E >= (int64_t(1) << 32)) return cudaErrorInvalidValue;
+  Entries en{L.n, L.k, L.labels, L.labels2, L.w1, L.w2, L.status};
 
-  const int fixed = agg_smem(dsp, kbs, dual, weighted).total;
-  const int nvec = 1 + (dual ? 1 : 0) + (weighted ? (dual ? 2 : 1) : 0);
-  const int stage = int(round_up(kAggRows * dsp * esz + nvec * kAggRows * 4, 128));
-  const char* force_generic = getenv("SIL_AGG_GENERIC");
-  AggMaps maps{};
-  bool tma = !(force_generic && force_generic[0] == '1') && L.n < (int64_t(1) << 31);
-  int stages = 0, smem = 0;
-  if (tma) {
-    // two CTAs per SM when two stages fit twice, else one CTA with up to four stages
-    const int two_cta = (220 * 1024) / 2;
-    if (fixed + 128 + 2 * stage <= two_cta) {
-      stages = std::min(4, (two_cta - fixed - 128) / stage);
-    } else {
-      stages = std::min(4, (220 * 1024 - fixed - 128) / stage);
-    }
-    tma = stages >= 2 && make_maps(L, k, &maps);
-    smem = fixed + 128 + stages * stage;
+  // 1-3: counting sort of the entries by bucket
+  cudaError_t e = cudaMemsetAsync(L.bcount, 0, size_t(nb) * 4, L.stream);
+  if (e != cudaSuccess) return e;
+  {
+    const unsigned grid = unsigned(std::max<int64_t>(1, std::min<int64_t>(cdiv(E, 256 * 16), int64_t(kNumSMs) * 2)));
+    const size_t smem = nb <= kHistSmem ? size_t(nb) * 4 : 0;
+    k_bucket_count<<<grid, 256, smem, L.stream>>>(en, E, nb, L.bcount);
   }
-  if (!tma) smem = fixed + kAggRows * dsp * 4;
-  k.stages = stages;
-  k.stage_bytes = stage;
-  const int per_sm = std::max(1, std::min(4, (220 * 1024) / std::max(smem, 1)));
-  const int64_t tiles = cdiv(L.n, kAggRows);
-  const int64_t slices = int64_t(k.nslc) * nkslc;
-  int64_t row_blocks = std::max<int64_t>(1, (int64_t(kNumSMs) * per_sm * (tma ? 1 : 2)) / slices);
-  row_blocks = std::min<int64_t>(row_blocks, tiles);
-  row_blocks = std::min<int64_t>(row_blocks, 65535);
-  k.rows_per_cta = cdiv(tiles, row_blocks) * kAggRows;
-  row_blocks = cdiv(L.n, k.rows_per_cta);
-  const dim3 grid(static_cast<unsigned>(slices), static_cast<unsigned>(row_blocks));
-  if (dual) return dispatch<true, true>(L.dtype, tma, k, maps, grid, smem, L.stream);
-  if (weighted) return dispatch<false, true>(L.dtype, tma, k, maps, grid, smem, L.stream);
-  return dispatch<false, false>(L.dtype, tma, k, maps, grid, smem, L.stream);
+  k_bucket_scan<<<1, kScanThreads, 0, L.stream>>>(L.bcount, nb, L.k, L.bstart, L.cursor, dual ? nullptr : L.count);
+  k_bucket_scatter<<<unsigned(cdiv(E, 256 * kScatterIPT)), 256, 0, L.stream>>>(en, E, nb, L.cursor, L.idx,
+                                                                              L.w1 ? L.widx : nullptr);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+
+  // 4: gather-reduce over the sorted order
+  const int esz = elem_bytes(L.dtype);
+  const int q = 16 / esz;
+  GatherK g{};
+  g.X = static_cast<const unsigned char*>(L.X);
+  g.n = L.n;
+  g.d = L.d;
+  g.ldx_bytes = L.ldx * esz;
+  g.cs = L.cs;
+  g.k = L.k;
+  g.nb = nb;
+  g.dz = int(round_up(L.d, 4));
+  g.idx = L.idx;
+  g.widx = L.w1 ? L.widx : nullptr;
+  g.bstart = L.bstart;
+  g.rs = L.rs;
+  g.invnorm = L.invnorm;
+  g.cosine = L.dist == SIL_COSINE;
+  g.vec = (reinterpret_cast<uintptr_t>(L.X) % 16 == 0) && (g.ldx_bytes % 16 == 0);
+  g.nch = int(cdiv(L.d, q));
+  int cpl = 1, G = 1;
+  if (g.nch <= 32) {
+    while (G < g.nch) G <<= 1;
+  } else {
+    G = 32;
+    cpl = int(std::min<int64_t>(cdiv(g.nch, 32), max_cpl(L.dtype)));
+    if (cpl == 3) cpl = 4;
+    if (cpl > max_cpl(L.dtype)) cpl = max_cpl(L.dtype);
+  }
+  g.G = G;
+  g.lgG = 0;
+  while ((1 << g.lgG) < G) ++g.lgG;
+  g.ch_slice = G * cpl;
+  const int slices = int(cdiv(g.nch, g.ch_slice));
+  if (slices > 1 && g.cosine && L.invnorm == nullptr) return cudaErrorInvalidValue;
+  g.s1 = L.s1;
+  g.s2 = L.s2;
+  g.wsum = L.wsum;
+  g.status = L.status;
+  const int64_t warps = int64_t(kNumSMs) * 4 * (kGatherThreads / 32);
+  g.wchunk = round_up(std::max<int64_t>(256, cdiv(E, warps * 2)), 32);
+  g.nitems = cdiv(E, g.wchunk);
+  const dim3 grid(unsigned(std::min<int64_t>(cdiv(g.nitems, kGatherThreads / 32), int64_t(kNumSMs) * 4)),
+                  unsigned(slices));
+  switch (L.dtype) {
+    case SIL_F32:
+      return cpl == 1   ? launch_gather_t<SIL_F32, 1>(g, grid, L.stream)
+             : cpl == 2 ? launch_gather_t<SIL_F32, 2>(g, grid, L.stream)
+                        : launch_gather_t<SIL_F32, 4>(g, grid, L.stream);
+    case SIL_BF16:
+      return cpl == 1 ? launch_gather_t<SIL_BF16, 1>(g, grid, L.stream) : launch_gather_t<SIL_BF16, 2>(g, grid, L.stream);
+    default:
+      return launch_gather_t<SIL_FP8_E4M3, 1>(g, grid, L.stream);
+  }
 }
 
 }  // namespace sil

@@ -33,6 +33,9 @@ WsLayout ws_layout(int64_t n, int32_t d, int32_t k, int32_t dtype, int32_t dist,
   L.bw_ab = take(2 * N * 4);
   L.bw_f = take((K * dz + K) * 4);
   L.saved = take(N * 12);
+  L.bk = take((3 * 2 * K + 1) * 4);
+  L.bidx = take(2 * N * 4);
+  L.bw = take(2 * N * 4);
   L.zbf = take(tc_pack_bytes(k, d));
   L.tcp = take(tc_partial_bytes(n, d, k, dtype));
   L.batch = take(K * (size_t(d) + 2) * 8);
@@ -59,7 +62,7 @@ int check_common(const void* X, int32_t dtype, int64_t n, int32_t d, int64_t ldx
   if (n > 0 && (X == nullptr || labels == nullptr)) return SIL_EINVAL;
   if (dtype == SIL_FP8_E4M3 && cs == nullptr) return SIL_EINVAL;
   if (k > (1 << 22) || d > (1 << 16)) return SIL_EUNSUPPORTED;
-  if (n >= (int64_t(1) << 40)) return SIL_EUNSUPPORTED;
+  if (n >= (int64_t(1) << 31)) return SIL_EUNSUPPORTED;  // row indices of the pass-1 sort are 32-bit
   return SIL_OK;
 }
 
@@ -78,6 +81,18 @@ inline int cu(cudaError_t e) { return e == cudaSuccess ? SIL_OK : SIL_ECUDA; }
     if (rc_ != SIL_OK) return rc_; \
   } while (0)
 
+// Counting-sort scratch of pass 1 inside the workspace (sized for 2k buckets
+// and 2n entries, the backward pass's dual form).
+void set_sort_scratch(AggLaunch* a, void* ws, const WsLayout& L, int32_t k, int64_t n) {
+  (void)n;
+  uint32_t* bk = at<uint32_t>(ws, L.bk);
+  a->bcount = bk;
+  a->cursor = bk + 2 * size_t(k);
+  a->bstart = bk + 4 * size_t(k);
+  a->idx = at<uint32_t>(ws, L.bidx);
+  a->widx = at<float>(ws, L.bw);
+}
+
 // Pass 1 into (count, s1, s2), status into the workspace word.
 int run_aggregate(const void* X, int32_t dtype, int64_t n, int32_t d, int64_t ldx, const float* cs,
                   const int32_t* labels, int32_t k, int32_t dist, int64_t* count, double* s1,
@@ -92,7 +107,7 @@ int run_aggregate(const void* X, int32_t dtype, int64_t n, int32_t d, int64_t ld
   float* rs = at<float>(ws, L.rs);
   SIL_TRY(cu(launch_shift(X, dtype, n, d, ldx, cs, labels, k, dist, at<int32_t>(ws, L.rep), rs, st)));
   const float* invnorm = nullptr;
-  if (dist == SIL_COSINE && agg_needs_invnorm(d, k, false)) {
+  if (dist == SIL_COSINE && agg_needs_invnorm(dtype, d)) {
     SIL_TRY(cu(launch_invnorm(X, dtype, n, d, ldx, cs, at<float>(ws, L.invnorm), wst, st)));
     invnorm = at<float>(ws, L.invnorm);
   }
@@ -112,6 +127,7 @@ int run_aggregate(const void* X, int32_t dtype, int64_t n, int32_t d, int64_t ld
   a.s1 = s1;
   a.s2 = s2;
   a.status = wst;
+  set_sort_scratch(&a, ws, L, k, n);
   a.stream = st;
   return cu(launch_aggregate(a));
 }
@@ -286,7 +302,7 @@ int sil_score_backward(const void* X, int32_t dtype, int64_t n, int32_t d, int64
   SIL_TRY(cu(cudaMemsetAsync(bw_w, 0, size_t(2) * k * 8, st)));
   SIL_TRY(cu(cudaMemsetAsync(bw_p, 0, size_t(2) * k * size_t(d) * 8, st)));
   const float* invnorm = nullptr;
-  if (dist == SIL_COSINE && agg_needs_invnorm(d, k, true)) {
+  if (dist == SIL_COSINE && agg_needs_invnorm(dtype, d)) {
     SIL_TRY(cu(launch_invnorm(X, dtype, n, d, ldx, col_scale, at<float>(ws, L.invnorm), wst, st)));
     invnorm = at<float>(ws, L.invnorm);
   }
@@ -308,6 +324,7 @@ int sil_score_backward(const void* X, int32_t dtype, int64_t n, int32_t d, int64
   a.s1 = bw_p;
   a.wsum = bw_w;
   a.status = wst;
+  set_sort_scratch(&a, ws, L, k, n);
   a.stream = st;
   SIL_TRY(cu(launch_aggregate(a)));
   float* Wf = at<float>(ws, L.bw_f);

@@ -113,8 +113,9 @@ __device__ __forceinline__ void tc_fence_after() {
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
 
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
-  uint32_t r[16];
+// Start loading 16 consecutive accumulator columns of this warp's 32 lanes;
+// the registers are valid only after tmem_wait_ld() and reg_fence16().
+__device__ __forceinline__ void tmem_ld16_async(uint32_t taddr, uint32_t (&r)[16]) {
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
       "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
@@ -122,9 +123,16 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
         "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
         "=r"(r[14]), "=r"(r[15])
       : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// Ties the registers to the preceding wait so no use is scheduled before it.
+__device__ __forceinline__ void reg_fence16(uint32_t (&r)[16]) {
+  asm volatile(""
+               : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]),
+                 "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]),
+                 "+r"(r[14]), "+r"(r[15]));
 }
 
 // Byte offset of 16-byte chunk q of row r inside a 128-byte-swizzled block.
@@ -604,26 +612,37 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_score_tc(TcK a, const __grid_
       int kb = -1;
       const uint32_t tbase = tmem + uint32_t(bsel * a.acc_cols) + (uint32_t(q * 32) << 16);
       const float2 sc2 = make_float2(sc, sc);
-      for (int c0 = 0; c0 < a.kp; c0 += 16) {
-        float v[16];
-        tmem_ld16(tbase + uint32_t(c0), v);
-        const float4* cb4 = reinterpret_cast<const float4*>(cbs + c0);
+      // 64 columns per round trip to TMEM: four loads in flight, one wait
+      for (int c0 = 0; c0 < a.kp; c0 += 64) {
+        uint32_t rv[4][16];
 #pragma unroll
-        for (int q4 = 0; q4 < 4; ++q4) {
-          const float4 cq = cb4[q4];
-          const float2 va = __ffma2_rn(sc2, make_float2(v[4 * q4], v[4 * q4 + 1]), make_float2(cq.x, cq.y));
-          const float2 vb = __ffma2_rn(sc2, make_float2(v[4 * q4 + 2], v[4 * q4 + 3]), make_float2(cq.z, cq.w));
-          const float vals[4] = {va.x, va.y, vb.x, vb.y};
+        for (int j = 0; j < 4; ++j)
+          if (c0 + 16 * j < a.kp) tmem_ld16_async(tbase + uint32_t(c0 + 16 * j), rv[j]);
+        tmem_wait_ld();
 #pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            const int kk = c0 + 4 * q4 + e;
-            if (SAVE) {
-              if (kk != own && vals[e] < best) {
-                best = vals[e];
-                kb = kk;
+        for (int j = 0; j < 4; ++j) {
+          if (c0 + 16 * j >= a.kp) break;
+          reg_fence16(rv[j]);
+          const float4* cb4 = reinterpret_cast<const float4*>(cbs + c0 + 16 * j);
+#pragma unroll
+          for (int q4 = 0; q4 < 4; ++q4) {
+            const float4 cq = cb4[q4];
+            const float2 va = __ffma2_rn(sc2, make_float2(__uint_as_float(rv[j][4 * q4]), __uint_as_float(rv[j][4 * q4 + 1])),
+                                         make_float2(cq.x, cq.y));
+            const float2 vb = __ffma2_rn(sc2, make_float2(__uint_as_float(rv[j][4 * q4 + 2]), __uint_as_float(rv[j][4 * q4 + 3])),
+                                         make_float2(cq.z, cq.w));
+            const float vals[4] = {va.x, va.y, vb.x, vb.y};
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              const int kk = c0 + 16 * j + 4 * q4 + e;
+              if (SAVE) {
+                if (kk != own && vals[e] < best) {
+                  best = vals[e];
+                  kb = kk;
+                }
+              } else if (kk != own) {
+                best = fminf(best, vals[e]);
               }
-            } else if (kk != own) {
-              best = fminf(best, vals[e]);
             }
           }
         }

@@ -18,8 +18,6 @@
 
 namespace sil {
 
-constexpr int kAggRows = 128;        // rows per pass-1 tile
-constexpr int kAggThreads = 256;     // threads per pass-1 CTA
 constexpr int kScoreThreads = 256;   // threads per SIMT pass-2 CTA
 constexpr int kMaxPartials = 8192;   // per-CTA partial sums of s_i
 constexpr int kRepRows = 65536;      // rows searched for per-cluster reference points
@@ -53,6 +51,9 @@ struct WsLayout {
   size_t bw_ab;     // float[2n]         backward: alpha_i then beta_i
   size_t bw_f;      // float[k*dz + k]   backward: W_c rows then C_c
   size_t saved;     // 12 bytes * n      recomputed forward record
+  size_t bk;        // uint32[3 * 2k + 1] pass-1 bucket counts, starts, cursors
+  size_t bidx;      // uint32[2n]        pass-1 row indices in bucket order
+  size_t bw;        // float[2n]         pass-1 weights in bucket order (backward)
   size_t zbf;       // bf16 centroid tiles for the tensor path
   size_t tcp;       // tensor path with several cluster blocks: per-block minima
   size_t batch;     // batched aggregates
@@ -145,6 +146,13 @@ struct AggLaunch {
   double* s2;
   double* wsum;
   uint32_t* status;
+  // counting-sort scratch (workspace): per bucket counts, starts (nb + 1) and
+  // cursors; the sorted row indices and weights (one per entry)
+  uint32_t* bcount;
+  uint32_t* bstart;
+  uint32_t* cursor;
+  uint32_t* idx;
+  float* widx;
   cudaStream_t stream;
 };
 
@@ -155,8 +163,9 @@ cudaError_t launch_shift(const void* X, int32_t dtype, int64_t n, int32_t d, int
 // Enqueue 1/||x_i|| for every row (cosine, column-sliced pass 1).
 cudaError_t launch_invnorm(const void* X, int32_t dtype, int64_t n, int32_t d, int64_t ldx,
                            const float* cs, float* invnorm, uint32_t* status, cudaStream_t stream);
-// Whether pass 1 for these sizes needs full rows per CTA for the cosine norm.
-bool agg_needs_invnorm(int32_t d, int32_t k, bool dual);
+// Whether pass 1 splits the rows into column slices, so that the cosine norm
+// must come from launch_invnorm.
+bool agg_needs_invnorm(int32_t dtype, int32_t d);
 // Enqueue pass 1 (outputs must be zeroed or hold sums to add to).
 cudaError_t launch_aggregate(const AggLaunch& a);
 
