@@ -31,6 +31,7 @@
 #include <cstdlib>
 
 #include "sil_internal.cuh"
+#include "tma.cuh"
 
 namespace sil {
 
@@ -38,7 +39,7 @@ namespace {
 
 constexpr int kHistSmem = 12288;    // buckets privatised in shared memory by the count kernel
 constexpr int kScatterSmem = 4096;  // buckets privatised by the scatter kernel
-constexpr int kScatterIPT = 16;     // entries per thread of the scatter kernel
+constexpr int kScatterIPT = 8;      // entries per thread of the scatter kernel
 constexpr int kScanThreads = 1024;
 constexpr int kGatherThreads = 256;
 
@@ -167,13 +168,18 @@ __global__ void __launch_bounds__(256) k_bucket_count(Entries en, int64_t E, int
     for (int b = threadIdx.x; b < nb; b += blockDim.x) hist[b] = 0;
   __syncthreads();
   const int lane = threadIdx.x & 31;
+  constexpr int UNR = 8;  // labels in flight per thread
   const int64_t stride = int64_t(gridDim.x) * blockDim.x;
   // the loop bound is uniform per warp, so every lane reaches the warp collectives
-  for (int64_t base = int64_t(blockIdx.x) * blockDim.x + threadIdx.x - lane; base < E; base += stride) {
-    const int64_t e = base + lane;
-    const int b = e < E ? en.bucket(e, true) : -1;
-    unsigned* ctr = b >= 0 ? (priv ? &hist[b] : &bcount[b]) : nullptr;
-    warp_reserve(b, ctr);
+  for (int64_t base = int64_t(blockIdx.x) * blockDim.x + threadIdx.x - lane; base < E; base += stride * UNR) {
+    int b[UNR];
+#pragma unroll
+    for (int i = 0; i < UNR; ++i) {
+      const int64_t e = base + i * stride + lane;
+      b[i] = e < E ? en.bucket(e, true) : -1;
+    }
+#pragma unroll
+    for (int i = 0; i < UNR; ++i) warp_reserve(b[i], b[i] >= 0 ? (priv ? &hist[b[i]] : &bcount[b[i]]) : nullptr);
   }
   if (priv) {
     __syncthreads();
@@ -244,11 +250,12 @@ __global__ void __launch_bounds__(256) k_bucket_scatter(Entries en, int64_t E, i
   int bk[kScatterIPT];
   unsigned rk[kScatterIPT];
 #pragma unroll
-  for (int i = 0; i < kScatterIPT; ++i) {
+  for (int i = 0; i < kScatterIPT; ++i) {  // all label loads first, then the reservations
     const int64_t e = c0 + int64_t(i) * 256 + tid;
     bk[i] = e < E ? en.bucket(e, false) : -1;
-    rk[i] = warp_reserve(bk[i], bk[i] >= 0 ? &lh[bk[i]] : nullptr);
   }
+#pragma unroll
+  for (int i = 0; i < kScatterIPT; ++i) rk[i] = warp_reserve(bk[i], bk[i] >= 0 ? &lh[bk[i]] : nullptr);
   __syncthreads();
   for (int b = tid; b < nb; b += 256) {
     const uint32_t c = lh[b];
@@ -288,6 +295,8 @@ struct GatherK {
   int32_t ch_slice;  // chunks per column slice (= G * CPL, or fewer in the last)
   int64_t wchunk;    // sorted entries per warp work item
   int64_t nitems;
+  int32_t rb;        // TMA-gather kernel: bytes of one row slot in shared memory
+  int32_t stages;    // TMA-gather kernel: 32-row blocks in flight per warp
   double* s1;
   double* s2;
   double* wsum;
@@ -363,23 +372,89 @@ __device__ __forceinline__ uint4 load_chunk(const GatherK& a, uint32_t row, int 
   return make_uint4(w[0], w[1], w[2], w[3]);
 }
 
-// One warp walks its work items of the sorted order.  Lane layout: G lanes
-// per row (lane % G = 16-byte chunk, CPL chunks per lane), 32/G rows side by
-// side, U rows per lane group in flight.  Per run of one bucket the lanes
-// keep FP32 sums of the shifted values in registers; at the end of the run
-// the row groups are folded with shuffles and the run is added to the FP64
-// outputs.
-template <int DT, int CPL>
-__global__ void __launch_bounds__(kGatherThreads, 3) k_gather_reduce(GatherK a) {
+// End of a run of bucket b: fold the row groups (lanes with the same chunk
+// position hold the same columns), un-shift in FP64 and add to the outputs.
+// Every lane of the warp must call it.
+template <int DT, int CPL, bool WEIGHTED>
+__device__ __forceinline__ void run_flush(const GatherK& a, int b, float2* acc, const float2* rsh, float2 sq2,
+                                          float wacc, double mrows, const int* colb, const int* colend, int G,
+                                          int rg, int lane) {
   constexpr int Q = Chunk<DT>::Q;
-  constexpr int EL = CPL * Q;  // elements per lane
-  constexpr int U = EL >= 16 ? (CPL >= 4 ? 1 : 2) : (EL == 8 ? 2 : 4);  // rows in flight per lane group
+  constexpr int EL2 = CPL * Q / 2;
+  for (int o = G; o < 32; o <<= 1) {
+#pragma unroll
+    for (int i = 0; i < EL2; ++i) {
+      acc[i].x += __shfl_xor_sync(0xffffffffu, acc[i].x, o);
+      acc[i].y += __shfl_xor_sync(0xffffffffu, acc[i].y, o);
+    }
+    if (WEIGHTED) wacc += __shfl_xor_sync(0xffffffffu, wacc, o);
+  }
+  // weighted: every lane now holds the run's total weight in wacc
+  const double m = WEIGHTED ? double(wacc) : mrows;
+  double s2p = WEIGHTED ? 0.0 : double(sq2.x) + double(sq2.y);
+  if (rg == 0) {
+#pragma unroll
+    for (int i = 0; i < EL2; ++i) {
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int j = (2 * i + h) / Q, t = (2 * i + h) % Q;
+        const int col = colb[j] + t;
+        if (col >= colend[j]) continue;
+        const double r = -double(h ? rsh[i].y : rsh[i].x), sv = h ? acc[i].y : acc[i].x;
+        // weighted (backward) sums stay shifted: the gradient kernel works
+        // with sum w (x - r) and sum w directly
+        atomicAdd(a.s1 + int64_t(b) * a.d + col, WEIGHTED ? sv : sv + m * r);
+        if (!WEIGHTED) s2p += 2.0 * r * sv + m * r * r;
+      }
+    }
+  }
+  if (!WEIGHTED) {
+    for (int o = 16; o > 0; o >>= 1) s2p += __shfl_xor_sync(0xffffffffu, s2p, o);
+    if (lane == 0) atomicAdd(a.s2 + b, s2p);
+  } else if (lane == 0 && blockIdx.y == 0) {
+    atomicAdd(a.wsum + b, m);
+  }
+}
+
+// Shift of bucket b for this lane's elements (negated), packed in pairs.
+template <int DT, int CPL>
+__device__ __forceinline__ void load_shift(const GatherK& a, int b, const int* colb, const int* colend, float2* rsh) {
+  constexpr int Q = Chunk<DT>::Q;
+  constexpr int EL2 = CPL * Q / 2;
+  const int kc = b < a.k ? b : b - a.k;  // cluster whose reference point shifts this bucket
+#pragma unroll
+  for (int i = 0; i < EL2; ++i) {
+    float r[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int j = (2 * i + h) / Q, t = (2 * i + h) % Q;
+      const int col = colb[j] + t;
+      r[h] = col < colend[j] ? __ldg(a.rs + int64_t(kc) * a.dz + col) : 0.f;
+    }
+    rsh[i] = make_float2(-r[0], -r[1]);
+  }
+}
+
+// One warp walks its work items of the sorted order.  Lane layout: G lanes
+// per row (lane % G = first 16-byte chunk, CPL chunks per lane, G apart), 32/G
+// rows side by side; every lane issues the loads of RPL rows before it
+// consumes any, so a warp keeps 32/G * RPL rows (a few KB) in flight.  The
+// run's sorted indices arrive 32 at a time in one coalesced load, one block
+// ahead, and lanes take their rows from it by shuffle.  Per run of one bucket
+// the lanes keep FP32 sums of the shifted values (packed FP32x2 arithmetic);
+// at the end of the run the row groups are folded with shuffles and the run
+// is added to the FP64 outputs.
+template <int DT, int CPL, bool WEIGHTED, bool COS>
+__global__ void __launch_bounds__(kGatherThreads, 2) k_gather_reduce(GatherK a) {
+  constexpr int Q = Chunk<DT>::Q;
+  constexpr int EL = CPL * Q;        // elements per lane
+  constexpr int EL2 = EL / 2;        // packed pairs
+  constexpr int RPL = 8 / CPL;  // rows in flight per lane (eight 16-byte loads)
   const int lane = threadIdx.x & 31;
   const int G = a.G, R = 32 >> a.lgG;
   const int rg = lane >> a.lgG, cl = lane & (G - 1);
   const int ch0 = int(blockIdx.y) * a.ch_slice;  // first chunk of this column slice
   const int chn = min(a.ch_slice, a.nch - ch0);  // chunks of this slice
-  const bool weighted = a.widx != nullptr;
   const uint32_t total = a.bstart[a.nb];
   // column of element t of this lane's chunk j: colb[j] + t, valid while < colend[j]
   int colb[CPL], colend[CPL];
@@ -389,12 +464,17 @@ __global__ void __launch_bounds__(kGatherThreads, 3) k_gather_reduce(GatherK a) 
     colb[j] = (ch0 + ch) * Q;
     colend[j] = ch < chn ? min(a.d, colb[j] + Q) : colb[j];
   }
-  float csc[EL];
+  float2 csc[EL2];
 #pragma unroll
-  for (int j = 0; j < CPL; ++j)
+  for (int i = 0; i < EL2; ++i) {
+    float c[2];
 #pragma unroll
-    for (int t = 0; t < Q; ++t)
-      csc[j * Q + t] = (DT == SIL_FP8_E4M3 && colb[j] + t < colend[j]) ? __ldg(a.cs + colb[j] + t) : 1.f;
+    for (int h = 0; h < 2; ++h) {
+      const int j = (2 * i + h) / Q, t = (2 * i + h) % Q;
+      c[h] = (DT == SIL_FP8_E4M3 && colb[j] + t < colend[j]) ? __ldg(a.cs + colb[j] + t) : 1.f;
+    }
+    csc[i] = make_float2(c[0], c[1]);
+  }
 
   const int64_t gw = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
@@ -414,108 +494,327 @@ __global__ void __launch_bounds__(kGatherThreads, 3) k_gather_reduce(GatherK a) 
     while (cur < e1) {
       while (__ldg(a.bstart + b + 1) <= uint32_t(cur)) ++b;  // skip empty buckets
       const int64_t se = min(e1, int64_t(__ldg(a.bstart + b + 1)));
-      const int kc = b < a.k ? b : b - a.k;  // cluster whose reference point shifts this bucket
-      float rsh[EL], acc[EL];
+      float2 rsh[EL2], acc[EL2];
+      load_shift<DT, CPL>(a, b, colb, colend, rsh);
 #pragma unroll
-      for (int j = 0; j < CPL; ++j)
+      for (int i = 0; i < EL2; ++i) acc[i] = make_float2(0.f, 0.f);
+      float2 sq2 = make_float2(0.f, 0.f);
+      float wacc = 0.f;
+      int64_t blk = cur;
+      uint32_t iv = blk + lane < se ? __ldg(a.idx + blk + lane) : 0u;
+      float wvb = (WEIGHTED && blk + lane < se) ? __ldg(a.widx + blk + lane) : 0.f;
+      while (blk < se) {
+        const int64_t nxt = blk + 32;
+        const uint32_t ivn = nxt + lane < se ? __ldg(a.idx + nxt + lane) : 0u;
+        const float wvn = (WEIGHTED && nxt + lane < se) ? __ldg(a.widx + nxt + lane) : 0.f;
+        const int cnt = int(min(int64_t(32), se - blk));
+        for (int p0 = 0; p0 < cnt; p0 += R * RPL) {
+          uint4 raw[RPL][CPL];
+          uint32_t rowv[RPL];
+          bool ok[RPL];
 #pragma unroll
-        for (int t = 0; t < Q; ++t) {
-          const int col = colb[j] + t;
-          rsh[j * Q + t] = col < colend[j] ? __ldg(a.rs + int64_t(kc) * a.dz + col) : 0.f;
-          acc[j * Q + t] = 0.f;
-        }
-      float sq = 0.f, wacc = 0.f;
-      for (int64_t base = cur; base < se; base += int64_t(R) * U) {
-        uint4 raw[U][CPL];
-        uint32_t rowv[U];
-        float wv[U];
-        bool ok[U];
+          for (int u = 0; u < RPL; ++u) {
+            const int pos = p0 + u * R + rg;
+            ok[u] = pos < cnt;
+            rowv[u] = __shfl_sync(0xffffffffu, iv, pos & 31);
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-          const int64_t en = base + int64_t(u) * R + rg;
-          ok[u] = en < se;
-          rowv[u] = ok[u] ? __ldg(a.idx + en) : 0u;
-          wv[u] = (weighted && ok[u]) ? __ldg(a.widx + en) : 0.f;
-#pragma unroll
-          for (int j = 0; j < CPL; ++j) {
-            const int ch = cl + G * j;
-            raw[u][j] = (ok[u] && ch < chn) ? load_chunk<DT>(a, rowv[u], (ch0 + ch) * Q) : make_uint4(0, 0, 0, 0);
+            for (int j = 0; j < CPL; ++j)
+              raw[u][j] = (ok[u] && colb[j] < colend[j]) ? load_chunk<DT>(a, rowv[u], colb[j]) : make_uint4(0, 0, 0, 0);
           }
-        }
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-          float v[EL];
+          for (int u = 0; u < RPL; ++u) {
+            float w = 1.f;
+            if (WEIGHTED) w = __shfl_sync(0xffffffffu, wvb, (p0 + u * R + rg) & 31);
+            float v[EL];
 #pragma unroll
-          for (int j = 0; j < CPL; ++j) Chunk<DT>::cvt(raw[u][j], v + j * Q);
+            for (int j = 0; j < CPL; ++j) Chunk<DT>::cvt(raw[u][j], v + j * Q);
+            float2 v2[EL2];
 #pragma unroll
-          for (int i = 0; i < EL; ++i) v[i] *= csc[i];
-          float sc = 1.f;
-          if (a.cosine) {
-            if (a.invnorm) {
-              sc = ok[u] ? __ldg(a.invnorm + rowv[u]) : 0.f;
-            } else {
-              float ss = 0.f;
-#pragma unroll
-              for (int i = 0; i < EL; ++i) ss = fmaf(v[i], v[i], ss);
-              for (int o = 1; o < G; o <<= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
-              if (ok[u] && !(ss > 0.f) && cl == 0) set_status(a.status, SIL_EZERONORM);
-              sc = ss > 0.f ? rsqrtf(ss) : 0.f;
+            for (int i = 0; i < EL2; ++i) {
+              v2[i] = make_float2(v[2 * i], v[2 * i + 1]);
+              if (DT == SIL_FP8_E4M3) v2[i] = __fmul2_rn(v2[i], csc[i]);
             }
-          }
-          if (ok[u]) {
-            const float w = wv[u];
-#pragma unroll
-            for (int i = 0; i < EL; ++i) {
-              float t = fmaf(sc, v[i], -rsh[i]);
-              if (weighted) {
-                t *= w;
+            float sc = 1.f;
+            if (COS) {
+              if (a.invnorm) {
+                sc = ok[u] ? __ldg(a.invnorm + rowv[u]) : 0.f;
               } else {
-                sq = fmaf(t, t, sq);
+                float2 ss = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int i = 0; i < EL2; ++i) ss = __ffma2_rn(v2[i], v2[i], ss);
+                float s1 = ss.x + ss.y;
+                for (int o = 1; o < G; o <<= 1) s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+                if (ok[u] && !(s1 > 0.f) && cl == 0) set_status(a.status, SIL_EZERONORM);
+                sc = s1 > 0.f ? rsqrtf(s1) : 0.f;
               }
-              acc[i] += t;
             }
-            wacc += w;
+            if (ok[u]) {
+              const float2 sc2 = make_float2(sc, sc);
+#pragma unroll
+              for (int i = 0; i < EL2; ++i) {
+                float2 t = __ffma2_rn(sc2, v2[i], rsh[i]);  // sc x - r
+                if (WEIGHTED) {
+                  t = __fmul2_rn(t, make_float2(w, w));
+                } else {
+                  sq2 = __ffma2_rn(t, t, sq2);
+                }
+                acc[i] = __fadd2_rn(acc[i], t);
+              }
+              if (WEIGHTED) wacc += w;
+            }
           }
         }
+        iv = ivn;
+        wvb = wvn;
+        blk = nxt;
       }
-      // fold the row groups: lanes with the same chunk position hold the same columns
-      for (int o = G; o < 32; o <<= 1) {
-#pragma unroll
-        for (int i = 0; i < EL; ++i) acc[i] += __shfl_xor_sync(0xffffffffu, acc[i], o);
-        wacc += __shfl_xor_sync(0xffffffffu, wacc, o);
-      }
-      // every lane now holds the run's total weight in wacc
-      const double m = weighted ? double(wacc) : double(se - cur);
-      double s2p = weighted ? 0.0 : double(sq);
-      if (rg == 0) {
-#pragma unroll
-        for (int j = 0; j < CPL; ++j)
-#pragma unroll
-          for (int t = 0; t < Q; ++t) {
-            const int col = colb[j] + t;
-            if (col >= colend[j]) continue;
-            const double r = rsh[j * Q + t], sv = acc[j * Q + t];
-            // weighted (backward) sums stay shifted: the gradient kernel
-            // works with sum w (x - r) and sum w directly
-            atomicAdd(a.s1 + int64_t(b) * a.d + col, weighted ? sv : sv + m * r);
-            if (!weighted) s2p += 2.0 * r * sv + m * r * r;
-          }
-      }
-      if (!weighted) {
-        for (int o = 16; o > 0; o >>= 1) s2p += __shfl_xor_sync(0xffffffffu, s2p, o);
-        if (lane == 0) atomicAdd(a.s2 + b, s2p);
-      } else if (lane == 0 && blockIdx.y == 0) {
-        atomicAdd(a.wsum + b, m);
-      }
+      run_flush<DT, CPL, WEIGHTED>(a, b, acc, rsh, sq2, wacc, WEIGHTED ? 0.0 : double(se - cur), colb, colend, G, rg, lane);
       cur = se;
     }
   }
 }
 
-template <int DT, int CPL>
-cudaError_t launch_gather_t(const GatherK& g, dim3 grid, cudaStream_t st) {
-  k_gather_reduce<DT, CPL><<<grid, kGatherThreads, 0, st>>>(g);
+// The same reduction with the rows brought into shared memory by the tensor
+// memory accelerator's row gather (cp.async.bulk.tensor ... tile::gather4,
+// four rows by index per instruction): every warp owns a ring of `stages`
+// 32-row blocks and keeps all but one of them in flight while it sums the
+// oldest one, so the bytes in flight per SM no longer depend on registers.
+// A block may cross bucket boundaries; rows are summed into the bucket they
+// belong to and the run is flushed where the bucket changes.  Waits are
+// bounded: on a timeout the warp flags SIL_ETIMEOUT, waits (bounded) for its
+// own copies in flight and stops.
+template <int DT, int CPL, bool WEIGHTED, bool COS>
+__global__ void __launch_bounds__(256, 1) k_gather_reduce_tma(GatherK a, const __grid_constant__ CUtensorMap xmap) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* base = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+  constexpr int Q = Chunk<DT>::Q;
+  constexpr int EL = CPL * Q;
+  constexpr int EL2 = EL / 2;
+  constexpr int esz = int(sizeof(typename Elem<DT>::T));
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  const int S = a.stages;
+  const int SB = 32 * a.rb;
+  unsigned char* ring = base + size_t(warp) * S * SB;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(base + size_t(nwarp) * S * SB) + warp * S;
+  if (lane < S) mbar_init(&bars[lane], 1);
+  fence_mbar_init();
+  __syncwarp();
+  const int G = a.G, R = 32 >> a.lgG;
+  const int rg = lane >> a.lgG, cl = lane & (G - 1);
+  const int RS = R < 32 ? R * (32 / R >= 2 ? 2 : 1) : 32;  // rows per step (two per lane group when they fit)
+  const uint32_t total = a.bstart[a.nb];
+  int colb[CPL], colend[CPL];
+#pragma unroll
+  for (int j = 0; j < CPL; ++j) {
+    const int ch = cl + G * j;
+    colb[j] = ch * Q;
+    colend[j] = ch < a.nch ? min(a.d, colb[j] + Q) : colb[j];
+  }
+  float2 csc[EL2];
+#pragma unroll
+  for (int i = 0; i < EL2; ++i) {
+    float c[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int j = (2 * i + h) / Q, t = (2 * i + h) % Q;
+      c[h] = (DT == SIL_FP8_E4M3 && colb[j] + t < colend[j]) ? __ldg(a.cs + colb[j] + t) : 1.f;
+    }
+    csc[i] = make_float2(c[0], c[1]);
+  }
+
+  uint32_t gblk = 0;  // blocks this warp has consumed (ring position and phase)
+  const int64_t gw = int64_t(blockIdx.x) * nwarp + warp;
+  const int64_t nw = int64_t(gridDim.x) * nwarp;
+  for (int64_t item = gw; item < a.nitems; item += nw) {
+    const int64_t e0 = item * a.wchunk;
+    const int64_t e1 = min(int64_t(total), e0 + a.wchunk);
+    if (e0 >= e1) break;
+    const int nblk = int(cdiv(e1 - e0, 32));
+    // rows of block t (dummy rows past e1 repeat the block's first row)
+    auto block_rows = [&](int t) -> uint32_t {
+      const int64_t e = e0 + int64_t(t) * 32 + lane;
+      const uint32_t r = e < e1 ? __ldg(a.idx + e) : 0xFFFFFFFFu;
+      const uint32_t r0 = __shfl_sync(0xffffffffu, r, 0);
+      return r == 0xFFFFFFFFu ? r0 : r;
+    };
+    auto issue = [&](int t, uint32_t rows) {
+      const int slot = int((gblk + uint32_t(t)) % uint32_t(S));
+      uint32_t rr[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) rr[q] = __shfl_sync(0xffffffffu, rows, (4 * lane + q) & 31);
+      if (lane == 0) mbar_arrive_expect_tx(&bars[slot], uint32_t(SB));
+      __syncwarp();
+      if (lane < 8)
+        tma_gather4(ring + size_t(slot) * SB + size_t(lane) * 4 * a.rb, &xmap, 0, int32_t(rr[0]), int32_t(rr[1]),
+                    int32_t(rr[2]), int32_t(rr[3]), &bars[slot]);
+    };
+    const int pre = nblk < S ? nblk : S;
+    for (int t = 0; t < pre; ++t) issue(t, block_rows(t));
+    uint32_t pending = pre < nblk ? block_rows(pre) : 0u;
+
+    // bucket holding e0
+    int lo = 0, hi = a.nb - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (__ldg(a.bstart + mid) <= uint32_t(e0)) lo = mid;
+      else hi = mid - 1;
+    }
+    int b = lo;
+    int64_t blo = e0;                                            // first entry of the current run
+    int64_t bend = min(e1, int64_t(__ldg(a.bstart + b + 1)));  // end of the current run
+    float2 rsh[EL2], acc[EL2];
+    load_shift<DT, CPL>(a, b, colb, colend, rsh);
+#pragma unroll
+    for (int i = 0; i < EL2; ++i) acc[i] = make_float2(0.f, 0.f);
+    float2 sq2 = make_float2(0.f, 0.f);
+    float wacc = 0.f;
+
+    for (int t = 0; t < nblk; ++t) {
+      const int slot = int((gblk + uint32_t(t)) % uint32_t(S));
+      const uint32_t par = ((gblk + uint32_t(t)) / uint32_t(S)) & 1u;
+      const int64_t eb = e0 + int64_t(t) * 32;
+      const float wblk = (WEIGHTED && eb + lane < e1) ? __ldg(a.widx + eb + lane) : 0.f;
+      if (!mbar_wait(&bars[slot], par)) {
+        if (lane == 0) set_status(a.status, SIL_ETIMEOUT);
+        // blocks t .. min(nblk, t + S) - 1 were issued and not consumed
+        for (int u = t; u < nblk && u < t + S; ++u)
+          mbar_wait(&bars[(gblk + uint32_t(u)) % uint32_t(S)], ((gblk + uint32_t(u)) / uint32_t(S)) & 1u);
+        return;
+      }
+      const unsigned char* blkp = ring + size_t(slot) * SB;
+      for (int p0 = 0; p0 < 32; p0 += RS) {
+        constexpr int RPL = 2;
+        uint4 raw[RPL][CPL];
+        int64_t ev[RPL];
+        bool in_blk[RPL];
+#pragma unroll
+        for (int u = 0; u < RPL; ++u) {
+          const int p = p0 + u * R + rg;
+          ev[u] = eb + p;
+          in_blk[u] = (u * R < RS) && p < 32 && ev[u] < e1;
+#pragma unroll
+          for (int j = 0; j < CPL; ++j)
+            raw[u][j] = (in_blk[u] && colb[j] < colend[j])
+                            ? *reinterpret_cast<const uint4*>(blkp + size_t(p) * a.rb + size_t(colb[j]) * esz)
+                            : make_uint4(0, 0, 0, 0);
+        }
+        float2 v2[RPL][EL2];
+        float scv[RPL], wv[RPL];
+#pragma unroll
+        for (int u = 0; u < RPL; ++u) {
+          float v[EL];
+#pragma unroll
+          for (int j = 0; j < CPL; ++j) Chunk<DT>::cvt(raw[u][j], v + j * Q);
+#pragma unroll
+          for (int i = 0; i < EL2; ++i) {
+            v2[u][i] = make_float2(v[2 * i], v[2 * i + 1]);
+            if (DT == SIL_FP8_E4M3) v2[u][i] = __fmul2_rn(v2[u][i], csc[i]);
+          }
+          scv[u] = 1.f;
+          if (COS) {
+            float2 ss = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int i = 0; i < EL2; ++i) ss = __ffma2_rn(v2[u][i], v2[u][i], ss);
+            float s1 = ss.x + ss.y;
+            for (int o = 1; o < G; o <<= 1) s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+            if (in_blk[u] && !(s1 > 0.f) && cl == 0) set_status(a.status, SIL_EZERONORM);
+            scv[u] = s1 > 0.f ? rsqrtf(s1) : 0.f;
+          }
+          wv[u] = WEIGHTED ? __shfl_sync(0xffffffffu, wblk, (p0 + u * R + rg) & 31) : 1.f;
+        }
+        // rows of this step go to the run they belong to; the step may cross runs
+        const int64_t slast = min(eb + p0 + RS, e1) - 1;  // last entry of the step
+        while (true) {
+#pragma unroll
+          for (int u = 0; u < RPL; ++u) {
+            if (!(in_blk[u] && ev[u] >= blo && ev[u] < bend)) continue;
+            const float2 sc2 = make_float2(scv[u], scv[u]);
+#pragma unroll
+            for (int i = 0; i < EL2; ++i) {
+              float2 tt = __ffma2_rn(sc2, v2[u][i], rsh[i]);  // sc x - r
+              if (WEIGHTED) {
+                tt = __fmul2_rn(tt, make_float2(wv[u], wv[u]));
+              } else {
+                sq2 = __ffma2_rn(tt, tt, sq2);
+              }
+              acc[i] = __fadd2_rn(acc[i], tt);
+            }
+            if (WEIGHTED) wacc += wv[u];
+          }
+          if (slast < bend) break;
+          // the run ends inside this step: add it and start the next bucket
+          run_flush<DT, CPL, WEIGHTED>(a, b, acc, rsh, sq2, wacc, double(bend - blo), colb, colend, G, rg, lane);
+          blo = bend;
+          while (__ldg(a.bstart + b + 1) <= uint32_t(blo)) ++b;
+          bend = min(e1, int64_t(__ldg(a.bstart + b + 1)));
+          load_shift<DT, CPL>(a, b, colb, colend, rsh);
+#pragma unroll
+          for (int i = 0; i < EL2; ++i) acc[i] = make_float2(0.f, 0.f);
+          sq2 = make_float2(0.f, 0.f);
+          wacc = 0.f;
+        }
+      }
+      __syncwarp();  // every lane is done with the slot before it is refilled
+      if (t + S < nblk) {
+        issue(t + S, pending);
+        pending = t + S + 1 < nblk ? block_rows(t + S + 1) : 0u;
+      }
+    }
+    if (bend > blo) run_flush<DT, CPL, WEIGHTED>(a, b, acc, rsh, sq2, wacc, double(bend - blo), colb, colend, G, rg, lane);
+    gblk += uint32_t(nblk);
+  }
+}
+
+// One wave of resident CTAs; each warp takes about four work items of the
+// sorted order.
+template <int DT, int CPL, bool WEIGHTED, bool COS>
+cudaError_t launch_gather_t(GatherK g, int64_t E, int slices, cudaStream_t st) {
+  auto fn = k_gather_reduce<DT, CPL, WEIGHTED, COS>;
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kGatherThreads, 0);
+  if (e != cudaSuccess) return e;
+  per_sm = std::max(1, per_sm);
+  const int64_t ctas = std::max<int64_t>(1, int64_t(kNumSMs) * per_sm / slices);
+  const int64_t warps = ctas * (kGatherThreads / 32);
+  g.wchunk = round_up(std::max<int64_t>(128, cdiv(E, warps * 4)), 32);
+  g.nitems = cdiv(E, g.wchunk);
+  const dim3 grid(unsigned(std::min<int64_t>(ctas, cdiv(g.nitems, kGatherThreads / 32))), unsigned(slices));
+  fn<<<grid, kGatherThreads, 0, st>>>(g);
   return cudaGetLastError();
+}
+
+// Rows into shared memory by TMA row gather: one persistent CTA per SM,
+// `warps` warps each with a ring of `stages` 32-row blocks.
+template <int DT, int CPL, bool WEIGHTED, bool COS>
+cudaError_t launch_gather_tma_t(GatherK g, const CUtensorMap& map, int64_t E, int warps, int smem,
+                                cudaStream_t st) {
+  auto fn = k_gather_reduce_tma<DT, CPL, WEIGHTED, COS>;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  const int64_t wtot = int64_t(kNumSMs) * warps;
+  g.wchunk = round_up(std::max<int64_t>(256, cdiv(E, wtot * 2)), 32);
+  g.nitems = cdiv(E, g.wchunk);
+  const unsigned grid = unsigned(std::max<int64_t>(1, std::min<int64_t>(kNumSMs, cdiv(g.nitems, warps))));
+  fn<<<grid, warps * 32, smem, st>>>(g, map);
+  return cudaGetLastError();
+}
+
+template <int DT, int CPL>
+cudaError_t launch_gather_tma_mode(const GatherK& g, const CUtensorMap& map, int64_t E, int warps, int smem,
+                                   cudaStream_t st) {
+  const bool w = g.widx != nullptr;
+  if (g.cosine)
+    return w ? launch_gather_tma_t<DT, CPL, true, true>(g, map, E, warps, smem, st)
+             : launch_gather_tma_t<DT, CPL, false, true>(g, map, E, warps, smem, st);
+  return w ? launch_gather_tma_t<DT, CPL, true, false>(g, map, E, warps, smem, st)
+           : launch_gather_tma_t<DT, CPL, false, false>(g, map, E, warps, smem, st);
+}
+
+template <int DT, int CPL>
+cudaError_t launch_gather_mode(const GatherK& g, int64_t E, int slices, cudaStream_t st) {
+  const bool w = g.widx != nullptr;
+  if (g.cosine) return w ? launch_gather_t<DT, CPL, true, true>(g, E, slices, st) : launch_gather_t<DT, CPL, false, true>(g, E, slices, st);
+  return w ? launch_gather_t<DT, CPL, true, false>(g, E, slices, st) : launch_gather_t<DT, CPL, false, false>(g, E, slices, st);
 }
 
 // Largest number of 16-byte chunks one lane handles (16 elements per lane).
@@ -571,7 +870,7 @@ cudaError_t launch_aggregate(const AggLaunch& L) {
   cudaError_t e = cudaMemsetAsync(L.bcount, 0, size_t(nb) * 4, L.stream);
   if (e != cudaSuccess) return e;
   {
-    const unsigned grid = unsigned(std::max<int64_t>(1, std::min<int64_t>(cdiv(E, 256 * 16), int64_t(kNumSMs) * 2)));
+    const unsigned grid = unsigned(std::max<int64_t>(1, std::min<int64_t>(cdiv(E, 256 * 8), int64_t(kNumSMs) * 8)));
     const size_t smem = nb <= kHistSmem ? size_t(nb) * 4 : 0;
     k_bucket_count<<<grid, 256, smem, L.stream>>>(en, E, nb, L.bcount);
   }
@@ -600,15 +899,23 @@ cudaError_t launch_aggregate(const AggLaunch& L) {
   g.cosine = L.dist == SIL_COSINE;
   g.vec = (reinterpret_cast<uintptr_t>(L.X) % 16 == 0) && (g.ldx_bytes % 16 == 0);
   g.nch = int(cdiv(L.d, q));
-  int cpl = 1, G = 1;
-  if (g.nch <= 32) {
-    while (G < g.nch) G <<= 1;
-  } else {
-    G = 32;
-    cpl = int(std::min<int64_t>(cdiv(g.nch, 32), max_cpl(L.dtype)));
-    if (cpl == 3) cpl = 4;
-    if (cpl > max_cpl(L.dtype)) cpl = max_cpl(L.dtype);
-  }
+  // TMA row gather when a whole row is one box of at most 512 bytes (rows
+  // padded to 32 bytes keep every 4-row destination 128-byte aligned);
+  // SIL_AGG_LDG=1 in the environment keeps the register-load kernel
+  const char* force_ldg = getenv("SIL_AGG_LDG");
+  const int dbox = int(round_up(L.d, 32 / esz));
+  const int rb = dbox * esz;
+  const bool tma = !(force_ldg && force_ldg[0] == '1') && g.vec && dbox <= 256 && rb <= 512;
+  // up to 16 elements per lane, as few lanes per row as that allows; rows
+  // read from shared memory take at least 8 lanes (128 contiguous bytes per
+  // 8-lane phase: no bank conflicts)
+  const int mc = max_cpl(L.dtype);
+  int G = 1;
+  if (tma)
+    while (G < 8 && G < g.nch) G <<= 1;
+  while (G < 32 && G * mc < g.nch) G <<= 1;
+  int cpl = int(std::min<int64_t>(mc, cdiv(g.nch, G)));
+  if (cpl == 3) cpl = 4;
   g.G = G;
   g.lgG = 0;
   while ((1 << g.lgG) < G) ++g.lgG;
@@ -619,20 +926,43 @@ cudaError_t launch_aggregate(const AggLaunch& L) {
   g.s2 = L.s2;
   g.wsum = L.wsum;
   g.status = L.status;
-  const int64_t warps = int64_t(kNumSMs) * 4 * (kGatherThreads / 32);
-  g.wchunk = round_up(std::max<int64_t>(256, cdiv(E, warps * 2)), 32);
-  g.nitems = cdiv(E, g.wchunk);
-  const dim3 grid(unsigned(std::min<int64_t>(cdiv(g.nitems, kGatherThreads / 32), int64_t(kNumSMs) * 4)),
-                  unsigned(slices));
+  if (tma && slices == 1) {
+    CUtensorMap map;
+    const CUtensorMapDataType tt = L.dtype == SIL_F32    ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                   : L.dtype == SIL_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                                         : CU_TENSOR_MAP_DATA_TYPE_UINT8;
+    if (encode_tmap_2d(&map, L.X, tt, esz, uint64_t(L.d), uint64_t(L.n), uint64_t(g.ldx_bytes), uint32_t(dbox), 1,
+                       CU_TENSOR_MAP_SWIZZLE_NONE)) {
+      const int sb = 32 * rb;
+      const int budget = 200 * 1024;
+      const int warps = std::max(1, std::min(8, budget / (3 * sb)));
+      const int stages = std::max(2, std::min(8, budget / (warps * sb)));
+      g.rb = rb;
+      g.stages = stages;
+      const int smem = warps * stages * sb + warps * stages * 8 + 1024;
+      switch (L.dtype) {
+        case SIL_F32:
+          return cpl == 1   ? launch_gather_tma_mode<SIL_F32, 1>(g, map, E, warps, smem, L.stream)
+                 : cpl == 2 ? launch_gather_tma_mode<SIL_F32, 2>(g, map, E, warps, smem, L.stream)
+                            : launch_gather_tma_mode<SIL_F32, 4>(g, map, E, warps, smem, L.stream);
+        case SIL_BF16:
+          return cpl == 1 ? launch_gather_tma_mode<SIL_BF16, 1>(g, map, E, warps, smem, L.stream)
+                          : launch_gather_tma_mode<SIL_BF16, 2>(g, map, E, warps, smem, L.stream);
+        default:
+          return launch_gather_tma_mode<SIL_FP8_E4M3, 1>(g, map, E, warps, smem, L.stream);
+      }
+    }
+  }
   switch (L.dtype) {
     case SIL_F32:
-      return cpl == 1   ? launch_gather_t<SIL_F32, 1>(g, grid, L.stream)
-             : cpl == 2 ? launch_gather_t<SIL_F32, 2>(g, grid, L.stream)
-                        : launch_gather_t<SIL_F32, 4>(g, grid, L.stream);
+      return cpl == 1   ? launch_gather_mode<SIL_F32, 1>(g, E, slices, L.stream)
+             : cpl == 2 ? launch_gather_mode<SIL_F32, 2>(g, E, slices, L.stream)
+                        : launch_gather_mode<SIL_F32, 4>(g, E, slices, L.stream);
     case SIL_BF16:
-      return cpl == 1 ? launch_gather_t<SIL_BF16, 1>(g, grid, L.stream) : launch_gather_t<SIL_BF16, 2>(g, grid, L.stream);
+      return cpl == 1 ? launch_gather_mode<SIL_BF16, 1>(g, E, slices, L.stream)
+                      : launch_gather_mode<SIL_BF16, 2>(g, E, slices, L.stream);
     default:
-      return launch_gather_t<SIL_FP8_E4M3, 1>(g, grid, L.stream);
+      return launch_gather_mode<SIL_FP8_E4M3, 1>(g, E, slices, L.stream);
   }
 }
 

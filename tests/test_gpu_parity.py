@@ -206,13 +206,22 @@ def test_batched_matches_oracle_per_labeling(metric):
 @pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16])
 @pytest.mark.parametrize("N,D,K", [(100003, 64, 100), (7777, 24, 6), (50001, 128, 1000), (3001, 256, 40),
                                    (20000, 600, 7), (30000, 16, 5000), (40000, 8, 20000)])
-def test_pass1_vector_and_elementwise_loads_agree(metric, dtype, N, D, K):
+def test_pass1_load_paths_agree(metric, dtype, N, D, K, monkeypatch):
+    # rows by TMA row gather (the default where a row fits one box), by
+    # 16-byte register loads, and element by element at an odd row stride.
     # D = 600 splits the rows into column slices (cosine then takes its norms
     # from a separate kernel); K = 5000 and 20000 exceed the shared-memory
     # bucket tables of the sort kernels, which then use global atomics
     X, lab = case(600 + N + D, N, D, K, metric)
     Xt, lt = to_dev(X, lab, dtype)
     fast = sil.aggregate(Xt, lt, K, metric)
+    monkeypatch.setenv("SIL_AGG_LDG", "1")
+    regs = sil.aggregate(Xt, lt, K, metric)
+    monkeypatch.delenv("SIL_AGG_LDG")
+    torch.cuda.synchronize()
+    assert torch.equal(fast[0], regs[0])
+    torch.testing.assert_close(fast[1], regs[1], rtol=1e-6, atol=1e-6 * float(regs[1].abs().max()))
+    torch.testing.assert_close(fast[2], regs[2], rtol=1e-6, atol=0.0)
     # the same rows at an odd row stride: no 16-byte loads are possible
     wide = torch.zeros(N, D + 1, dtype=dtype, device="cuda")
     wide[:, :D] = Xt
