@@ -362,7 +362,7 @@ def main():
     if ms_pass2 >= ms_pass1:
         kname, kbytes, kms = p2_kernel, bytes_pass2, ms_pass2
     else:
-        kname, kbytes, kms = "k_gather_reduce (pass 1)", bytes_pass1, ms_pass1
+        kname, kbytes, kms = "k_gather_reduce_tma (pass 1)", bytes_pass1, ms_pass1
     achieved = kbytes / (kms / 1e3) / 1e9
     roof = {"kernel": kname, "bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
             "frac": achieved / pk["hbm_gbs"], "traffic": None,
@@ -419,10 +419,10 @@ def main():
         cpu = cpu_oracle_sample(X.cpu().numpy(), lab.cpu().numpy(), K)
 
     if rank == 0:
-        # pass 1: rep_init, rep_find, shift_build, bucket_count, bucket_scan,
-        #         bucket_scatter, gather_reduce, publish_status;
+        # pass 1: bucket_count, bucket_scan, bucket_scatter, shift_build,
+        #         gather_reduce, publish_status;
         # pass 2: fin_global, fin_clusters, (tc_pack,) score, reduce_S
-        launches_per_step = 8 + (5 if plan is not None else 4)
+        launches_per_step = 6 + (5 if plan is not None else 4)
         line = {"metric": METRIC, "value": value, "unit": "points/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": t / args.steps * 1e3,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",

@@ -19,7 +19,7 @@
 //                        in FP32 registers while the bucket stays the same,
 //                        and add into the FP64 outputs once per run.
 // Values are accumulated shifted by a per-cluster reference point r_k (the
-// first row of cluster k among the first 65,536 rows), which keeps the FP32
+// first row of cluster k in the sorted order), which keeps the FP32
 // partials well conditioned when clusters sit far from the origin; a run's
 // sums are un-shifted in FP64 when they are added:
 //   s1 += sum(x - r) + m r,   s2 += sum||x - r||^2 + 2 r.sum(x - r) + m ||r||^2.
@@ -39,33 +39,21 @@ namespace {
 
 constexpr int kHistSmem = 12288;    // buckets privatised in shared memory by the count kernel
 constexpr int kScatterSmem = 4096;  // buckets privatised by the scatter kernel
-constexpr int kScatterIPT = 8;      // entries per thread of the scatter kernel
+constexpr int kScatterIPT = 16;     // entries per thread of the scatter kernel
 constexpr int kScanThreads = 1024;
 constexpr int kGatherThreads = 256;
 
-__global__ void k_rep_init(int32_t* rep, int32_t k) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < k) rep[i] = INT_MAX;
-}
-
-__global__ void k_rep_find(const int32_t* labels, int64_t m, int32_t k, int32_t* rep) {
-  int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (i < m) {
-    int32_t l = labels[i];
-    if (l >= 0 && l < k) atomicMin(&rep[l], int32_t(i));
-  }
-}
-
-// One CTA per cluster: rs[k][c] = x_rep (normalised for cosine), 0 when the
-// cluster has no point among the rows searched.
+// One CTA per cluster: rs[k][c] = x_r for the first row r of cluster k in
+// the sorted order (normalised for cosine), 0 when the cluster is empty.
 template <int DT>
-__global__ void k_shift_build(const void* X, int32_t d, int64_t ldx, const float* cs,
-                              const int32_t* rep, int32_t dist, float* rs, int32_t dz) {
+__global__ void k_shift_build(const void* X, int32_t d, int64_t ldx, const float* cs, const uint32_t* idx,
+                              const uint32_t* bstart, int32_t dist, float* rs, int32_t dz) {
   __shared__ float red[32];
   const int kk = blockIdx.x;
-  const int32_t r = rep[kk];
+  const bool empty = bstart[kk + 1] <= bstart[kk];
+  const int64_t r = empty ? 0 : int64_t(idx[bstart[kk]]);
   float* out = rs + int64_t(kk) * dz;
-  if (r == INT_MAX) {
+  if (empty) {
     for (int c = threadIdx.x; c < dz; c += blockDim.x) out[c] = 0.f;
     return;
   }
@@ -178,8 +166,16 @@ __global__ void __launch_bounds__(256) k_bucket_count(Entries en, int64_t E, int
       const int64_t e = base + i * stride + lane;
       b[i] = e < E ? en.bucket(e, true) : -1;
     }
+    // shared-memory counters take one fire-and-forget increment per label;
+    // global ones are aggregated per warp first
 #pragma unroll
-    for (int i = 0; i < UNR; ++i) warp_reserve(b[i], b[i] >= 0 ? (priv ? &hist[b[i]] : &bcount[b[i]]) : nullptr);
+    for (int i = 0; i < UNR; ++i) {
+      if (priv) {
+        if (b[i] >= 0) atomicAdd(&hist[b[i]], 1u);
+      } else {
+        warp_reserve(b[i], b[i] >= 0 ? &bcount[b[i]] : nullptr);
+      }
+    }
   }
   if (priv) {
     __syncthreads();
@@ -254,8 +250,10 @@ __global__ void __launch_bounds__(256) k_bucket_scatter(Entries en, int64_t E, i
     const int64_t e = c0 + int64_t(i) * 256 + tid;
     bk[i] = e < E ? en.bucket(e, false) : -1;
   }
+  // ranks within the CTA: one shared-memory atomic per entry (independent,
+  // so they pipeline); lanes hitting one counter get distinct values
 #pragma unroll
-  for (int i = 0; i < kScatterIPT; ++i) rk[i] = warp_reserve(bk[i], bk[i] >= 0 ? &lh[bk[i]] : nullptr);
+  for (int i = 0; i < kScatterIPT; ++i) rk[i] = bk[i] >= 0 ? atomicAdd(&lh[bk[i]], 1u) : 0u;
   __syncthreads();
   for (int b = tid; b < nb; b += 256) {
     const uint32_t c = lh[b];
@@ -828,22 +826,6 @@ bool agg_needs_invnorm(int32_t dtype, int32_t d) {
   return cdiv(d, q) > 32 * max_cpl(dtype);
 }
 
-cudaError_t launch_shift(const void* X, int32_t dtype, int64_t n, int32_t d, int64_t ldx,
-                         const float* cs, const int32_t* labels, int32_t k, int32_t dist,
-                         int32_t* rep, float* rs, cudaStream_t stream) {
-  const int dz = int(round_up(d, 4));
-  k_rep_init<<<unsigned(cdiv(k, 256)), 256, 0, stream>>>(rep, k);
-  const int64_t m = n < kRepRows ? n : kRepRows;
-  if (m > 0) k_rep_find<<<unsigned(cdiv(m, 256)), 256, 0, stream>>>(labels, m, k, rep);
-  const int th = 128;
-  switch (dtype) {
-    case SIL_F32: k_shift_build<SIL_F32><<<k, th, 0, stream>>>(X, d, ldx, cs, rep, dist, rs, dz); break;
-    case SIL_BF16: k_shift_build<SIL_BF16><<<k, th, 0, stream>>>(X, d, ldx, cs, rep, dist, rs, dz); break;
-    default: k_shift_build<SIL_FP8_E4M3><<<k, th, 0, stream>>>(X, d, ldx, cs, rep, dist, rs, dz); break;
-  }
-  return cudaGetLastError();
-}
-
 cudaError_t launch_invnorm(const void* X, int32_t dtype, int64_t n, int32_t d, int64_t ldx,
                            const float* cs, float* invnorm, uint32_t* status, cudaStream_t stream) {
   if (n == 0) return cudaSuccess;
@@ -877,6 +859,23 @@ cudaError_t launch_aggregate(const AggLaunch& L) {
   k_bucket_scan<<<1, kScanThreads, 0, L.stream>>>(L.bcount, nb, L.k, L.bstart, L.cursor, dual ? nullptr : L.count);
   k_bucket_scatter<<<unsigned(cdiv(E, 256 * kScatterIPT)), 256, 0, L.stream>>>(en, E, nb, L.cursor, L.idx,
                                                                               L.w1 ? L.widx : nullptr);
+  // reference points: the first row of each cluster's bucket (buckets k + c
+  // of the dual form share cluster c's)
+  {
+    const int dz = int(round_up(L.d, 4));
+    switch (L.dtype) {
+      case SIL_F32:
+        k_shift_build<SIL_F32><<<L.k, 128, 0, L.stream>>>(L.X, L.d, L.ldx, L.cs, L.idx, L.bstart, L.dist, L.rs, dz);
+        break;
+      case SIL_BF16:
+        k_shift_build<SIL_BF16><<<L.k, 128, 0, L.stream>>>(L.X, L.d, L.ldx, L.cs, L.idx, L.bstart, L.dist, L.rs, dz);
+        break;
+      default:
+        k_shift_build<SIL_FP8_E4M3><<<L.k, 128, 0, L.stream>>>(L.X, L.d, L.ldx, L.cs, L.idx, L.bstart, L.dist, L.rs,
+                                                                dz);
+        break;
+    }
+  }
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
 
   // 4: gather-reduce over the sorted order

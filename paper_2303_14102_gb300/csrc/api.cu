@@ -20,7 +20,6 @@ WsLayout ws_layout(int64_t n, int32_t d, int32_t k, int32_t dtype, int32_t dist,
     return at;
   };
   L.misc = take(64 * 4);
-  L.rep = take(K * 4);
   L.rs = take(K * dz * 4);
   L.g = take(dz * 8);
   L.gf = take(dz * 4);
@@ -105,7 +104,6 @@ int run_aggregate(const void* X, int32_t dtype, int64_t n, int32_t d, int64_t ld
   }
   if (n == 0) return SIL_OK;
   float* rs = at<float>(ws, L.rs);
-  SIL_TRY(cu(launch_shift(X, dtype, n, d, ldx, cs, labels, k, dist, at<int32_t>(ws, L.rep), rs, st)));
   const float* invnorm = nullptr;
   if (dist == SIL_COSINE && agg_needs_invnorm(dtype, d)) {
     SIL_TRY(cu(launch_invnorm(X, dtype, n, d, ldx, cs, at<float>(ws, L.invnorm), wst, st)));
@@ -255,8 +253,7 @@ int sil_score_backward(const void* X, int32_t dtype, int64_t n, int32_t d, int64
   if (n == 0) return cu(launch_publish_status(wst, dev_status, st));
   SIL_TRY(run_finalize(count, s1, s2, k, d, dist, ws, L, st));
   float* rs = at<float>(ws, L.rs);
-  SIL_TRY(cu(launch_shift(X, dtype, n, d, ldx, col_scale, labels, k, dist, at<int32_t>(ws, L.rep), rs,
-                          st)));
+  // rs is written by the dual pass 1 below, before the gradient kernel reads it
   const float* sa;
   const float* sb;
   const int32_t* skstar;
@@ -371,6 +368,20 @@ int sil_tensor_plan(int32_t dtype, int32_t d, int32_t k, int32_t* block_k, int32
   if (!block_k || !n_blocks || d <= 0 || k <= 0) return SIL_EINVAL;
   if (dtype < SIL_F32 || dtype > SIL_FP8_E4M3) return SIL_EINVAL;
   return tc_plan_query(dtype, d, k, block_k, n_blocks) ? SIL_OK : SIL_EUNSUPPORTED;
+}
+
+int sil_tensor_plan_candidates(int32_t dtype, int32_t d, int32_t k, int32_t* plans, int32_t max_plans,
+                               int32_t* n_plans) {
+  if (!plans || !n_plans || max_plans < 0 || d <= 0 || k <= 0) return SIL_EINVAL;
+  if (dtype < SIL_F32 || dtype > SIL_FP8_E4M3) return SIL_EINVAL;
+  *n_plans = tc_plan_candidates(dtype, d, k, plans, max_plans);
+  return SIL_OK;
+}
+
+int sil_tensor_plan_set(int32_t dtype, int32_t d, int32_t k, int32_t block_k, int32_t a_buffers,
+                        int32_t x_stages, int32_t stage_centroids) {
+  if (d <= 0 || k <= 0 || dtype < SIL_F32 || dtype > SIL_FP8_E4M3) return SIL_EINVAL;
+  return tc_plan_set(dtype, d, k, block_k, a_buffers, x_stages, stage_centroids);
 }
 
 const char* sil_status_string(int32_t status) {

@@ -50,6 +50,8 @@
 
 #include <algorithm>
 #include <cstdlib>
+#include <mutex>
+#include <vector>
 
 #include "sil_internal.cuh"
 #include "tma.cuh"
@@ -803,14 +805,22 @@ struct TcPlan {
   int kp, nblk, nxs, nab, zst, smem;
 };
 
-bool tc_plan(int32_t dtype, int32_t k, int32_t d, TcPlan* out) {
+// Plans chosen by measurement (sil_tensor_plan_set) for one (dtype, d, k);
+// they take precedence over the cost model.
+struct PlanOverride {
+  int32_t dtype, d, k, kp, nab, nxs, stage_z;
+};
+std::mutex g_plan_mu;
+std::vector<PlanOverride> g_plan_over;
+
+// Every plan whose shared memory fits, with its modelled cost.
+template <class F>
+void tc_plan_enumerate(int32_t dtype, int32_t k, int32_t d, F&& visit) {
   const int mode = mode_of(dtype);
   const bool staged = mode != kModeBF16;
   const int dp = int(round_up(d, 64));
   const int dz = int(round_up(d, 4));
   const int kmax = int(std::min<int64_t>(round_up(std::max(k, 16), 16), kMaxBlockN));
-  double best_cost = 0.0;
-  bool found = false;
   for (int kp = kmax; kp >= 16; kp -= 16) {
     const int nblk = int(cdiv(k, kp));
     for (int nab = 1; nab <= 4; ++nab) {
@@ -828,15 +838,38 @@ bool tc_plan(int32_t dtype, int32_t k, int32_t d, TcPlan* out) {
           if (staged && nxs == 2) cost *= 1.02;
           if (!staged && nab == 2) cost *= 1.02;
           if (!zst) cost *= 1.05;
-          if (!found || cost < best_cost) {
-            found = true;
-            best_cost = cost;
-            *out = TcPlan{kp, nblk, nxs, nab, zst, smem};
-          }
+          visit(TcPlan{kp, nblk, nxs, nab, zst, smem}, cost);
         }
       }
     }
   }
+}
+
+bool tc_plan(int32_t dtype, int32_t k, int32_t d, TcPlan* out) {
+  const int mode = mode_of(dtype);
+  const int dp = int(round_up(d, 64));
+  const int dz = int(round_up(d, 4));
+  {
+    std::lock_guard<std::mutex> lock(g_plan_mu);
+    for (const PlanOverride& o : g_plan_over) {
+      if (o.dtype != dtype || o.d != d || o.k != k) continue;
+      const int zst = o.stage_z ? dz + 4 : 0;
+      const int smem = tc_smem(mode, dp, o.kp, o.nxs, o.nab, zst).total;
+      if (smem <= kSmemMax) {
+        *out = TcPlan{o.kp, int(cdiv(k, o.kp)), o.nxs, o.nab, zst, smem};
+        return true;
+      }
+    }
+  }
+  double best_cost = 0.0;
+  bool found = false;
+  tc_plan_enumerate(dtype, k, d, [&](const TcPlan& p, double cost) {
+    if (!found || cost < best_cost) {
+      found = true;
+      best_cost = cost;
+      *out = p;
+    }
+  });
   return found;
 }
 
@@ -869,6 +902,41 @@ bool tc_plan_query(int32_t dtype, int32_t d, int32_t k, int32_t* block_k, int32_
   *block_k = p.kp;
   *n_blocks = p.nblk;
   return true;
+}
+
+int tc_plan_candidates(int32_t dtype, int32_t d, int32_t k, int32_t* plans, int32_t max_plans) {
+  if (d > 128 || d <= 0 || k <= 0) return 0;
+  std::vector<std::pair<double, TcPlan>> all;
+  tc_plan_enumerate(dtype, k, d, [&](const TcPlan& p, double cost) { all.emplace_back(cost, p); });
+  std::stable_sort(all.begin(), all.end(), [](const auto& a, const auto& b) { return a.first < b.first; });
+  int n = 0;
+  for (const auto& c : all) {
+    if (n >= max_plans) break;
+    plans[4 * n + 0] = c.second.kp;
+    plans[4 * n + 1] = c.second.nab;
+    plans[4 * n + 2] = c.second.nxs;
+    plans[4 * n + 3] = c.second.zst ? 1 : 0;
+    ++n;
+  }
+  return n;
+}
+
+int tc_plan_set(int32_t dtype, int32_t d, int32_t k, int32_t kp, int32_t nab, int32_t nxs, int32_t stage_z) {
+  std::lock_guard<std::mutex> lock(g_plan_mu);
+  for (size_t i = 0; i < g_plan_over.size(); ++i)
+    if (g_plan_over[i].dtype == dtype && g_plan_over[i].d == d && g_plan_over[i].k == k) {
+      g_plan_over.erase(g_plan_over.begin() + long(i));
+      break;
+    }
+  if (kp == 0) return SIL_OK;  // cleared: back to the cost model
+  if (d > 128 || kp < 16 || kp > kMaxBlockN || kp % 16 || nab < 1 || nab > 4 || nxs < 1 || nxs > 3)
+    return SIL_EINVAL;
+  const int mode = mode_of(dtype);
+  const int zst = stage_z ? int(round_up(d, 4)) + 4 : 0;
+  if (tc_smem(mode, int(round_up(d, 64)), kp, mode == kModeBF16 ? 1 : nxs, nab, zst).total > kSmemMax)
+    return SIL_EUNSUPPORTED;
+  g_plan_over.push_back(PlanOverride{dtype, d, k, kp, nab, mode == kModeBF16 ? 1 : nxs, stage_z ? 1 : 0});
+  return SIL_OK;
 }
 
 size_t tc_pack_bytes(int32_t k, int32_t d) {

@@ -20,7 +20,6 @@ namespace sil {
 
 constexpr int kScoreThreads = 256;   // threads per SIMT pass-2 CTA
 constexpr int kMaxPartials = 8192;   // per-CTA partial sums of s_i
-constexpr int kRepRows = 65536;      // rows searched for per-cluster reference points
 constexpr int kNumSMs = 152;         // GB300
 constexpr int kSmemBudget = 100 * 1024;  // dynamic shared memory per CTA we aim for
 
@@ -38,7 +37,6 @@ inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 struct WsLayout {
   size_t misc;      // uint32 flags[64]
-  size_t rep;       // int32[k]          first row of each cluster among the first kRepRows
   size_t rs;        // float[k*dz]       per-cluster shift (reference point)
   size_t g;         // double[dz]        global centre
   size_t gf;        // float[dz]
@@ -139,7 +137,7 @@ struct AggLaunch {
   const float* w2;         // weights of entry 1 (dual)
   int32_t k;
   int32_t dist;
-  const float* rs;         // shift [k][dz]
+  float* rs;               // out: shift [k][dz] (the reference point of each cluster)
   const float* invnorm;    // nullable
   unsigned long long* count;
   double* s1;
@@ -156,10 +154,6 @@ struct AggLaunch {
   cudaStream_t stream;
 };
 
-// Enqueue the reference-point search and shift table (ws.rep, ws.rs).
-cudaError_t launch_shift(const void* X, int32_t dtype, int64_t n, int32_t d, int64_t ldx,
-                         const float* cs, const int32_t* labels, int32_t k, int32_t dist,
-                         int32_t* rep, float* rs, cudaStream_t stream);
 // Enqueue 1/||x_i|| for every row (cosine, column-sliced pass 1).
 cudaError_t launch_invnorm(const void* X, int32_t dtype, int64_t n, int32_t d, int64_t ldx,
                            const float* cs, float* invnorm, uint32_t* status, cudaStream_t stream);
@@ -213,8 +207,12 @@ cudaError_t launch_score_simt(ScoreLaunch& s);
 bool tc_eligible(int32_t dtype, int64_t n, int32_t d, int64_t ldx, int32_t k, const void* X,
                  const int32_t* labels);
 size_t tc_pack_bytes(int32_t k, int32_t d);
-// Host-only: the cluster-block plan (false when none fits).
+// Host-only: the cluster-block plan (false when none fits), the feasible
+// plans ranked by the cost model (4 ints each: block_k, A buffers, X
+// stages, staged centroids), and a measured choice for one shape.
 bool tc_plan_query(int32_t dtype, int32_t d, int32_t k, int32_t* block_k, int32_t* n_blocks);
+int tc_plan_candidates(int32_t dtype, int32_t d, int32_t k, int32_t* plans, int32_t max_plans);
+int tc_plan_set(int32_t dtype, int32_t d, int32_t k, int32_t kp, int32_t nab, int32_t nxs, int32_t stage_z);
 // Bytes of the per-block results when k needs several cluster blocks (else 0).
 size_t tc_partial_bytes(int64_t n, int32_t d, int32_t k, int32_t dtype);
 cudaError_t launch_score_tc(const ScoreLaunch& s, const double* g, void* pack, void* partial_ws,

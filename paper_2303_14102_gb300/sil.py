@@ -31,8 +31,8 @@ SIL_AGG_ACCUMULATE = 1
 METRICS = {"sqeuclidean": 0, "cosine": 1}
 PATHS = {"auto": 0, "simt": 1, "tensor": 2}
 EXPORTED = ("sil_workspace_size", "sil_saved_size", "sil_aggregate", "sil_score",
-            "sil_score_backward", "sil_score_batched", "sil_tensor_plan", "sil_status_string",
-            "sil_version")
+            "sil_score_backward", "sil_score_batched", "sil_tensor_plan", "sil_tensor_plan_candidates",
+            "sil_tensor_plan_set", "sil_status_string", "sil_version")
 
 _lock = threading.Lock()
 _lib = None
@@ -79,6 +79,10 @@ def load(build_if_stale: bool = True) -> ctypes.CDLL:
             lib.sil_score_noalloc.restype = ctypes.c_int
             lib.sil_tensor_plan.argtypes = [i32, i32, i32, vp, vp]
             lib.sil_tensor_plan.restype = ctypes.c_int
+            lib.sil_tensor_plan_candidates.argtypes = [i32, i32, i32, vp, i32, vp]
+            lib.sil_tensor_plan_candidates.restype = ctypes.c_int
+            lib.sil_tensor_plan_set.argtypes = [i32, i32, i32, i32, i32, i32, i32]
+            lib.sil_tensor_plan_set.restype = ctypes.c_int
             lib.sil_status_string.argtypes = [i32]
             lib.sil_status_string.restype = ctypes.c_char_p
             lib.sil_version.restype = i32
@@ -290,12 +294,62 @@ def tensor_plan(dtype: torch.dtype, D: int, K: int):
     """(clusters per block, number of blocks) of the tensor-core pass 2, or None."""
     lib = load()
     bk, nb = ctypes.c_int32(0), ctypes.c_int32(0)
-    code = {torch.float32: 0, torch.bfloat16: 1, torch.float8_e4m3fn: 2}[dtype]
-    rc = lib.sil_tensor_plan(code, D, K, ctypes.byref(bk), ctypes.byref(nb))
+    rc = lib.sil_tensor_plan(_DTYPES[dtype], D, K, ctypes.byref(bk), ctypes.byref(nb))
     if rc == SIL_EUNSUPPORTED:
         return None
     _rc(rc, "sil_tensor_plan")
     return bk.value, nb.value
+
+
+_DTYPES = {torch.float32: 0, torch.bfloat16: 1, torch.float8_e4m3fn: 2}
+
+
+def tensor_plan_candidates(dtype: torch.dtype, D: int, K: int, max_plans: int = 8):
+    """Feasible tensor-path plans (block_k, A buffers, X stages, staged centroids), best modelled first."""
+    lib = load()
+    buf = (ctypes.c_int32 * (4 * max_plans))()
+    n = ctypes.c_int32(0)
+    _rc(lib.sil_tensor_plan_candidates(_DTYPES[dtype], D, K, buf, max_plans, ctypes.byref(n)),
+        "sil_tensor_plan_candidates")
+    return [tuple(buf[4 * i:4 * i + 4]) for i in range(n.value)]
+
+
+def tensor_plan_set(dtype: torch.dtype, D: int, K: int, plan=None) -> None:
+    """Make `plan` (from tensor_plan_candidates) the choice for this shape; None restores the model."""
+    lib = load()
+    bk, nab, nxs, stz = plan if plan is not None else (0, 0, 0, 0)
+    _rc(lib.sil_tensor_plan_set(_DTYPES[dtype], D, K, bk, nab, nxs, stz), "sil_tensor_plan_set")
+
+
+def autotune(X: torch.Tensor, labels: torch.Tensor, K: int, metric: str = "sqeuclidean",
+             col_scale: torch.Tensor | None = None, max_plans: int = 6, reps: int = 3):
+    """Time pass 2 under each of the best-modelled tensor-path plans for this
+    shape on these inputs and keep the fastest for the rest of the process.
+
+    Returns [(seconds per call, plan), ...] in the order tried (empty when the
+    tensor path does not serve the shape).  The timing runs the real kernels
+    on the caller's data; nothing is cached across processes.
+    """
+    N, D = X.shape
+    plans = tensor_plan_candidates(X.dtype, D, K, max_plans)
+    if not plans or tensor_plan(X.dtype, D, K) is None:
+        return []
+    agg = aggregate(X, labels, K, metric, col_scale=col_scale)
+    stream = torch.cuda.current_stream(X.device)
+    results = []
+    for plan in plans:
+        tensor_plan_set(X.dtype, D, K, plan)
+        score(X, labels, K, agg, metric, col_scale=col_scale, path="tensor")
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            score(X, labels, K, agg, metric, col_scale=col_scale, path="tensor")
+        e1.record(stream)
+        torch.cuda.synchronize(X.device)
+        results.append((e0.elapsed_time(e1) / 1e3 / reps, plan))
+    best = min(results)[1]
+    tensor_plan_set(X.dtype, D, K, best)
+    return results
 
 
 def silhouette(X: torch.Tensor, labels: torch.Tensor, K: int, metric: str = "sqeuclidean",

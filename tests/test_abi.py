@@ -124,3 +124,25 @@ def test_tensor_plan_rejects_bad_arguments(lib):
     assert lib.sil_tensor_plan(0, 64, 100, None, ctypes.byref(out)) == sil.SIL_EINVAL
     assert lib.sil_tensor_plan(7, 64, 100, ctypes.byref(out), ctypes.byref(out)) == sil.SIL_EINVAL
     assert lib.sil_tensor_plan(0, 64, 0, ctypes.byref(out), ctypes.byref(out)) == sil.SIL_EINVAL
+
+
+def test_tensor_plan_candidates_and_override():
+    import torch
+    cands = sil.tensor_plan_candidates(torch.float32, 64, 100, 8)
+    assert 1 <= len(cands) <= 8
+    assert cands[0][0] == sil.tensor_plan(torch.float32, 64, 100)[0]  # best modelled first
+    for bk, nab, nxs, stz in cands:
+        assert bk % 16 == 0 and 1 <= nab <= 4 and 1 <= nxs <= 3 and stz in (0, 1)
+    try:
+        sil.tensor_plan_set(torch.float32, 64, 100, (48, 2, 2, 0))
+        assert sil.tensor_plan(torch.float32, 64, 100) == (48, 3)
+        assert sil.tensor_plan(torch.float32, 64, 101) == (112, 1)  # other shapes untouched
+    finally:
+        sil.tensor_plan_set(torch.float32, 64, 100, None)
+    assert sil.tensor_plan(torch.float32, 64, 100) == (112, 1)
+
+
+def test_tensor_plan_set_rejects_bad_plans(lib):
+    assert lib.sil_tensor_plan_set(0, 64, 100, 40, 2, 2, 0) == sil.SIL_EINVAL      # not a multiple of 16
+    assert lib.sil_tensor_plan_set(0, 64, 100, 256, 4, 3, 1) == sil.SIL_EUNSUPPORTED  # too much shared memory
+    assert lib.sil_tensor_plan_set(0, 256, 100, 64, 2, 2, 0) == sil.SIL_EINVAL     # d > 128
