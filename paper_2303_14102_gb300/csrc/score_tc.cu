@@ -197,8 +197,13 @@ __host__ __device__ constexpr int raw_tile_bytes(int mode, int dp) {
 }
 
 // zst: row stride (floats) of the staged centroids, 0 = read them from global memory.
+// FP32 rows wider than 128 columns (dp = 256) use the K-chunked layout: the A
+// buffers and raw X stages hold one 64-column chunk of a tile, and the row
+// terms live in a ring of two tile slots of their own.
 __host__ __device__ inline TcSmem tc_smem(int mode, int dp, int kp, int nxs, int nab, int zst) {
   const int natom = dp / 64;
+  const bool wide = dp > 128;
+  const int natom_a = wide ? 1 : natom;  // atoms of one A buffer
   const bool staged = mode != kModeBF16;
   TcSmem s;
   int o = 0;
@@ -207,15 +212,15 @@ __host__ __device__ inline TcSmem tc_smem(int mode, int dp, int kp, int nxs, int
   s.zl = o; o += natom * kp * 128;
   o = (o + 1023) & ~1023;
   s.abuf = o;
-  s.lo_off = natom * kAtomBytes;
-  s.abuf_stride = natom * kAtomBytes * (mode == kModeF32 ? 2 : 1);
+  s.lo_off = natom_a * kAtomBytes;
+  s.abuf_stride = natom_a * kAtomBytes * (mode == kModeF32 ? 2 : 1);
   o += nab * s.abuf_stride;
   s.xs = o;
-  s.xs_stride = staged ? raw_tile_bytes(mode, dp) + 1024 : 0;  // + labels (512 B), keeps 1024 alignment
+  s.xs_stride = staged ? raw_tile_bytes(mode, wide ? 64 : dp) + 1024 : 0;  // + labels (512 B), keeps 1024 alignment
   o += staged ? nxs * s.xs_stride : 0;
   s.side = o;
   s.side_stride = kTM * 16 + 512;  // xn2, aown, inv, code + labels (BF16 mode)
-  o += nab * s.side_stride;
+  o += (wide ? 2 : nab) * s.side_stride;
   s.cb = o; o += kp * 4 + 16;  // + 4 floats of block-reduction scratch
   o = (o + 15) & ~15;
   s.gsm = o; o += dp * 4;
@@ -224,18 +229,18 @@ __host__ __device__ inline TcSmem tc_smem(int mode, int dp, int kp, int nxs, int
   s.zst = zst;
   s.zsm = o; o += kp * zst * 4;
   o = (o + 15) & ~15;
-  s.bars = o; o += 8 * (2 * nxs + 4 * nab + 4 + 1) + 16;  // + TMEM base, abort flag
+  s.bars = o; o += 8 * (2 * nxs + 4 * nab + 4 + 1 + (wide ? 4 : 0)) + 16;  // + TMEM base, abort flag
   s.total = o + 1024;  // slack for aligning the dynamic base to 1024
   return s;
 }
 
 struct TcBars {
-  uint64_t *xfull, *xempty, *afull, *aempty, *pfull, *accfull, *accempty, *zfull;
+  uint64_t *xfull, *xempty, *afull, *aempty, *pfull, *accfull, *accempty, *zfull, *sfull, *sempty;
   uint32_t* tmem_base;
   int* abort_flag;
 };
 
-__device__ inline TcBars tc_bars(unsigned char* base, const TcSmem& L, int nxs, int nab) {
+__device__ inline TcBars tc_bars(unsigned char* base, const TcSmem& L, int nxs, int nab, bool wide = false) {
   TcBars b;
   uint64_t* p = reinterpret_cast<uint64_t*>(base + L.bars);
   b.xfull = p; p += nxs;
@@ -246,6 +251,8 @@ __device__ inline TcBars tc_bars(unsigned char* base, const TcSmem& L, int nxs, 
   b.accfull = p; p += 2;
   b.accempty = p; p += 2;
   b.zfull = p; p += 1;
+  b.sfull = p; p += wide ? 2 : 0;
+  b.sempty = p; p += wide ? 2 : 0;
   b.tmem_base = reinterpret_cast<uint32_t*>(p);
   b.abort_flag = reinterpret_cast<int*>(p) + 1;
   return b;
@@ -702,6 +709,391 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_score_tc(TcK a, const __grid_
   }
 }
 
+// FP32 rows of 129..256 columns.  The same roles and epilogue as k_score_tc,
+// but the GEMM runs over K-chunks of 64 columns: the producer loads one chunk
+// of a tile per raw stage (labels with chunk 0), converter threads split one
+// chunk at a time into an A buffer while they accumulate their row terms over
+// the chunks, and the MMA warp accumulates the four chunks of a tile into one
+// TMEM accumulator.  The split centroids of all 256 columns stay resident.
+// Row terms: squared Euclidean uses the exact difference forms chunk by
+// chunk; cosine needs 1/||x|| before x' exists, so it accumulates x.x, x.g,
+// x.(g + mu'_c), g.g and ||g + mu'_c||^2 and forms ||x' ||^2 and
+// ||x' - mu'_c||^2 from them at the end (all terms are O(1) for unit vectors).
+template <bool SAVE>
+__global__ void __launch_bounds__(kTcThreads, 1) k_score_tc_wide(TcK a, const __grid_constant__ TcMaps maps) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* base = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+  constexpr int DP = 256, NCH = 4, natom = 4;
+  const TcSmem L = tc_smem(kModeF32, DP, a.kp, a.nxs, a.nab, a.zst);
+  const TcBars B = tc_bars(base, L, a.nxs, a.nab, true);
+  volatile int* abort_flag = B.abort_flag;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t ntiles = cdiv(a.n, kTM);
+  const int my_tiles = blockIdx.x < ntiles ? int(cdiv(ntiles - blockIdx.x, gridDim.x)) : 0;
+  const int kb0 = int(blockIdx.y) * a.kp;
+  const int kblk = min(a.kp, a.k - kb0);
+  const bool fused = a.nblk == 1;
+  float* cbs = reinterpret_cast<float*>(base + L.cb);
+
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < a.nxs; ++i) {
+      mbar_init(&B.xfull[i], 1);
+      mbar_init(&B.xempty[i], kConvWarps);
+    }
+    for (int i = 0; i < a.nab; ++i) {
+      mbar_init(&B.afull[i], kConvWarps);
+      mbar_init(&B.aempty[i], 1);  // MMA commit
+    }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&B.accfull[i], 1);
+      mbar_init(&B.accempty[i], 4);
+      mbar_init(&B.sfull[i], kConvWarps);
+      mbar_init(&B.sempty[i], 4);
+    }
+    mbar_init(B.zfull, 1);
+    *B.abort_flag = 0;
+    fence_mbar_init();
+  }
+  for (int i = threadIdx.x; i < a.kp; i += blockDim.x) cbs[i] = a.cb[kb0 + i];
+  float* gsm = reinterpret_cast<float*>(base + L.gsm);
+  float4* clsm = reinterpret_cast<float4*>(base + L.clsm);
+  float* zsm = reinterpret_cast<float*>(base + L.zsm);
+  for (int i = threadIdx.x; i < DP; i += blockDim.x) gsm[i] = i < a.dz ? a.gf[i] : 0.f;
+  for (int i = threadIdx.x; i < kblk; i += blockDim.x) clsm[i] = a.cl[kb0 + i];
+  if (a.zst)
+    for (int i = threadIdx.x; i < kblk * a.zst; i += blockDim.x) {
+      const int kk = i / a.zst, c = i - kk * a.zst;
+      zsm[i] = c < a.dz ? a.zf[int64_t(kb0 + kk) * a.dz + c] : 0.f;
+    }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(B.tmem_base)),
+                 "r"(2 * a.acc_cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    tc_fence_before();
+  }
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *B.tmem_base;
+  constexpr int raw = 2 * kAtomBytes;  // two 32-column FP32 boxes per chunk
+
+  if (warp == 0) {
+    // ------------------------------------------------------- TMA producer
+    if (lane == 0) {
+      mbar_arrive_expect_tx(B.zfull, uint32_t(2 * natom * a.kp * 128));
+      for (int at = 0; at < natom; ++at) {
+        tma_load_2d(base + L.zh + at * a.kp * 128, &maps.zh, at * 64, kb0, B.zfull);
+        tma_load_2d(base + L.zl + at * a.kp * 128, &maps.zl, at * 64, kb0, B.zfull);
+      }
+      int u = 0;
+      for (int t = 0; t < my_tiles && !*abort_flag; ++t) {
+        const int32_t row0 = int32_t((blockIdx.x + int64_t(t) * gridDim.x) * kTM);
+        for (int c = 0; c < NCH; ++c, ++u) {
+          const int j = u % a.nxs;
+          if (!tc_wait(&B.xempty[j], ((u / a.nxs) & 1) ^ 1, abort_flag, a.status)) break;
+          unsigned char* xs = base + L.xs + j * L.xs_stride;
+          mbar_arrive_expect_tx(&B.xfull[j], uint32_t(raw + (c == 0 ? kTM * 4 : 0)));
+          tma_load_2d(xs, &maps.x, c * 64, row0, &B.xfull[j]);
+          tma_load_2d(xs + kAtomBytes, &maps.x, c * 64 + 32, row0, &B.xfull[j]);
+          if (c == 0) tma_load_1d(xs + raw, &maps.lab, row0, &B.xfull[j]);
+        }
+      }
+      if (*abort_flag) {
+        const int first = u - a.nxs > 0 ? u - a.nxs : 0;
+        for (int v = first; v < u; ++v) mbar_wait(&B.xfull[v % a.nxs], uint32_t((v / a.nxs) & 1));
+        mbar_wait(B.zfull, 0);
+      }
+    }
+  } else if (warp == 1) {
+    // --------------------------------------------------------- MMA issuer
+    if (lane == 0) {
+      const uint32_t idesc = umma_idesc_bf16(kTM, a.kp);
+      int u = 0, issued = -1;
+      bool ok = tc_wait(B.zfull, 0, abort_flag, a.status);
+      for (int t = 0; ok && t < my_tiles; ++t) {
+        const int bsel = t & 1;
+        if (!tc_wait(&B.accempty[bsel], ((t >> 1) & 1) ^ 1, abort_flag, a.status)) break;
+        const uint32_t d_tmem = tmem + uint32_t(bsel * a.acc_cols);
+        for (int c = 0; c < NCH; ++c, ++u) {
+          const int i = u % a.nab;
+          if (!tc_wait(&B.afull[i], (u / a.nab) & 1, abort_flag, a.status)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t ahi = smem_u32(base + L.abuf + i * L.abuf_stride);
+          const uint32_t alo = ahi + uint32_t(L.lo_off);
+          const uint32_t zh = smem_u32(base + L.zh) + uint32_t(c * a.kp * 128);
+          const uint32_t zl = smem_u32(base + L.zl) + uint32_t(c * a.kp * 128);
+#pragma unroll
+          for (int ks = 0; ks < 4; ++ks) {
+            const uint32_t ao = uint32_t(ks * 32), bo = uint32_t(ks * 32);
+            umma_bf16(d_tmem, umma_desc_sw128(ahi + ao), umma_desc_sw128(zh + bo), idesc, (c | ks) != 0);
+            umma_bf16(d_tmem, umma_desc_sw128(ahi + ao), umma_desc_sw128(zl + bo), idesc, 1);
+            umma_bf16(d_tmem, umma_desc_sw128(alo + ao), umma_desc_sw128(zh + bo), idesc, 1);
+          }
+          umma_commit(&B.aempty[i]);
+          issued = u;
+        }
+        if (!ok) break;
+        umma_commit(&B.accfull[bsel]);
+      }
+      if (*abort_flag && issued >= 0) {
+        // every MMA issued so far has completed once its last commit arrived
+        mbar_wait(&B.aempty[issued % a.nab], uint32_t((issued / a.nab) & 1));
+      }
+    }
+  } else if (warp < kEpiWarp0) {
+    // ------------------------------------------------ converter warps 2..9
+    constexpr int HP = 32;  // columns of a chunk per thread (half of 64)
+    const int h = lane >> 4;
+    const int r = (warp - 2) * 16 + (lane & 15);
+    const bool cosine = a.cosine != 0;
+    int u = 0;
+    for (int t = 0; t < my_tiles; ++t) {
+      const int64_t row = (blockIdx.x + int64_t(t) * gridDim.x) * kTM + r;
+      int own = -1, olc = 0;
+      bool valid = row < a.n, in_blk = false;
+      // squared Euclidean: s0 = ||x'||^2, s1 = ||x' - mu'_c||^2 (exact forms);
+      // cosine: x.x, x.g, x.(g + mu'_c), g.g, ||g + mu'_c||^2
+      float2 s0 = make_float2(0.f, 0.f), s1 = s0, s2 = s0, s3 = s0, s4 = s0;
+      bool stop = false;
+      for (int c = 0; c < NCH; ++c, ++u) {
+        const int i = u % a.nab, j = u % a.nxs;
+        if (!tc_wait(&B.xfull[j], (u / a.nxs) & 1, abort_flag, a.status) ||
+            !tc_wait(&B.aempty[i], ((u / a.nab) & 1) ^ 1, abort_flag, a.status)) {
+          stop = true;
+          break;
+        }
+        const unsigned char* xs = base + L.xs + j * L.xs_stride;
+        unsigned char* ab = base + L.abuf + i * L.abuf_stride;
+        if (c == 0) {
+          own = reinterpret_cast<const int32_t*>(xs + raw)[r];
+          if (valid && (own < 0 || own >= a.k)) {
+            if (h == 0) set_status(a.status, SIL_ELABEL);
+            valid = false;
+          }
+          const int ol = own - kb0;
+          in_blk = valid && ol >= 0 && ol < kblk;
+          olc = in_blk ? ol : 0;
+        }
+        float x[HP];
+#pragma unroll
+        for (int c4 = 0; c4 < HP / 4; ++c4) {
+          const float4 v = *reinterpret_cast<const float4*>(xs + h * kAtomBytes + sw128(r, c4));
+          x[4 * c4 + 0] = v.x;
+          x[4 * c4 + 1] = v.y;
+          x[4 * c4 + 2] = v.z;
+          x[4 * c4 + 3] = v.w;
+        }
+#pragma unroll
+        for (int c4 = 0; c4 < HP / 4; ++c4) {
+          const int col = c * 64 + h * HP + 4 * c4;  // global column
+          const float4 g = *reinterpret_cast<const float4*>(gsm + col);
+          float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (col < a.dz) {
+            if (a.zst)
+              z = *reinterpret_cast<const float4*>(zsm + olc * a.zst + col);
+            else
+              z = __ldg(reinterpret_cast<const float4*>(a.zf + int64_t(kb0 + olc) * a.dz + col));
+          }
+          const float2 xa = make_float2(x[4 * c4], x[4 * c4 + 1]), xb = make_float2(x[4 * c4 + 2], x[4 * c4 + 3]);
+          const float2 ga = make_float2(g.x, g.y), gb = make_float2(g.z, g.w);
+          if (!cosine) {
+            const float2 ca = __fadd2_rn(xa, make_float2(-g.x, -g.y));
+            const float2 cb = __fadd2_rn(xb, make_float2(-g.z, -g.w));
+            s0 = __ffma2_rn(ca, ca, s0);
+            s0 = __ffma2_rn(cb, cb, s0);
+            const float2 da = __fadd2_rn(ca, make_float2(-z.x, -z.y));
+            const float2 db = __fadd2_rn(cb, make_float2(-z.z, -z.w));
+            s1 = __ffma2_rn(da, da, s1);
+            s1 = __ffma2_rn(db, db, s1);
+          } else {
+            const float2 gza = __fadd2_rn(ga, make_float2(z.x, z.y)), gzb = __fadd2_rn(gb, make_float2(z.z, z.w));
+            s0 = __ffma2_rn(xa, xa, s0);
+            s0 = __ffma2_rn(xb, xb, s0);
+            s1 = __ffma2_rn(xa, ga, s1);
+            s1 = __ffma2_rn(xb, gb, s1);
+            s2 = __ffma2_rn(xa, gza, s2);
+            s2 = __ffma2_rn(xb, gzb, s2);
+            s3 = __ffma2_rn(ga, ga, s3);
+            s3 = __ffma2_rn(gb, gb, s3);
+            s4 = __ffma2_rn(gza, gza, s4);
+            s4 = __ffma2_rn(gzb, gzb, s4);
+          }
+        }
+        // hi/lo BF16 split of this thread's 32 columns of the chunk
+#pragma unroll
+        for (int c8 = 0; c8 < HP / 8; ++c8) {
+          const int col = h * HP + 8 * c8;  // column within the chunk
+          uint32_t hw[4], lw[4];
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const float2 xv = make_float2(x[8 * c8 + 2 * e], x[8 * c8 + 2 * e + 1]);
+            const __nv_bfloat162 hv = __floats2bfloat162_rn(xv.x, xv.y);
+            const float2 hf = __bfloat1622float2(hv);
+            const float2 rem = __fadd2_rn(xv, make_float2(-hf.x, -hf.y));
+            hw[e] = *reinterpret_cast<const uint32_t*>(&hv);
+            lw[e] = pack_bf16x2(rem.x, rem.y);
+          }
+          const int off = sw128(r, col / 8);
+          *reinterpret_cast<uint4*>(ab + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+          *reinterpret_cast<uint4*>(ab + L.lo_off + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+        }
+        fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0) {
+          mbar_arrive(&B.afull[i]);
+          mbar_arrive(&B.xempty[j]);
+        }
+      }
+      if (stop) break;
+      // both halves of the row: fold and form the row terms
+      float v0 = s0.x + s0.y, v1 = s1.x + s1.y, v2 = s2.x + s2.y, v3 = s3.x + s3.y, v4 = s4.x + s4.y;
+      v0 += __shfl_xor_sync(0xffffffffu, v0, 16);
+      v1 += __shfl_xor_sync(0xffffffffu, v1, 16);
+      v2 += __shfl_xor_sync(0xffffffffu, v2, 16);
+      v3 += __shfl_xor_sync(0xffffffffu, v3, 16);
+      v4 += __shfl_xor_sync(0xffffffffu, v4, 16);
+      float inv = 1.f, xn2 = v0, aes = v1;
+      if (cosine) {
+        if (valid && !(v0 > 0.f)) {
+          if (h == 0) set_status(a.status, SIL_EZERONORM);
+          valid = false;
+          in_blk = false;
+        }
+        inv = v0 > 0.f ? rsqrtf(v0) : 0.f;
+        const float xx = v0 * inv * inv;  // ||x_hat||^2 (= 1 up to rounding)
+        xn2 = fmaxf(0.f, xx - 2.f * inv * v1 + v3);
+        aes = fmaxf(0.f, xx - 2.f * inv * v2 + v4);
+      }
+      const int s = t & 1;
+      if (!tc_wait(&B.sempty[s], ((t >> 1) & 1) ^ 1, abort_flag, a.status)) break;
+      float* side = reinterpret_cast<float*>(base + L.side + s * L.side_stride);
+      if (h == 0) {
+        float aown = 0.f;
+        int code = valid ? kOwnElsewhere : kRowInvalid;
+        if (in_blk) {
+          const float4 co = clsm[olc];
+          aown = fmaf(co.y, aes, co.z);
+          code = co.w < 1.5f ? -2 - olc : olc;
+        }
+        side[r] = xn2;
+        side[kTM + r] = aown;
+        side[2 * kTM + r] = inv;
+        reinterpret_cast<int*>(side)[3 * kTM + r] = code;
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&B.sfull[s]);
+    }
+  } else {
+    // ---------------------------------------------- epilogue warps 10..13
+    const int q = warp & 3;
+    const int r = q * 32 + lane;
+    float tsum = 0.f;
+    for (int t = 0; t < my_tiles; ++t) {
+      const int bsel = t & 1;
+      if (!tc_wait(&B.accfull[bsel], (t >> 1) & 1, abort_flag, a.status)) break;
+      if (!tc_wait(&B.sfull[bsel], (t >> 1) & 1, abort_flag, a.status)) break;
+      tc_fence_after();
+      const float* side = reinterpret_cast<const float*>(base + L.side + bsel * L.side_stride);
+      const int code = reinterpret_cast<const int*>(side)[3 * kTM + r];
+      const bool row_ok = code != kRowInvalid;
+      const int own = code >= 0 ? code : (row_ok && code <= -2 ? -2 - code : -1);
+      const float sc = -2.f * side[2 * kTM + r];
+      const float xn2 = side[r], aown = side[kTM + r];
+      float best = INFINITY;
+      int kb = -1;
+      const uint32_t tbase = tmem + uint32_t(bsel * a.acc_cols) + (uint32_t(q * 32) << 16);
+      const float2 sc2 = make_float2(sc, sc);
+      for (int c0 = 0; c0 < a.kp; c0 += 64) {
+        uint32_t rv[4][16];
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj)
+          if (c0 + 16 * jj < a.kp) tmem_ld16_async(tbase + uint32_t(c0 + 16 * jj), rv[jj]);
+        tmem_wait_ld();
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj) {
+          if (c0 + 16 * jj >= a.kp) break;
+          reg_fence16(rv[jj]);
+          const float4* cb4 = reinterpret_cast<const float4*>(cbs + c0 + 16 * jj);
+#pragma unroll
+          for (int q4 = 0; q4 < 4; ++q4) {
+            const float4 cq = cb4[q4];
+            const float2 va = __ffma2_rn(sc2, make_float2(__uint_as_float(rv[jj][4 * q4]), __uint_as_float(rv[jj][4 * q4 + 1])),
+                                         make_float2(cq.x, cq.y));
+            const float2 vb = __ffma2_rn(sc2, make_float2(__uint_as_float(rv[jj][4 * q4 + 2]), __uint_as_float(rv[jj][4 * q4 + 3])),
+                                         make_float2(cq.z, cq.w));
+            const float vals[4] = {va.x, va.y, vb.x, vb.y};
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              const int kk = c0 + 16 * jj + 4 * q4 + e;
+              if (SAVE) {
+                if (kk != own && vals[e] < best) {
+                  best = vals[e];
+                  kb = kk;
+                }
+              } else if (kk != own) {
+                best = fminf(best, vals[e]);
+              }
+            }
+          }
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) {
+        mbar_arrive(&B.accempty[bsel]);
+        mbar_arrive(&B.sempty[bsel]);
+      }
+      const int64_t row = (blockIdx.x + int64_t(t) * gridDim.x) * kTM + r;
+      if (row < a.n) {
+        if (fused) {
+          float av = 0.f, bv = INFINITY, sv = 0.f;
+          if (row_ok) {
+            const bool has_b = best < INFINITY;
+            av = fmaxf(0.f, a.scale * aown);
+            bv = has_b ? fmaxf(0.f, a.scale * (xn2 + best)) : INFINITY;
+            if (code >= 0 && has_b) {
+              const float m = fmaxf(av, bv);
+              sv = m > 0.f ? (av <= bv ? 1.f - av / bv : bv / av - 1.f) : 0.f;
+            }
+            if (!has_b) kb = -1;
+          } else {
+            kb = -1;
+          }
+          if (a.s_out) a.s_out[row] = sv;
+          if (SAVE) {
+            a.sa[row] = av;
+            a.sb[row] = bv;
+            a.skstar[row] = kb;
+          }
+          tsum += sv;
+        } else {
+          const int64_t o = int64_t(blockIdx.y) * a.n + row;
+          a.pmin[o] = row_ok ? best : __int_as_float(0x7fc00000);
+          if (SAVE) a.parg[o] = (row_ok && kb >= 0) ? kb0 + kb : -1;
+          if (own >= 0) a.pown[row] = make_float2(aown, xn2);
+        }
+      }
+    }
+    if (fused) {
+      for (int o = 16; o > 0; o >>= 1) tsum += __shfl_xor_sync(0xffffffffu, tsum, o);
+      float* red = cbs + a.kp;
+      if (lane == 0) red[q] = tsum;
+      asm volatile("bar.sync 1, 128;" ::: "memory");
+      if (warp == kEpiWarp0 && lane == 0) a.partials[blockIdx.x] = double(red[0]) + red[1] + red[2] + red[3];
+    }
+  }
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * a.acc_cols)
+                 : "memory");
+  }
+}
+
 // s_i from the per-block results when the clusters span several blocks: the
 // minimum over the blocks (lowest cluster index on ties: blocks are visited
 // in order and only a strictly smaller value replaces the best), then Eq. 2
@@ -795,6 +1187,11 @@ int pow2_at_least(int v) {
 
 int mode_of(int32_t dtype) { return dtype == SIL_F32 ? kModeF32 : dtype == SIL_BF16 ? kModeBF16 : kModeFP8; }
 
+// Padded row width of the tensor path: 64 or 128 columns in one piece, FP32
+// rows of up to 256 columns in 64-column chunks (k_score_tc_wide).
+int tc_dp(int32_t d) { return d > 128 ? 256 : int(round_up(d, 64)); }
+int tc_max_d(int32_t dtype) { return dtype == SIL_F32 ? 256 : 128; }
+
 // Launch plan: cluster-block width kp, ring depths and whether the centroids
 // are staged for the own-cluster term.  Candidates are ranked by a small cost
 // model -- work per point over the G blocks times penalties for shallow rings
@@ -818,7 +1215,7 @@ template <class F>
 void tc_plan_enumerate(int32_t dtype, int32_t k, int32_t d, F&& visit) {
   const int mode = mode_of(dtype);
   const bool staged = mode != kModeBF16;
-  const int dp = int(round_up(d, 64));
+  const int dp = tc_dp(d);
   const int dz = int(round_up(d, 4));
   const int kmax = int(std::min<int64_t>(round_up(std::max(k, 16), 16), kMaxBlockN));
   for (int kp = kmax; kp >= 16; kp -= 16) {
@@ -832,7 +1229,7 @@ void tc_plan_enumerate(int32_t dtype, int32_t k, int32_t d, F&& visit) {
           // per block and tile: MMA + epilogue ~ kp columns (the MMA is bound by
           // its A-operand reads below ~64), plus a fixed share for conversion,
           // row terms and the per-block results
-          double cost = double(nblk) * (std::max(kp, 64) + 64);
+          double cost = double(nblk) * (std::max(kp, 64) + dp);
           if (nab < 2) cost *= 1.4;
           if (staged && nxs < 2) cost *= 1.2;
           if (staged && nxs == 2) cost *= 1.02;
@@ -847,7 +1244,7 @@ void tc_plan_enumerate(int32_t dtype, int32_t k, int32_t d, F&& visit) {
 
 bool tc_plan(int32_t dtype, int32_t k, int32_t d, TcPlan* out) {
   const int mode = mode_of(dtype);
-  const int dp = int(round_up(d, 64));
+  const int dp = tc_dp(d);
   const int dz = int(round_up(d, 4));
   {
     std::lock_guard<std::mutex> lock(g_plan_mu);
@@ -879,7 +1276,7 @@ bool tc_eligible(int32_t dtype, int64_t n, int32_t d, int64_t ldx, int32_t k, co
                  const int32_t* labels) {
   const char* e = getenv("SIL_TC_DISABLE");
   if (e && e[0] == '1') return false;
-  if (n <= 0 || n >= (int64_t(1) << 31) || d > 128) return false;
+  if (n <= 0 || n >= (int64_t(1) << 31) || d > tc_max_d(dtype)) return false;
   if (reinterpret_cast<uintptr_t>(X) % 16 || reinterpret_cast<uintptr_t>(labels) % 16) return false;
   const int esz = dtype == SIL_F32 ? 4 : dtype == SIL_BF16 ? 2 : 1;
   if ((ldx * esz) % 16) return false;
@@ -896,7 +1293,7 @@ bool tc_eligible(int32_t dtype, int64_t n, int32_t d, int64_t ldx, int32_t k, co
 }
 
 bool tc_plan_query(int32_t dtype, int32_t d, int32_t k, int32_t* block_k, int32_t* n_blocks) {
-  if (d > 128 || d <= 0 || k <= 0) return false;
+  if (d > tc_max_d(dtype) || d <= 0 || k <= 0) return false;
   TcPlan p;
   if (!tc_plan(dtype, k, d, &p)) return false;
   *block_k = p.kp;
@@ -905,7 +1302,7 @@ bool tc_plan_query(int32_t dtype, int32_t d, int32_t k, int32_t* block_k, int32_
 }
 
 int tc_plan_candidates(int32_t dtype, int32_t d, int32_t k, int32_t* plans, int32_t max_plans) {
-  if (d > 128 || d <= 0 || k <= 0) return 0;
+  if (d > tc_max_d(dtype) || d <= 0 || k <= 0) return 0;
   std::vector<std::pair<double, TcPlan>> all;
   tc_plan_enumerate(dtype, k, d, [&](const TcPlan& p, double cost) { all.emplace_back(cost, p); });
   std::stable_sort(all.begin(), all.end(), [](const auto& a, const auto& b) { return a.first < b.first; });
@@ -929,11 +1326,11 @@ int tc_plan_set(int32_t dtype, int32_t d, int32_t k, int32_t kp, int32_t nab, in
       break;
     }
   if (kp == 0) return SIL_OK;  // cleared: back to the cost model
-  if (d > 128 || kp < 16 || kp > kMaxBlockN || kp % 16 || nab < 1 || nab > 4 || nxs < 1 || nxs > 3)
+  if (d > tc_max_d(dtype) || kp < 16 || kp > kMaxBlockN || kp % 16 || nab < 1 || nab > 4 || nxs < 1 || nxs > 3)
     return SIL_EINVAL;
   const int mode = mode_of(dtype);
   const int zst = stage_z ? int(round_up(d, 4)) + 4 : 0;
-  if (tc_smem(mode, int(round_up(d, 64)), kp, mode == kModeBF16 ? 1 : nxs, nab, zst).total > kSmemMax)
+  if (tc_smem(mode, tc_dp(d), kp, mode == kModeBF16 ? 1 : nxs, nab, zst).total > kSmemMax)
     return SIL_EUNSUPPORTED;
   g_plan_over.push_back(PlanOverride{dtype, d, k, kp, nab, mode == kModeBF16 ? 1 : nxs, stage_z ? 1 : 0});
   return SIL_OK;
@@ -941,12 +1338,12 @@ int tc_plan_set(int32_t dtype, int32_t d, int32_t k, int32_t kp, int32_t nab, in
 
 size_t tc_pack_bytes(int32_t k, int32_t d) {
   // nblk * kp < k + kp <= k + 256
-  const size_t kpad = size_t(round_up(std::max(k, 16), 16)) + kMaxBlockN, dp = size_t(round_up(d, 64));
+  const size_t kpad = size_t(round_up(std::max(k, 16), 16)) + kMaxBlockN, dp = size_t(tc_dp(d));
   return 2 * kpad * dp * 2 + kpad * 4 + 256;
 }
 
 size_t tc_partial_bytes(int64_t n, int32_t d, int32_t k, int32_t dtype) {
-  if (n <= 0 || d > 128 || dtype < SIL_F32 || dtype > SIL_FP8_E4M3) return 0;
+  if (n <= 0 || dtype < SIL_F32 || dtype > SIL_FP8_E4M3 || d > tc_max_d(dtype)) return 0;
   TcPlan p;
   if (!tc_plan(dtype, k, d, &p) || p.nblk == 1) return 0;
   const size_t N = size_t(n), G = size_t(p.nblk);
@@ -957,9 +1354,26 @@ cudaError_t launch_score_tc(const ScoreLaunch& s, const double* g, void* pack, v
                             size_t partial_bytes, uint32_t* status) {
   TcPlan plan;
   if (!tc_plan(s.dtype, s.k, s.d, &plan)) return cudaErrorInvalidValue;
-  if (plan.nblk > 1 && partial_bytes < tc_partial_bytes(s.n, s.d, s.k, s.dtype)) return cudaErrorInvalidValue;
+  auto need = [&](int nblk) {
+    const size_t N = size_t(s.n), G = size_t(nblk);
+    return nblk > 1 ? align256(G * N * 4) * 2 + align256(N * 8) : size_t(0);
+  };
+  if (need(plan.nblk) > partial_bytes) {
+    // the workspace was sized for another plan (e.g. a larger k of a batch):
+    // the cheapest plan whose per-block results fit
+    double best = 0.0;
+    bool found = false;
+    tc_plan_enumerate(s.dtype, s.k, s.d, [&](const TcPlan& p, double cost) {
+      if (need(p.nblk) <= partial_bytes && (!found || cost < best)) {
+        found = true;
+        best = cost;
+        plan = p;
+      }
+    });
+    if (!found) return cudaErrorInvalidValue;
+  }
   const int mode = mode_of(s.dtype);
-  const int dp = int(round_up(s.d, 64));
+  const int dp = tc_dp(s.d);
   const int kp = plan.kp;
   const int kpad = plan.nblk * kp;
   const int dz = int(round_up(s.d, 4));
@@ -1031,7 +1445,8 @@ cudaError_t launch_score_tc(const ScoreLaunch& s, const double* g, void* pack, v
   };
   cudaError_t e;
   if (mode == kModeF32) {
-    if (dp == 64) e = save ? launch(k_score_tc<kModeF32, 64, true>) : launch(k_score_tc<kModeF32, 64, false>);
+    if (dp == 256) e = save ? launch(k_score_tc_wide<true>) : launch(k_score_tc_wide<false>);
+    else if (dp == 64) e = save ? launch(k_score_tc<kModeF32, 64, true>) : launch(k_score_tc<kModeF32, 64, false>);
     else e = save ? launch(k_score_tc<kModeF32, 128, true>) : launch(k_score_tc<kModeF32, 128, false>);
   } else if (mode == kModeBF16) {
     if (dp == 64) e = save ? launch(k_score_tc<kModeBF16, 64, true>) : launch(k_score_tc<kModeBF16, 64, false>);

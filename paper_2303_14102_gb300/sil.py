@@ -290,6 +290,38 @@ def score_batched(X: torch.Tensor, labels: torch.Tensor, ks, metric: str = "sqeu
     return S
 
 
+class BatchedGraph:
+    """sil_score_batched captured once into a CUDA graph and replayed.
+
+    All B labelings' launches (pass 1, finalisation, pass 2 and the mean for
+    each) are recorded on a side stream at construction; run() replays them
+    with one graph launch and returns the FP64 S of every labeling.  The
+    graph keeps the device addresses of X, labels, the workspace and its
+    output, so it is only valid while those tensors live and keep their
+    contents' layout; build a new one for other inputs.
+    """
+
+    def __init__(self, X: torch.Tensor, labels: torch.Tensor, ks, metric: str = "sqeuclidean",
+                 col_scale: torch.Tensor | None = None, status: torch.Tensor | None = None):
+        self.X, self.labels, self.col_scale, self.status = X, labels, col_scale, status
+        self.ks, self.metric = [int(k) for k in ks], metric
+        score_batched(X, labels, self.ks, metric, col_scale=col_scale, status=status)  # sizes the workspace
+        # the graph keeps this workspace's address: hold the buffer even if a
+        # later, larger call replaces it in the cache
+        self._ws, _ = _ws_for(X, max(self.ks), metric, batch=len(self.ks))
+        torch.cuda.synchronize(X.device)
+        self.graph = torch.cuda.CUDAGraph()
+        side = torch.cuda.Stream(X.device)
+        with torch.cuda.stream(side):
+            with torch.cuda.graph(self.graph, stream=side):
+                self.S = score_batched(X, labels, self.ks, metric, col_scale=col_scale, status=status)
+        torch.cuda.synchronize(X.device)
+
+    def run(self) -> torch.Tensor:
+        self.graph.replay()
+        return self.S
+
+
 def tensor_plan(dtype: torch.dtype, D: int, K: int):
     """(clusters per block, number of blocks) of the tensor-core pass 2, or None."""
     lib = load()

@@ -116,7 +116,11 @@ def test_tensor_plan_is_host_arithmetic():
         bk, nb = sil.tensor_plan(dt, d, k)
         assert bk % 16 == 0 and 16 <= bk <= 256
         assert (nb - 1) * bk < k <= nb * bk
-    assert sil.tensor_plan(torch.float32, 256, 100) is None  # d > 128: SIMT only
+    # FP32 rows up to 256 columns run in 64-column chunks; wider rows and
+    # wide BF16 rows take the SIMT kernels
+    assert sil.tensor_plan(torch.float32, 256, 100) is not None
+    assert sil.tensor_plan(torch.float32, 257, 100) is None
+    assert sil.tensor_plan(torch.bfloat16, 256, 100) is None
 
 
 def test_tensor_plan_rejects_bad_arguments(lib):
@@ -145,4 +149,4 @@ def test_tensor_plan_candidates_and_override():
 def test_tensor_plan_set_rejects_bad_plans(lib):
     assert lib.sil_tensor_plan_set(0, 64, 100, 40, 2, 2, 0) == sil.SIL_EINVAL      # not a multiple of 16
     assert lib.sil_tensor_plan_set(0, 64, 100, 256, 4, 3, 1) == sil.SIL_EUNSUPPORTED  # too much shared memory
-    assert lib.sil_tensor_plan_set(0, 256, 100, 64, 2, 2, 0) == sil.SIL_EINVAL     # d > 128
+    assert lib.sil_tensor_plan_set(0, 300, 100, 64, 2, 2, 0) == sil.SIL_EINVAL     # d > 256

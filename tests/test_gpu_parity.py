@@ -236,3 +236,16 @@ def test_pass1_load_paths_agree(metric, dtype, N, D, K, monkeypatch):
     # s2 sums n_k * D squared FP32 terms (partials over runs of <= 256 rows,
     # up to 16 columns per lane): a few 1e-6 relative at D = 600
     np.testing.assert_allclose(fast[2].cpu().numpy(), r2, rtol=1e-5, atol=1e-9 * np.abs(r2).max())
+
+
+def test_batched_graph_replay_matches_direct_call():
+    rng = np.random.default_rng(77)
+    X = (rng.normal(size=(5000, 32)) + rng.integers(0, 4, size=(5000, 1)) * 3).astype(np.float32)
+    ks = [2, 9, 300, 40]
+    labs = np.stack([rng.integers(0, k, size=5000).astype(np.int32) for k in ks])
+    Xt, lt = torch.as_tensor(X).cuda(), torch.as_tensor(labs).cuda()
+    direct = sil.score_batched(Xt, lt, ks).cpu().numpy()
+    g = sil.BatchedGraph(Xt, lt, ks)
+    for _ in range(2):
+        S = g.run().cpu().numpy()
+        np.testing.assert_allclose(S, direct, rtol=0, atol=1e-9)

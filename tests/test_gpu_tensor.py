@@ -82,6 +82,34 @@ def test_auto_picks_tensor_when_eligible():
 
 
 @pytest.mark.parametrize("metric", METRICS)
+@pytest.mark.parametrize("N,D,K", [(3000, 256, 7), (2500, 256, 100), (1500, 160, 300), (2000, 256, 1000),
+                                   (129, 200, 3)])
+def test_wide_fp32_rows_in_chunks_against_bruteforce(metric, N, D, K):
+    # FP32 rows of 129..256 columns: the GEMM accumulates four 64-column chunks
+    X, lab = case(1300 + N + D + K, N, D, K, metric)
+    Xt, lt = to_dev(X, lab)
+    r, st = run(Xt, lt, K, metric, "tensor")
+    ref = oracle.bruteforce(dequant(Xt), lab, K, metric)
+    assert st == 0
+    assert_scores(r.s, r.S, ref, what=f"wide tensor {metric} N={N} D={D} K={K}")
+    a, b, ks = sil.unpack_saved(r.saved, N)
+    ok = ref["s"] != 0
+    np.testing.assert_allclose(a.cpu().double().numpy()[ok], ref["a"][ok], rtol=1e-4, atol=1e-4)
+    np.testing.assert_allclose(b.cpu().double().numpy()[ok], ref["b"][ok], rtol=1e-4, atol=1e-4)
+    assert np.mean(ks.cpu().numpy()[ok] == ref["kstar"][ok]) > 0.995
+
+
+@pytest.mark.parametrize("metric", METRICS)
+def test_wide_fp32_tensor_and_simt_agree_on_grad_recipe(metric):
+    w = synth.workload_grad(device="cuda", N=100_000)
+    ra, sa_ = run(w.X, w.labels, w.K, metric, "tensor", save=False)
+    rb, sb_ = run(w.X, w.labels, w.K, metric, "simt", save=False)
+    assert sa_ == 0 and sb_ == 0
+    assert float((ra.s - rb.s).abs().max()) <= TOL_SI
+    assert abs(float(ra.S) - float(rb.S)) <= TOL_S
+
+
+@pytest.mark.parametrize("metric", METRICS)
 @pytest.mark.parametrize("N,K", [(1000, 5), (4097, 100), (3000, 300), (2000, 1000)])
 def test_fp8_tensor_path_against_bruteforce(metric, N, K):
     X, lab = case(900 + N + K, N, 128, K, metric)
