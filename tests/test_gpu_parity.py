@@ -248,4 +248,7 @@ def test_batched_graph_replay_matches_direct_call():
     g = sil.BatchedGraph(Xt, lt, ks)
     for _ in range(2):
         S = g.run().cpu().numpy()
-        np.testing.assert_allclose(S, direct, rtol=0, atol=1e-9)
+        # pass 1 sums rows in an order that depends on scheduling: equal to FP32 rounding
+        np.testing.assert_allclose(S, direct, rtol=0, atol=TOL_S)
+    ref = [oracle.linear(X.astype(np.float64), labs[b], k)["S"] for b, k in enumerate(ks)]
+    np.testing.assert_allclose(S, ref, rtol=0, atol=TOL_S)
