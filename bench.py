@@ -281,6 +281,44 @@ def variant_lines(dev, steps, budget_s, pk_sustained):
     return out
 
 
+def run_case(args):
+    """One small case of a secondary workload, untimed, for profiler captures:
+    the same recipe and seed as the full workload at args.n points."""
+    import torch
+    from paper_2303_14102_gb300 import sil, synth
+    from paper_2303_14102_gb300.autograd import silhouette_loss
+    dev = torch.device("cuda", 0)
+    if args.case.startswith("precision"):
+        w = synth.workload_precision(device=dev, N=args.n)
+        cs = None
+        if args.case == "precision_bf16":
+            X = synth.to_bf16(w.X)
+        else:
+            X, cs = synth.to_fp8_e4m3(w.X)
+        st = sil.new_status(dev)
+        agg = sil.aggregate(X, w.labels, w.K, col_scale=cs, status=st)
+        for _ in range(3):
+            r = sil.score(X, w.labels, w.K, agg, col_scale=cs, status=st)
+        torch.cuda.synchronize()
+        sil.check_status(st, args.case)
+        print(json.dumps({"case": args.case, "N": args.n, "S": float(r.S)}))
+    elif args.case == "grad":
+        w = synth.workload_grad(device=dev, N=args.n)
+        for _ in range(2):
+            Xg = w.X.detach().requires_grad_(True)
+            S = silhouette_loss(Xg, w.labels, w.K, "sqeuclidean")
+            S.backward()
+        torch.cuda.synchronize()
+        print(json.dumps({"case": args.case, "N": args.n, "S": float(S.detach())}))
+    else:
+        X, labs, ks = synth.workload_batched(device=dev, B=args.batch)
+        for _ in range(2):
+            S = sil.score_batched(X, labs, ks)
+        torch.cuda.synchronize()
+        print(json.dumps({"case": args.case, "B": args.batch, "ks": ks, "S": S.tolist()}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -291,9 +329,14 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--n", type=int, default=10_000_000,
                     help="points of the at_scale workload (smaller only for profiling captures)")
+    ap.add_argument("--case", default=None, choices=["precision_bf16", "precision_fp8", "grad", "batched"],
+                    help="run one untimed small case of another workload (for profiler captures) and exit")
+    ap.add_argument("--batch", type=int, default=2, help="labelings of the batched case")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.case is not None:
+        return run_case(args)
 
     import numpy as np
     import torch

@@ -67,6 +67,7 @@ constexpr int kEpiWarp0 = 2 + kConvWarps;  // warps 10..13
 constexpr int kAtomBytes = kTM * 128;      // one 128-row x 128-byte swizzle column
 constexpr int kMaxBlockN = 256;            // clusters per block (MMA N)
 constexpr int kSmemMax = 227 * 1024;
+constexpr int kSideSlots = 4;  // row-term ring of the modes whose converters write it
 
 enum TcMode { kModeF32 = 0, kModeBF16 = 1, kModeFP8 = 2 };
 
@@ -220,7 +221,9 @@ __host__ __device__ inline TcSmem tc_smem(int mode, int dp, int kp, int nxs, int
   o += staged ? nxs * s.xs_stride : 0;
   s.side = o;
   s.side_stride = kTM * 16 + 512;  // xn2, aown, inv, code + labels (BF16 mode)
-  o += (wide ? 2 : nab) * s.side_stride;
+  // BF16: one slot per A buffer (TMA writes the labels beside the tile);
+  // otherwise a ring of its own, so that an A buffer is free once its MMAs are
+  o += (staged ? kSideSlots : nab) * s.side_stride;
   s.cb = o; o += kp * 4 + 16;  // + 4 floats of block-reduction scratch
   o = (o + 15) & ~15;
   s.gsm = o; o += dp * 4;
@@ -229,7 +232,7 @@ __host__ __device__ inline TcSmem tc_smem(int mode, int dp, int kp, int nxs, int
   s.zst = zst;
   s.zsm = o; o += kp * zst * 4;
   o = (o + 15) & ~15;
-  s.bars = o; o += 8 * (2 * nxs + 4 * nab + 4 + 1 + (wide ? 4 : 0)) + 16;  // + TMEM base, abort flag
+  s.bars = o; o += 8 * (2 * nxs + 4 * nab + 4 + 1 + 2 * kSideSlots) + 16;  // + TMEM base, abort flag
   s.total = o + 1024;  // slack for aligning the dynamic base to 1024
   return s;
 }
@@ -240,7 +243,7 @@ struct TcBars {
   int* abort_flag;
 };
 
-__device__ inline TcBars tc_bars(unsigned char* base, const TcSmem& L, int nxs, int nab, bool wide = false) {
+__device__ inline TcBars tc_bars(unsigned char* base, const TcSmem& L, int nxs, int nab) {
   TcBars b;
   uint64_t* p = reinterpret_cast<uint64_t*>(base + L.bars);
   b.xfull = p; p += nxs;
@@ -251,8 +254,8 @@ __device__ inline TcBars tc_bars(unsigned char* base, const TcSmem& L, int nxs, 
   b.accfull = p; p += 2;
   b.accempty = p; p += 2;
   b.zfull = p; p += 1;
-  b.sfull = p; p += wide ? 2 : 0;
-  b.sempty = p; p += wide ? 2 : 0;
+  b.sfull = p; p += kSideSlots;
+  b.sempty = p; p += kSideSlots;
   b.tmem_base = reinterpret_cast<uint32_t*>(p);
   b.abort_flag = reinterpret_cast<int*>(p) + 1;
   return b;
@@ -302,12 +305,17 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_score_tc(TcK a, const __grid_
     }
     for (int i = 0; i < a.nab; ++i) {
       mbar_init(&B.afull[i], STAGED ? kConvWarps : 1);  // converters, or the TMA transaction
-      mbar_init(&B.aempty[i], 1 + 4);                   // MMA commit + 4 epilogue warps
-      mbar_init(&B.pfull[i], kConvWarps);               // BF16 mode: the row terms are written
+      // MMA commit (+ the 4 epilogue warps in BF16 mode, whose row terms share the slot)
+      mbar_init(&B.aempty[i], STAGED ? 1 : 1 + 4);
+      mbar_init(&B.pfull[i], kConvWarps);  // BF16 mode: the row terms are written
     }
     for (int i = 0; i < 2; ++i) {
       mbar_init(&B.accfull[i], 1);
       mbar_init(&B.accempty[i], 4);
+    }
+    for (int i = 0; i < kSideSlots; ++i) {
+      mbar_init(&B.sfull[i], kConvWarps);
+      mbar_init(&B.sempty[i], 4);
     }
     mbar_init(B.zfull, 1);
     *B.abort_flag = 0;
@@ -430,7 +438,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_score_tc(TcK a, const __grid_
       const int i = t % a.nab;
       const int64_t row = (blockIdx.x + int64_t(t) * gridDim.x) * kTM + r;
       unsigned char* ab = base + L.abuf + i * L.abuf_stride;
-      float* side = reinterpret_cast<float*>(base + L.side + i * L.side_stride);
+      const int sl = STAGED ? t % kSideSlots : i;  // row-term slot
+      float* side = reinterpret_cast<float*>(base + L.side + sl * L.side_stride);
       float x[HP];
       int own;
       if (STAGED) {
@@ -489,6 +498,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_score_tc(TcK a, const __grid_
           }
         }
         own = reinterpret_cast<const int32_t*>(xs + raw_tile_bytes(MODE, DP))[r];
+        // the stage is in registers now: let the producer refill it
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&B.xempty[j]);
       } else {
         if (!tc_wait(&B.afull[i], (t / a.nab) & 1, abort_flag, a.status)) break;
 #pragma unroll
@@ -579,6 +591,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_score_tc(TcK a, const __grid_
         }
         fence_proxy_async_smem();
       }
+      if (STAGED) {
+        // the A buffer is complete: the MMA may start while the row terms wait
+        // for their slot
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&B.afull[i]);
+        if (!tc_wait(&B.sempty[sl], ((t / kSideSlots) & 1) ^ 1, abort_flag, a.status)) break;
+      }
       if (h == 0) {
         float aown = 0.f;
         int code = valid ? kOwnElsewhere : kRowInvalid;
@@ -593,14 +612,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_score_tc(TcK a, const __grid_
         reinterpret_cast<int*>(side)[3 * kTM + r] = code;
       }
       __syncwarp();
-      if (lane == 0) {
-        if (STAGED) {
-          mbar_arrive(&B.afull[i]);
-          mbar_arrive(&B.xempty[t % a.nxs]);
-        } else {
-          mbar_arrive(&B.pfull[i]);
-        }
-      }
+      if (lane == 0) mbar_arrive(STAGED ? &B.sfull[sl] : &B.pfull[i]);
     }
   } else {
     // ---------------------------------------------- epilogue warps 10..13
@@ -608,11 +620,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_score_tc(TcK a, const __grid_
     const int r = q * 32 + lane;  // tile row = TMEM lane
     float tsum = 0.f;
     for (int t = 0; t < my_tiles; ++t) {
-      const int i = t % a.nab, bsel = t & 1;
+      const int i = t % a.nab, bsel = t & 1, sl = STAGED ? t % kSideSlots : i;
       if (!tc_wait(&B.accfull[bsel], (t >> 1) & 1, abort_flag, a.status)) break;
-      if (!tc_wait(STAGED ? &B.afull[i] : &B.pfull[i], (t / a.nab) & 1, abort_flag, a.status)) break;
+      if (STAGED) {
+        if (!tc_wait(&B.sfull[sl], (t / kSideSlots) & 1, abort_flag, a.status)) break;
+      } else if (!tc_wait(&B.pfull[i], (t / a.nab) & 1, abort_flag, a.status)) {
+        break;
+      }
       tc_fence_after();
-      const float* side = reinterpret_cast<const float*>(base + L.side + i * L.side_stride);
+      const float* side = reinterpret_cast<const float*>(base + L.side + sl * L.side_stride);
       const int code = reinterpret_cast<const int*>(side)[3 * kTM + r];
       const bool row_ok = code != kRowInvalid;
       const int own = code >= 0 ? code : (row_ok && code <= -2 ? -2 - code : -1);  // in-block index
@@ -690,7 +706,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_score_tc(TcK a, const __grid_
         }
       }
       __syncwarp();
-      if (lane == 0) mbar_arrive(&B.aempty[i]);
+      if (lane == 0) mbar_arrive(STAGED ? &B.sempty[sl] : &B.aempty[i]);
     }
     if (fused) {
       // block partial over the 128 epilogue threads
@@ -725,7 +741,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_score_tc_wide(TcK a, const __
   unsigned char* base = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
   constexpr int DP = 256, NCH = 4, natom = 4;
   const TcSmem L = tc_smem(kModeF32, DP, a.kp, a.nxs, a.nab, a.zst);
-  const TcBars B = tc_bars(base, L, a.nxs, a.nab, true);
+  const TcBars B = tc_bars(base, L, a.nxs, a.nab);
   volatile int* abort_flag = B.abort_flag;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t ntiles = cdiv(a.n, kTM);
@@ -747,6 +763,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_score_tc_wide(TcK a, const __
     for (int i = 0; i < 2; ++i) {
       mbar_init(&B.accfull[i], 1);
       mbar_init(&B.accempty[i], 4);
+    }
+    for (int i = 0; i < kSideSlots; ++i) {
       mbar_init(&B.sfull[i], kConvWarps);
       mbar_init(&B.sempty[i], 4);
     }
@@ -859,6 +877,23 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_score_tc_wide(TcK a, const __
       // cosine: x.x, x.g, x.(g + mu'_c), g.g, ||g + mu'_c||^2
       float2 s0 = make_float2(0.f, 0.f), s1 = s0, s2 = s0, s3 = s0, s4 = s0;
       bool stop = false;
+      // the own centroid's 32 columns of the chunk being worked on, loaded one
+      // chunk ahead so that the gathers overlap the waits and the split
+      float4 zr[HP / 4];
+      auto load_z = [&](int c) {
+#pragma unroll
+        for (int c4 = 0; c4 < HP / 4; ++c4) {
+          const int col = c * 64 + h * HP + 4 * c4;
+          float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (col < a.dz) {
+            if (a.zst)
+              z = *reinterpret_cast<const float4*>(zsm + olc * a.zst + col);
+            else
+              z = __ldg(reinterpret_cast<const float4*>(a.zf + int64_t(kb0 + olc) * a.dz + col));
+          }
+          zr[c4] = z;
+        }
+      };
       for (int c = 0; c < NCH; ++c, ++u) {
         const int i = u % a.nab, j = u % a.nxs;
         if (!tc_wait(&B.xfull[j], (u / a.nxs) & 1, abort_flag, a.status) ||
@@ -877,6 +912,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_score_tc_wide(TcK a, const __
           const int ol = own - kb0;
           in_blk = valid && ol >= 0 && ol < kblk;
           olc = in_blk ? ol : 0;
+          load_z(0);
         }
         float x[HP];
 #pragma unroll
@@ -887,17 +923,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_score_tc_wide(TcK a, const __
           x[4 * c4 + 2] = v.z;
           x[4 * c4 + 3] = v.w;
         }
+        // the stage is in registers now: let the producer refill it
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&B.xempty[j]);
 #pragma unroll
         for (int c4 = 0; c4 < HP / 4; ++c4) {
           const int col = c * 64 + h * HP + 4 * c4;  // global column
           const float4 g = *reinterpret_cast<const float4*>(gsm + col);
-          float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-          if (col < a.dz) {
-            if (a.zst)
-              z = *reinterpret_cast<const float4*>(zsm + olc * a.zst + col);
-            else
-              z = __ldg(reinterpret_cast<const float4*>(a.zf + int64_t(kb0 + olc) * a.dz + col));
-          }
+          const float4 z = zr[c4];
           const float2 xa = make_float2(x[4 * c4], x[4 * c4 + 1]), xb = make_float2(x[4 * c4 + 2], x[4 * c4 + 3]);
           const float2 ga = make_float2(g.x, g.y), gb = make_float2(g.z, g.w);
           if (!cosine) {
@@ -941,12 +974,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_score_tc_wide(TcK a, const __
           *reinterpret_cast<uint4*>(ab + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
           *reinterpret_cast<uint4*>(ab + L.lo_off + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
         }
+        if (c + 1 < NCH) load_z(c + 1);
         fence_proxy_async_smem();
         __syncwarp();
-        if (lane == 0) {
-          mbar_arrive(&B.afull[i]);
-          mbar_arrive(&B.xempty[j]);
-        }
+        if (lane == 0) mbar_arrive(&B.afull[i]);
       }
       if (stop) break;
       // both halves of the row: fold and form the row terms
@@ -968,8 +999,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_score_tc_wide(TcK a, const __
         xn2 = fmaxf(0.f, xx - 2.f * inv * v1 + v3);
         aes = fmaxf(0.f, xx - 2.f * inv * v2 + v4);
       }
-      const int s = t & 1;
-      if (!tc_wait(&B.sempty[s], ((t >> 1) & 1) ^ 1, abort_flag, a.status)) break;
+      const int s = t % kSideSlots;
+      if (!tc_wait(&B.sempty[s], ((t / kSideSlots) & 1) ^ 1, abort_flag, a.status)) break;
       float* side = reinterpret_cast<float*>(base + L.side + s * L.side_stride);
       if (h == 0) {
         float aown = 0.f;
@@ -993,11 +1024,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_score_tc_wide(TcK a, const __
     const int r = q * 32 + lane;
     float tsum = 0.f;
     for (int t = 0; t < my_tiles; ++t) {
-      const int bsel = t & 1;
+      const int bsel = t & 1, sl = t % kSideSlots;
       if (!tc_wait(&B.accfull[bsel], (t >> 1) & 1, abort_flag, a.status)) break;
-      if (!tc_wait(&B.sfull[bsel], (t >> 1) & 1, abort_flag, a.status)) break;
+      if (!tc_wait(&B.sfull[sl], (t / kSideSlots) & 1, abort_flag, a.status)) break;
       tc_fence_after();
-      const float* side = reinterpret_cast<const float*>(base + L.side + bsel * L.side_stride);
+      const float* side = reinterpret_cast<const float*>(base + L.side + sl * L.side_stride);
       const int code = reinterpret_cast<const int*>(side)[3 * kTM + r];
       const bool row_ok = code != kRowInvalid;
       const int own = code >= 0 ? code : (row_ok && code <= -2 ? -2 - code : -1);
@@ -1045,7 +1076,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_score_tc_wide(TcK a, const __
       __syncwarp();
       if (lane == 0) {
         mbar_arrive(&B.accempty[bsel]);
-        mbar_arrive(&B.sempty[bsel]);
+        mbar_arrive(&B.sempty[sl]);
       }
       const int64_t row = (blockIdx.x + int64_t(t) * gridDim.x) * kTM + r;
       if (row < a.n) {
