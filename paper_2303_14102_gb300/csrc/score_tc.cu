@@ -445,7 +445,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_score_tc(TcK a, const __grid_
       if (STAGED) {
         const int j = t % a.nxs;
         if (!tc_wait(&B.xfull[j], (t / a.nxs) & 1, abort_flag, a.status)) break;
-        if (!tc_wait(&B.aempty[i], ((t / a.nab) & 1) ^ 1, abort_flag, a.status)) break;
+        // FP8 writes the A operand while it reads the stage; FP32 waits for its
+        // A buffer only after the row terms (the MMA of the previous tile in
+        // that buffer overlaps them)
+        if (MODE == kModeFP8 && !tc_wait(&B.aempty[i], ((t / a.nab) & 1) ^ 1, abort_flag, a.status)) break;
         const unsigned char* xs = base + L.xs + j * L.xs_stride;
         if (MODE == kModeF32) {
 #pragma unroll
@@ -571,6 +574,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_score_tc(TcK a, const __grid_
       xn2s += __shfl_xor_sync(0xffffffffu, xn2s, 16);
       aes += __shfl_xor_sync(0xffffffffu, aes, 16);
       if (MODE == kModeF32) {
+        if (!tc_wait(&B.aempty[i], ((t / a.nab) & 1) ^ 1, abort_flag, a.status)) break;
         // hi/lo BF16 split of this half row into the swizzled A buffer
 #pragma unroll
         for (int c8 = 0; c8 < HP / 8; ++c8) {
