@@ -85,6 +85,12 @@ __device__ __forceinline__ uint64_t umma_desc_sw128(uint32_t saddr) {
          (uint64_t(1) << 46) | (uint64_t(2) << 61);
 }
 
+// K-major, 64-byte swizzle (rows of 32 BF16): 8-row groups 512 bytes apart.
+__device__ __forceinline__ uint64_t umma_desc_sw64(uint32_t saddr) {
+  return uint64_t((saddr >> 4) & 0x3FFF) | (uint64_t(1) << 16) | (uint64_t(512 >> 4) << 32) |
+         (uint64_t(1) << 46) | (uint64_t(4) << 61);
+}
+
 __host__ __device__ constexpr uint32_t umma_idesc_bf16(int M, int N) {
   return (1u << 4)                     // D: FP32
          | (1u << 7)                   // A: BF16
@@ -140,6 +146,8 @@ __device__ __forceinline__ void reg_fence16(uint32_t (&r)[16]) {
 
 // Byte offset of 16-byte chunk q of row r inside a 128-byte-swizzled block.
 __device__ __forceinline__ int sw128(int r, int q) { return r * 128 + ((q ^ (r & 7)) << 4); }
+// ... and inside a 64-byte-swizzled block (rows of 64 bytes, 512-byte atoms).
+__device__ __forceinline__ int sw64(int r, int q) { return r * 64 + ((q ^ ((r >> 1) & 3)) << 4); }
 
 __device__ __forceinline__ uint32_t pack_bf16x2(float lo_elem, float hi_elem) {
   // element with the lower column index goes to the low half
@@ -202,19 +210,22 @@ __host__ __device__ constexpr int raw_tile_bytes(int mode, int dp) {
 // buffers and raw X stages hold one 64-column chunk of a tile, and the row
 // terms live in a ring of two tile slots of their own.
 __host__ __device__ inline TcSmem tc_smem(int mode, int dp, int kp, int nxs, int nab, int zst) {
-  const int natom = dp / 64;
+  // operand atoms: 64 BF16 columns (128-byte rows), or one atom of 32
+  // columns (64-byte rows) when dp = 32
+  const int natom = dp >= 64 ? dp / 64 : 1;
+  const int rowb = dp >= 64 ? 128 : dp * 2;
   const bool wide = dp > 128;
   const int natom_a = wide ? 1 : natom;  // atoms of one A buffer
   const bool staged = mode != kModeBF16;
   TcSmem s;
   int o = 0;
-  s.zh = o; o += natom * kp * 128;
+  s.zh = o; o += natom * kp * rowb;
   o = (o + 1023) & ~1023;
-  s.zl = o; o += natom * kp * 128;
+  s.zl = o; o += natom * kp * rowb;
   o = (o + 1023) & ~1023;
   s.abuf = o;
-  s.lo_off = natom_a * kAtomBytes;
-  s.abuf_stride = natom_a * kAtomBytes * (mode == kModeF32 ? 2 : 1);
+  s.lo_off = natom_a * kTM * rowb;
+  s.abuf_stride = natom_a * kTM * rowb * (mode == kModeF32 ? 2 : 1);
   o += nab * s.abuf_stride;
   s.xs = o;
   s.xs_stride = staged ? raw_tile_bytes(mode, wide ? 64 : dp) + 1024 : 0;  // + labels (512 B), keeps 1024 alignment
@@ -284,7 +295,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_score_tc(TcK a, const __grid_
   // 1024-byte alignment for the swizzled tiles, by offsetting the shared array
   // itself so that every access below stays a shared-space access
   unsigned char* base = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
-  constexpr int natom = DP / 64;
+  constexpr bool NARROW = DP == 32;           // one 64-byte-swizzled atom of 32 columns
+  constexpr int natom = NARROW ? 1 : DP / 64;
+  constexpr int ROWB = NARROW ? 64 : 128;     // bytes of one operand row in an atom
   constexpr bool STAGED = MODE != kModeBF16;  // converters build the A operand
   const TcSmem L = tc_smem(MODE, DP, a.kp, a.nxs, a.nab, a.zst);
   const TcBars B = tc_bars(base, L, a.nxs, a.nab);
@@ -350,10 +363,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_score_tc(TcK a, const __grid_
   if (warp == 0) {
     // ------------------------------------------------------- TMA producer
     if (lane == 0) {
-      mbar_arrive_expect_tx(B.zfull, uint32_t(2 * natom * a.kp * 128));
+      mbar_arrive_expect_tx(B.zfull, uint32_t(2 * natom * a.kp * ROWB));
       for (int at = 0; at < natom; ++at) {
-        tma_load_2d(base + L.zh + at * a.kp * 128, &maps.zh, at * 64, kb0, B.zfull);
-        tma_load_2d(base + L.zl + at * a.kp * 128, &maps.zl, at * 64, kb0, B.zfull);
+        tma_load_2d(base + L.zh + at * a.kp * ROWB, &maps.zh, at * 64, kb0, B.zfull);
+        tma_load_2d(base + L.zl + at * a.kp * ROWB, &maps.zl, at * 64, kb0, B.zfull);
       }
       int t = 0;
       for (; t < my_tiles; ++t) {
@@ -406,17 +419,27 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_score_tc(TcK a, const __grid_
         const uint32_t ahi = smem_u32(base + L.abuf + i * L.abuf_stride);
         const uint32_t alo = ahi + uint32_t(L.lo_off);
         const uint32_t zh = smem_u32(base + L.zh), zl = smem_u32(base + L.zl);
+        if constexpr (NARROW) {
 #pragma unroll
-        for (int at = 0; at < natom; ++at) {
+          for (int ks = 0; ks < 2; ++ks) {
+            const uint32_t o = uint32_t(ks * 32);
+            umma_bf16(d_tmem, umma_desc_sw64(ahi + o), umma_desc_sw64(zh + o), idesc, ks != 0);
+            umma_bf16(d_tmem, umma_desc_sw64(ahi + o), umma_desc_sw64(zl + o), idesc, 1);
+            umma_bf16(d_tmem, umma_desc_sw64(alo + o), umma_desc_sw64(zh + o), idesc, 1);
+          }
+        } else {
 #pragma unroll
-          for (int ks = 0; ks < 4; ++ks) {
-            const uint32_t ao = uint32_t(at * kAtomBytes + ks * 32);
-            const uint32_t bo = uint32_t(at * a.kp * 128 + ks * 32);
-            umma_bf16(d_tmem, umma_desc_sw128(ahi + ao), umma_desc_sw128(zh + bo), idesc,
-                      (at | ks) != 0);
-            umma_bf16(d_tmem, umma_desc_sw128(ahi + ao), umma_desc_sw128(zl + bo), idesc, 1);
-            if (MODE == kModeF32)
-              umma_bf16(d_tmem, umma_desc_sw128(alo + ao), umma_desc_sw128(zh + bo), idesc, 1);
+          for (int at = 0; at < natom; ++at) {
+#pragma unroll
+            for (int ks = 0; ks < 4; ++ks) {
+              const uint32_t ao = uint32_t(at * kAtomBytes + ks * 32);
+              const uint32_t bo = uint32_t(at * a.kp * 128 + ks * 32);
+              umma_bf16(d_tmem, umma_desc_sw128(ahi + ao), umma_desc_sw128(zh + bo), idesc,
+                        (at | ks) != 0);
+              umma_bf16(d_tmem, umma_desc_sw128(ahi + ao), umma_desc_sw128(zl + bo), idesc, 1);
+              if (MODE == kModeF32)
+                umma_bf16(d_tmem, umma_desc_sw128(alo + ao), umma_desc_sw128(zh + bo), idesc, 1);
+            }
           }
         }
         umma_commit(&B.accfull[bsel]);
@@ -589,7 +612,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_score_tc(TcK a, const __grid_
             hw[e] = *reinterpret_cast<const uint32_t*>(&hv);
             lw[e] = pack_bf16x2(rem.x, rem.y);
           }
-          const int off = (col / 64) * kAtomBytes + sw128(r, (col % 64) / 8);
+          const int off = NARROW ? sw64(r, col / 8) : (col / 64) * kAtomBytes + sw128(r, (col % 64) / 8);
           *reinterpret_cast<uint4*>(ab + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
           *reinterpret_cast<uint4*>(ab + L.lo_off + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
         }
@@ -1224,7 +1247,7 @@ int mode_of(int32_t dtype) { return dtype == SIL_F32 ? kModeF32 : dtype == SIL_B
 
 // Padded row width of the tensor path: 64 or 128 columns in one piece, FP32
 // rows of up to 256 columns in 64-column chunks (k_score_tc_wide).
-int tc_dp(int32_t d) { return d > 128 ? 256 : int(round_up(d, 64)); }
+int tc_dp(int32_t d) { return d > 128 ? 256 : d == 32 ? 32 : int(round_up(d, 64)); }
 int tc_max_d(int32_t dtype) { return dtype == SIL_F32 ? 256 : 128; }
 
 // Launch plan: cluster-block width kp, ring depths and whether the centroids
@@ -1431,10 +1454,12 @@ cudaError_t launch_score_tc(const ScoreLaunch& s, const double* g, void* pack, v
     return cudaErrorInvalidValue;
   if (!encode_tmap_1d(&maps.lab, s.labels, CU_TENSOR_MAP_DATA_TYPE_INT32, uint64_t(s.n), kTM))
     return cudaErrorInvalidValue;
+  const uint32_t zbox = dp == 32 ? 32 : 64;  // BF16 columns per box (64- or 128-byte rows)
+  const CUtensorMapSwizzle zsw = dp == 32 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B;
   if (!encode_tmap_2d(&maps.zh, zh, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, uint64_t(dp), uint64_t(kpad),
-                      uint64_t(dp) * 2, 64, uint32_t(kp), CU_TENSOR_MAP_SWIZZLE_128B) ||
+                      uint64_t(dp) * 2, zbox, uint32_t(kp), zsw) ||
       !encode_tmap_2d(&maps.zl, zl, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, uint64_t(dp), uint64_t(kpad),
-                      uint64_t(dp) * 2, 64, uint32_t(kp), CU_TENSOR_MAP_SWIZZLE_128B))
+                      uint64_t(dp) * 2, zbox, uint32_t(kp), zsw))
     return cudaErrorInvalidValue;
 
   TcK k{};
@@ -1481,6 +1506,7 @@ cudaError_t launch_score_tc(const ScoreLaunch& s, const double* g, void* pack, v
   cudaError_t e;
   if (mode == kModeF32) {
     if (dp == 256) e = save ? launch(k_score_tc_wide<true>) : launch(k_score_tc_wide<false>);
+    else if (dp == 32) e = save ? launch(k_score_tc<kModeF32, 32, true>) : launch(k_score_tc<kModeF32, 32, false>);
     else if (dp == 64) e = save ? launch(k_score_tc<kModeF32, 64, true>) : launch(k_score_tc<kModeF32, 64, false>);
     else e = save ? launch(k_score_tc<kModeF32, 128, true>) : launch(k_score_tc<kModeF32, 128, false>);
   } else if (mode == kModeBF16) {

@@ -252,3 +252,50 @@ def test_batched_graph_replay_matches_direct_call():
         np.testing.assert_allclose(S, direct, rtol=0, atol=TOL_S)
     ref = [oracle.linear(X.astype(np.float64), labs[b], k)["S"] for b, k in enumerate(ks)]
     np.testing.assert_allclose(S, ref, rtol=0, atol=TOL_S)
+
+
+# ------------------------------------------- full-size workloads, sampled
+@pytest.mark.parametrize("metric", METRICS)
+def test_at_scale_workload_full_size_sampled(metric):
+    # the benchmark's headline workload (N = 1e7, D = 64, K = 100, FP32) in
+    # its launch configuration; s_i of 20,000 seeded rows against the FP64
+    # linear form with FP64 aggregates of all 1e7 rows, and S against the
+    # oracle's sample mean within its standard error
+    w = synth.workload_at_scale(device="cuda")
+    st = sil.new_status(w.X.device)
+    r = sil.silhouette(w.X, w.labels, w.K, metric, want_s=True, status=st)
+    torch.cuda.synchronize()
+    assert int(st.item()) == 0
+    s_gpu, S_gpu = r.s.cpu().double().numpy(), float(r.S)
+    N, K = w.X.shape[0], w.K
+    count = np.zeros(K, np.int64)
+    s1 = np.zeros((K, w.X.shape[1]), np.float64)
+    s2 = np.zeros(K, np.float64)
+    for lo in range(0, N, 2_000_000):
+        hi = min(N, lo + 2_000_000)
+        part = oracle.aggregate(w.X[lo:hi].cpu().double().numpy(), w.labels[lo:hi].cpu().numpy(), K, metric)
+        count += part[0]
+        s1 += part[1]
+        s2 += part[2]
+    idx = np.sort(np.random.default_rng(2028).choice(N, 20_000, replace=False))
+    it = torch.as_tensor(idx, device="cuda")
+    sub = oracle.linear(w.X[it].cpu().double().numpy(), w.labels[it].cpu().numpy(), K, metric,
+                        agg=(count, s1, s2), idx=np.arange(idx.shape[0]))
+    assert sub["status"] == oracle.OK
+    assert float(np.abs(s_gpu[idx] - sub["s"]).max()) <= TOL_SI
+    assert np.array_equal(count, sil.aggregate(w.X, w.labels, K, metric)[0].cpu().numpy())
+    se = float(np.std(sub["s"])) / np.sqrt(idx.shape[0])
+    assert abs(S_gpu - sub["S"]) <= 5 * se + TOL_S
+
+
+def test_batched_workload_full_size_sampled():
+    # all 256 labelings of the batched workload in one call; three of them
+    # (first, median k, last) against the FP64 linear form over all 2e6 rows
+    X, labs, ks = synth.workload_batched(device="cuda")
+    S = sil.score_batched(X, labs, ks).cpu().numpy()
+    assert S.shape == (len(ks),) and np.all(np.isfinite(S))
+    X64 = X.cpu().double().numpy()
+    order = np.argsort(ks)
+    for b in (0, int(order[len(ks) // 2]), len(ks) - 1):
+        ref = oracle.linear(X64, labs[b].cpu().numpy(), ks[b])
+        assert abs(S[b] - ref["S"]) <= TOL_S, (b, ks[b], S[b], ref["S"])

@@ -32,7 +32,7 @@ def run(Xt, lt, K, metric, path, save=True, cs=None):
 @pytest.mark.parametrize("N,D,K", [(1000, 64, 2), (4097, 64, 7), (20000, 64, 100), (3001, 128, 17),
                                    (5000, 100, 33), (2000, 40, 5), (300, 64, 256), (129, 64, 3),
                                    (700, 128, 128), (700, 128, 256), (3000, 64, 300),
-                                   (2500, 128, 700), (1500, 64, 1000)])
+                                   (2500, 128, 700), (1500, 64, 1000), (3000, 32, 7), (2000, 32, 300)])
 def test_tensor_path_against_bruteforce(metric, dtype, N, D, K):
     if dtype == torch.bfloat16 and (D < 64 or (2 * D) % 16):
         pytest.skip("BF16 tensor path needs d >= 64 and 16-byte rows (TMA)")
