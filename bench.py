@@ -268,6 +268,10 @@ def variant_lines(dev, steps, budget_s, pk_sustained):
     # launches captured once in a CUDA graph, one graph launch per step
     if left() > 0:
         X, labs, ks = synth.workload_batched(device=dev)
+        # tensor-path plans of every distinct k picked by measurement, before timing
+        t0 = time.perf_counter()
+        tuned = sil.autotune_batched(X, labs, ks)
+        t_tune = time.perf_counter() - t0
         sil.score_batched(X, labs, ks)
         s_loop = timed(lambda: sil.score_batched(X, labs, ks), 1, torch.cuda.current_stream())
         g = sil.BatchedGraph(X, labs, ks)
@@ -275,7 +279,9 @@ def variant_lines(dev, steps, budget_s, pk_sustained):
         s = timed(g.run, max(1, min(steps, 3)), torch.cuda.current_stream()) / max(1, min(steps, 3))
         out["batched"] = {"labelings_per_s": len(ks) / s, "point_labelings_per_s": len(ks) * X.shape[0] / s,
                           "ms": s * 1e3, "ms_without_graph": s_loop * 1e3, "N": X.shape[0], "D": 32,
-                          "B": len(ks), "sum_k": int(sum(ks)), "launch": "one CUDA graph per step"}
+                          "B": len(ks), "sum_k": int(sum(ks)), "launch": "one CUDA graph per step",
+                          "autotune": {"shapes": len(tuned), "seconds": t_tune,
+                                       "rank_pass_share": sum(1 for p in tuned.values() if p and p[4]) / max(1, len(tuned))}}
         del X, labs, g
         torch.cuda.empty_cache()
     return out

@@ -209,9 +209,14 @@ int sil_tensor_plan(int32_t dtype, int32_t d, int32_t k, int32_t* block_k, int32
 /*
  * Launch plans of the tensor-core pass 2 for one storage type and shape, for
  * an autotuner.  sil_tensor_plan_candidates writes up to max_plans feasible
- * plans (host int32[max_plans][4]: block_k, A-operand buffers, raw X stages,
- * 1 if the centroids are staged in shared memory for the own-cluster term),
- * best first by the library's cost model, and their number into *n_plans.
+ * plans (host int32[max_plans][5]: block_k, A-operand buffers, raw X stages,
+ * 1 if the centroids are staged in shared memory for the own-cluster term,
+ * rank_pass), best first by the library's cost model, and their number into
+ * *n_plans.  rank_pass = 1 tracks each point's nearest cluster during the
+ * pass over the GEMM results; rank_pass = 0 keeps only the minimum and looks
+ * the cluster up again for the points whose b_i is recomputed in the
+ * difference form (the ill-conditioned ones, see sil_score).  Both give the
+ * same results; which is faster depends on how many points that is.
  * sil_tensor_plan_set makes one plan the choice for (dtype, d, k) in this
  * process (block_k = 0 returns the shape to the cost model); it returns
  * SIL_EINVAL for values out of range and SIL_EUNSUPPORTED when the plan does
@@ -222,7 +227,7 @@ int sil_tensor_plan(int32_t dtype, int32_t d, int32_t k, int32_t* block_k, int32
 int sil_tensor_plan_candidates(int32_t dtype, int32_t d, int32_t k, int32_t* plans, int32_t max_plans,
                                int32_t* n_plans);
 int sil_tensor_plan_set(int32_t dtype, int32_t d, int32_t k, int32_t block_k, int32_t a_buffers,
-                        int32_t x_stages, int32_t stage_centroids);
+                        int32_t x_stages, int32_t stage_centroids, int32_t rank_pass);
 
 /* Human-readable name of a return code or of one status flag. */
 const char* sil_status_string(int32_t status);

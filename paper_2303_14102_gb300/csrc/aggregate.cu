@@ -374,7 +374,7 @@ __device__ __forceinline__ uint4 load_chunk(const GatherK& a, uint32_t row, int 
 // position hold the same columns), un-shift in FP64 and add to the outputs.
 // Every lane of the warp must call it.
 template <int DT, int CPL, bool WEIGHTED>
-__device__ __forceinline__ void run_flush(const GatherK& a, int b, float2* acc, const float2* rsh, float2 sq2,
+__device__ __forceinline__ void run_flush(const GatherK& a, int b, float2* acc, const float2* rsh, double sqd,
                                           float wacc, double mrows, const int* colb, const int* colend, int G,
                                           int rg, int lane) {
   constexpr int Q = Chunk<DT>::Q;
@@ -389,7 +389,7 @@ __device__ __forceinline__ void run_flush(const GatherK& a, int b, float2* acc, 
   }
   // weighted: every lane now holds the run's total weight in wacc
   const double m = WEIGHTED ? double(wacc) : mrows;
-  double s2p = WEIGHTED ? 0.0 : double(sq2.x) + double(sq2.y);
+  double s2p = WEIGHTED ? 0.0 : sqd;
   if (rg == 0) {
 #pragma unroll
     for (int i = 0; i < EL2; ++i) {
@@ -496,7 +496,10 @@ __global__ void __launch_bounds__(kGatherThreads, 2) k_gather_reduce(GatherK a) 
       load_shift<DT, CPL>(a, b, colb, colend, rsh);
 #pragma unroll
       for (int i = 0; i < EL2; ++i) acc[i] = make_float2(0.f, 0.f);
+      // squared terms: FP32 within a block of 32 entries, FP64 across blocks
+      // (short FP32 chains keep the sum of squares free of drift)
       float2 sq2 = make_float2(0.f, 0.f);
+      double sqd = 0.0;
       float wacc = 0.f;
       int64_t blk = cur;
       uint32_t iv = blk + lane < se ? __ldg(a.idx + blk + lane) : 0u;
@@ -562,11 +565,13 @@ __global__ void __launch_bounds__(kGatherThreads, 2) k_gather_reduce(GatherK a) 
             }
           }
         }
+        sqd += double(sq2.x) + double(sq2.y);
+        sq2 = make_float2(0.f, 0.f);
         iv = ivn;
         wvb = wvn;
         blk = nxt;
       }
-      run_flush<DT, CPL, WEIGHTED>(a, b, acc, rsh, sq2, wacc, WEIGHTED ? 0.0 : double(se - cur), colb, colend, G, rg, lane);
+      run_flush<DT, CPL, WEIGHTED>(a, b, acc, rsh, sqd, wacc, WEIGHTED ? 0.0 : double(se - cur), colb, colend, G, rg, lane);
       cur = se;
     }
   }
@@ -664,7 +669,8 @@ __global__ void __launch_bounds__(256, 1) k_gather_reduce_tma(GatherK a, const _
     load_shift<DT, CPL>(a, b, colb, colend, rsh);
 #pragma unroll
     for (int i = 0; i < EL2; ++i) acc[i] = make_float2(0.f, 0.f);
-    float2 sq2 = make_float2(0.f, 0.f);
+    float2 sq2 = make_float2(0.f, 0.f);  // squared terms: FP32 within a block, FP64 across
+    double sqd = 0.0;
     float wacc = 0.f;
 
     for (int t = 0; t < nblk; ++t) {
@@ -741,7 +747,9 @@ __global__ void __launch_bounds__(256, 1) k_gather_reduce_tma(GatherK a, const _
           }
           if (slast < bend) break;
           // the run ends inside this step: add it and start the next bucket
-          run_flush<DT, CPL, WEIGHTED>(a, b, acc, rsh, sq2, wacc, double(bend - blo), colb, colend, G, rg, lane);
+          run_flush<DT, CPL, WEIGHTED>(a, b, acc, rsh, sqd + double(sq2.x) + double(sq2.y), wacc,
+                                       double(bend - blo), colb, colend, G, rg, lane);
+          sqd = 0.0;
           blo = bend;
           while (__ldg(a.bstart + b + 1) <= uint32_t(blo)) ++b;
           bend = min(e1, int64_t(__ldg(a.bstart + b + 1)));
@@ -752,13 +760,20 @@ __global__ void __launch_bounds__(256, 1) k_gather_reduce_tma(GatherK a, const _
           wacc = 0.f;
         }
       }
-      __syncwarp();  // every lane is done with the slot before it is refilled
+      sqd += double(sq2.x) + double(sq2.y);
+      sq2 = make_float2(0.f, 0.f);
+      // every lane is done with the slot before the TMA (async proxy)
+      // refills it: fence the generic-proxy reads, then sync the warp
+      fence_proxy_async_smem();
+      __syncwarp();
       if (t + S < nblk) {
         issue(t + S, pending);
         pending = t + S + 1 < nblk ? block_rows(t + S + 1) : 0u;
       }
     }
-    if (bend > blo) run_flush<DT, CPL, WEIGHTED>(a, b, acc, rsh, sq2, wacc, double(bend - blo), colb, colend, G, rg, lane);
+    if (bend > blo)
+      run_flush<DT, CPL, WEIGHTED>(a, b, acc, rsh, sqd + double(sq2.x) + double(sq2.y), wacc, double(bend - blo), colb,
+                                   colend, G, rg, lane);
     gblk += uint32_t(nblk);
   }
 }

@@ -379,9 +379,9 @@ int sil_tensor_plan_candidates(int32_t dtype, int32_t d, int32_t k, int32_t* pla
 }
 
 int sil_tensor_plan_set(int32_t dtype, int32_t d, int32_t k, int32_t block_k, int32_t a_buffers,
-                        int32_t x_stages, int32_t stage_centroids) {
+                        int32_t x_stages, int32_t stage_centroids, int32_t rank_pass) {
   if (d <= 0 || k <= 0 || dtype < SIL_F32 || dtype > SIL_FP8_E4M3) return SIL_EINVAL;
-  return tc_plan_set(dtype, d, k, block_k, a_buffers, x_stages, stage_centroids);
+  return tc_plan_set(dtype, d, k, block_k, a_buffers, x_stages, stage_centroids, rank_pass);
 }
 
 const char* sil_status_string(int32_t status) {

@@ -31,10 +31,10 @@ namespace {
 // g = (sum_k Y_k) / (sum_k n_k); one warp-column per output column.
 __global__ void k_fin_global(const unsigned long long* count, const double* s1, int32_t k,
                              int32_t d, int32_t dz, double* g, float* gf, uint32_t* status) {
-  __shared__ double part[8][33];
+  __shared__ double part[32][33];
   __shared__ unsigned long long ntot;
   __shared__ int nnon;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
   if (threadIdx.x == 0) {
     ntot = 0;
     nnon = 0;
@@ -49,14 +49,20 @@ __global__ void k_fin_global(const unsigned long long* count, const double* s1, 
   atomicAdd(&ntot, my);
   atomicAdd(&nnon, mynon);
   const int c = blockIdx.x * 32 + lane;
-  double s = 0.0;
-  if (c < d)
-    for (int kk = warp; kk < k; kk += 8) s += s1[int64_t(kk) * d + c];
-  part[warp][lane] = s;
+  // four independent partial sums per lane keep several loads in flight
+  double s[4] = {0.0, 0.0, 0.0, 0.0};
+  if (c < d) {
+    int kk = warp;
+    for (; kk + 3 * nwarp < k; kk += 4 * nwarp)
+#pragma unroll
+      for (int u = 0; u < 4; ++u) s[u] += s1[int64_t(kk + u * nwarp) * d + c];
+    for (; kk < k; kk += nwarp) s[0] += s1[int64_t(kk) * d + c];
+  }
+  part[warp][lane] = (s[0] + s[1]) + (s[2] + s[3]);
   __syncthreads();
   if (warp == 0 && c < dz) {
     double t = 0.0;
-    for (int w = 0; w < 8; ++w) t += part[w][lane];
+    for (int w = 0; w < nwarp; ++w) t += part[w][lane];
     const double gv = (c < d && ntot > 0) ? t / double(ntot) : 0.0;
     g[c] = gv;
     gf[c] = float(gv);
@@ -494,8 +500,8 @@ bool vec_ok_s(const void* X, int32_t dtype, int64_t ldx) {
 
 cudaError_t launch_finalize(const FinLaunch& f) {
   const int dz = int(round_up(f.d, 4));
-  k_fin_global<<<unsigned(cdiv(dz, 32)), 256, 0, f.stream>>>(f.count, f.s1, f.k, f.d, dz, f.g, f.gf,
-                                                             f.status);
+  k_fin_global<<<unsigned(cdiv(dz, 32)), 1024, 0, f.stream>>>(f.count, f.s1, f.k, f.d, dz, f.g, f.gf,
+                                                              f.status);
   k_fin_clusters<<<f.k, 128, 0, f.stream>>>(f.count, f.s1, f.s2, f.d, dz, f.g, f.zf, f.cl);
   return cudaGetLastError();
 }

@@ -16,18 +16,21 @@
 //     centroids, x.mu' = q.(s * mu'): q.Zhi + q.Zlo.
 // The epilogue reads each point's accumulators from TMEM, forms
 // d_k = ||x'||^2 + cb_k - 2 inv x.mu'_k (cb_k = bias_k + 2 g.mu'_k folds the
-// centring on the global mean g back in; inv = 1/||x|| for cosine) and keeps
-// the minimum over k != own cluster.  The own-cluster term a_i uses the exact
-// difference form in FP32 on the converter warps.  The n x K matrix never
-// leaves TMEM.
+// centring on the global mean g back in; inv = 1/||x|| for cosine) and ranks
+// the clusters k != own cluster by it.  b_i itself is then the nearest
+// cluster's distance in the difference form ||x' - mu'_k||^2 + W_k/n_k,
+// from the point's operand row, which stays in shared memory until the
+// epilogue has read it; the own-cluster term a_i uses the same form on the
+// converter warps.  The n x K matrix never leaves TMEM.
 //
 // Clusters are processed in blocks of at most 256 (the MMA N).  With one
 // block the epilogue finishes s_i and the per-CTA sums itself.  With G > 1
 // blocks the grid is (point ranges) x (G blocks): each CTA keeps its block's
 // split centroids resident in shared memory and streams the X tiles of its
 // point range -- the G CTAs of a range read the same tiles at about the same
-// time, so the repeats are served by L2 -- and writes, per point, the minimum
-// over its block (and the argmin when the backward record is wanted).  The
+// time, so the repeats are served by L2 -- and writes, per point, the
+// distance to the nearest cluster of its block (and its index when the
+// backward record is wanted).  The
 // CTA whose block holds the point's own cluster also writes a_i and ||x'||^2.
 // k_tc_combine then takes the minimum over the blocks and finishes s_i.
 //
@@ -161,6 +164,191 @@ __device__ __forceinline__ float2 fp8x2_to_float2(uint32_t two_codes) {
   return __half22float2(__half2(h));
 }
 
+// Squared distance ||x inv - g - z||^2 of tile row r, read back from its
+// operand row in the A buffer (FP32: hi + lo, ~17 bits; BF16: exact; FP8:
+// the code times its column scale), to the centroid z (dz columns, from
+// shared memory when zsm is set, else global memory).  The difference form
+// has no cancellation, unlike ||x'||^2 + bias - 2 x'.mu'.
+template <int MODE, int DP>
+__device__ __forceinline__ float tc_row_dist(const unsigned char* ab, int lo_off, int r, float inv,
+                                             const float* gsm, const float* csm, const float* zsm,
+                                             const float* zg, int dz) {
+  float2 acc = make_float2(0.f, 0.f);
+  const float2 inv2 = make_float2(inv, inv);
+#pragma unroll
+  for (int c8 = 0; c8 < DP / 8; ++c8) {
+    const int col = 8 * c8;
+    const int off = DP == 32 ? sw64(r, c8) : (col / 64) * kAtomBytes + sw128(r, (col % 64) / 8);
+    const uint4 hv = *reinterpret_cast<const uint4*>(ab + off);
+    const uint32_t hw[4] = {hv.x, hv.y, hv.z, hv.w};
+    float x[8];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&hw[e]));
+      x[2 * e] = f.x;
+      x[2 * e + 1] = f.y;
+    }
+    if (MODE == kModeF32) {
+      const uint4 lv = *reinterpret_cast<const uint4*>(ab + lo_off + off);
+      const uint32_t lw[4] = {lv.x, lv.y, lv.z, lv.w};
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&lw[e]));
+        x[2 * e] += f.x;
+        x[2 * e + 1] += f.y;
+      }
+    }
+#pragma unroll
+    for (int h4 = 0; h4 < 2; ++h4) {
+      const int c4 = col + 4 * h4;
+      float2 xa = make_float2(x[4 * h4], x[4 * h4 + 1]), xb = make_float2(x[4 * h4 + 2], x[4 * h4 + 3]);
+      if (MODE == kModeFP8) {
+        const float4 s4 = *reinterpret_cast<const float4*>(csm + c4);
+        xa = __fmul2_rn(xa, make_float2(s4.x, s4.y));
+        xb = __fmul2_rn(xb, make_float2(s4.z, s4.w));
+      }
+      float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (c4 < dz) z = zsm ? *reinterpret_cast<const float4*>(zsm + c4) : __ldg(reinterpret_cast<const float4*>(zg + c4));
+      const float4 g = *reinterpret_cast<const float4*>(gsm + c4);
+      const float2 ca = __ffma2_rn(xa, inv2, make_float2(-g.x, -g.y));
+      const float2 cb = __ffma2_rn(xb, inv2, make_float2(-g.z, -g.w));
+      const float2 da = __fadd2_rn(ca, make_float2(-z.x, -z.y));
+      const float2 db = __fadd2_rn(cb, make_float2(-z.z, -z.w));
+      acc = __ffma2_rn(da, da, acc);
+      acc = __ffma2_rn(db, db, acc);
+    }
+  }
+  return acc.x + acc.y;
+}
+
+// The same distance with the row read from global memory (FP32, d columns).
+__device__ __forceinline__ float tc_row_dist_global(const float* xr, int d, float inv, const float* gsm,
+                                                    const float* zg) {
+  float2 acc = make_float2(0.f, 0.f);
+  const float2 inv2 = make_float2(inv, inv);
+  int c = 0;
+  for (; c + 4 <= d; c += 4) {
+    const float4 x = __ldg(reinterpret_cast<const float4*>(xr + c));
+    const float4 z = __ldg(reinterpret_cast<const float4*>(zg + c));
+    const float4 g = *reinterpret_cast<const float4*>(gsm + c);
+    const float2 ca = __ffma2_rn(make_float2(x.x, x.y), inv2, make_float2(-g.x, -g.y));
+    const float2 cb = __ffma2_rn(make_float2(x.z, x.w), inv2, make_float2(-g.z, -g.w));
+    const float2 da = __fadd2_rn(ca, make_float2(-z.x, -z.y));
+    const float2 db = __fadd2_rn(cb, make_float2(-z.z, -z.w));
+    acc = __ffma2_rn(da, da, acc);
+    acc = __ffma2_rn(db, db, acc);
+  }
+  float t = acc.x + acc.y;
+  for (; c < d; ++c) {
+    const float e = fmaf(__ldg(xr + c), inv, -gsm[c]) - __ldg(zg + c);
+    t = fmaf(e, e, t);
+  }
+  return t;
+}
+
+// The expanded form d_k = ||x'||^2 + v_k, v_k = cb_k - 2 inv x.mu'_k, loses
+// about log2(kappa) bits to cancellation, kappa = (||x inv|| + ||mu'_k||)^2 / d_k,
+// and the tensor-core sums round towards zero, so that loss is a bias that
+// survives the mean S.  Rows with kappa above kCondExact take the difference
+// form instead (the bias left on the others is ~1e-7 relative or less).
+// rb = ||g|| + sqrt(max_k bias_k) bounds ||x inv|| - ||x'|| + ||mu'_k||.
+constexpr float kCondExact = 6.f;
+__device__ __forceinline__ bool tc_ill_conditioned(float xn2, float best, float rb) {
+  const float m = sqrtf(xn2) + rb;
+  return !(m * m <= kCondExact * (xn2 + best));
+}
+
+// rb of tc_ill_conditioned over all k clusters (so that the choice of form
+// for a row does not depend on how the clusters are split into blocks) and
+// the centre g (dp columns, zero padded); warp-collective.
+__device__ __forceinline__ float tc_cond_radius(const float4* cl, int k, const float* g, int dp, int lane) {
+  float mb = 0.f, g2 = 0.f;
+  for (int i = lane; i < k; i += 32) {
+    const float v = __ldg(&cl[i]).x;
+    if (v < INFINITY) mb = fmaxf(mb, v);
+  }
+  for (int c = lane; c < dp; c += 32) g2 = fmaf(g[c], g[c], g2);
+  for (int o = 16; o > 0; o >>= 1) {
+    mb = fmaxf(mb, __shfl_xor_sync(0xffffffffu, mb, o));
+    g2 += __shfl_xor_sync(0xffffffffu, g2, o);
+  }
+  return sqrtf(g2) + sqrtf(mb);
+}
+
+// Minimum over the columns k != own of v_k = cb_k + sc acc_k of this warp's
+// 32 TMEM lanes (acc at tbase), with its index in kb when ARG; 64 columns per
+// round trip to TMEM (four loads in flight, one wait).  Warp-collective.
+template <bool ARG>
+__device__ __forceinline__ float tc_lane_min(uint32_t tbase, int kp, const float* cbs, float sc, int own, int& kb) {
+  float best = INFINITY;
+  const float2 sc2 = make_float2(sc, sc);
+  for (int c0 = 0; c0 < kp; c0 += 64) {
+    uint32_t rv[4][16];
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      if (c0 + 16 * j < kp) tmem_ld16_async(tbase + uint32_t(c0 + 16 * j), rv[j]);
+    tmem_wait_ld();
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      if (c0 + 16 * j >= kp) break;
+      reg_fence16(rv[j]);
+      const float4* cb4 = reinterpret_cast<const float4*>(cbs + c0 + 16 * j);
+#pragma unroll
+      for (int q4 = 0; q4 < 4; ++q4) {
+        const float4 cq = cb4[q4];
+        const float2 va = __ffma2_rn(sc2, make_float2(__uint_as_float(rv[j][4 * q4]), __uint_as_float(rv[j][4 * q4 + 1])),
+                                     make_float2(cq.x, cq.y));
+        const float2 vb = __ffma2_rn(sc2, make_float2(__uint_as_float(rv[j][4 * q4 + 2]), __uint_as_float(rv[j][4 * q4 + 3])),
+                                     make_float2(cq.z, cq.w));
+        const float vals[4] = {va.x, va.y, vb.x, vb.y};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int kk = c0 + 16 * j + 4 * q4 + e;
+          if (ARG) {
+            if (kk != own && vals[e] < best) {
+              best = vals[e];
+              kb = kk;
+            }
+          } else if (kk != own) {
+            best = fminf(best, vals[e]);
+          }
+        }
+      }
+    }
+  }
+  return best;
+}
+
+// Index of the first column k != own whose v_k, recomputed exactly as
+// tc_lane_min computes it, equals best; -1 if none or !want.  Warp-collective.
+__device__ __forceinline__ int tc_lane_find(uint32_t tbase, int kp, const float* cbs, float sc, int own, float best,
+                                            bool want) {
+  int kb = -1;
+  const float2 sc2 = make_float2(sc, sc);
+  for (int c0 = 0; c0 < kp; c0 += 16) {  // one load in flight: few live registers
+    uint32_t rv[16];
+    tmem_ld16_async(tbase + uint32_t(c0), rv);
+    tmem_wait_ld();
+    reg_fence16(rv);
+    const float4* cb4 = reinterpret_cast<const float4*>(cbs + c0);
+#pragma unroll
+    for (int q4 = 0; q4 < 4; ++q4) {
+      const float4 cq = cb4[q4];
+      const float2 va = __ffma2_rn(sc2, make_float2(__uint_as_float(rv[4 * q4]), __uint_as_float(rv[4 * q4 + 1])),
+                                   make_float2(cq.x, cq.y));
+      const float2 vb = __ffma2_rn(sc2, make_float2(__uint_as_float(rv[4 * q4 + 2]), __uint_as_float(rv[4 * q4 + 3])),
+                                   make_float2(cq.z, cq.w));
+      const float vals[4] = {va.x, va.y, vb.x, vb.y};
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int kk = c0 + 4 * q4 + e;
+        if (kb < 0 && kk != own && vals[e] == best) kb = kk;  // the first, as the argmin pass
+      }
+    }
+  }
+  return want ? kb : -1;
+}
+
 // ------------------------------------------------------------ parameters
 struct TcK {
   int64_t n;
@@ -175,6 +363,8 @@ struct TcK {
   int32_t nxs;  // raw X stages (MODE 0, 2)
   int32_t nab;  // A buffers
   int32_t zst;  // stride of the staged centroids (0: not staged)
+  const float* xg;  // the rows (FP32), for the difference form of ill-conditioned rows
+  int64_t ldx;
   const float* zf;
   const float4* cl;
   const float* gf;
@@ -185,9 +375,9 @@ struct TcK {
   float* sb;
   int32_t* skstar;
   double* partials;
-  float* pmin;    // [nblk][n] block minimum of (cb - 2 inv x.mu'), NaN for an invalid row
-  int32_t* parg;  // [nblk][n] its argmin (backward record)
-  float2* pown;   // [n]       (a_i before scaling, ||x'||^2), from the own cluster's block
+  float* pmin;    // [nblk][n] distance to the block's nearest cluster, NaN for an invalid row
+  int32_t* parg;  // [nblk][n] its index (backward record)
+  float* pown;    // [n]       a_i before scaling, from the own cluster's block
   uint32_t* status;
 };
 
@@ -289,7 +479,7 @@ __device__ __forceinline__ bool tc_wait(uint64_t* bar, uint32_t parity, volatile
   return true;
 }
 
-template <int MODE, int DP, bool SAVE>
+template <int MODE, int DP, bool TRACK>
 __global__ void __launch_bounds__(kTcThreads, 1) k_score_tc(TcK a, const __grid_constant__ TcMaps maps) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   // 1024-byte alignment for the swizzled tiles, by offsetting the shared array
@@ -318,8 +508,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_score_tc(TcK a, const __grid_
     }
     for (int i = 0; i < a.nab; ++i) {
       mbar_init(&B.afull[i], STAGED ? kConvWarps : 1);  // converters, or the TMA transaction
-      // MMA commit (+ the 4 epilogue warps in BF16 mode, whose row terms share the slot)
-      mbar_init(&B.aempty[i], STAGED ? 1 : 1 + 4);
+      // MMA commit + the 4 epilogue warps, which read the operand rows back
+      mbar_init(&B.aempty[i], 1 + 4);
       mbar_init(&B.pfull[i], kConvWarps);  // BF16 mode: the row terms are written
     }
     for (int i = 0; i < 2; ++i) {
@@ -419,13 +609,22 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_score_tc(TcK a, const __grid_
         const uint32_t ahi = smem_u32(base + L.abuf + i * L.abuf_stride);
         const uint32_t alo = ahi + uint32_t(L.lo_off);
         const uint32_t zh = smem_u32(base + L.zh), zl = smem_u32(base + L.zl);
+        // The small correction products (x.Z_lo, x_lo.Z_hi) go into the fresh
+        // accumulator first and the large x_hi.Z_hi products last: each
+        // tensor-core accumulation rounds relative to the running magnitude,
+        // so this order adds the fewest steps at the final, largest magnitude
+        // (a measured bias of ~1e-6 in b_i when the order was interleaved).
         if constexpr (NARROW) {
 #pragma unroll
           for (int ks = 0; ks < 2; ++ks) {
             const uint32_t o = uint32_t(ks * 32);
-            umma_bf16(d_tmem, umma_desc_sw64(ahi + o), umma_desc_sw64(zh + o), idesc, ks != 0);
-            umma_bf16(d_tmem, umma_desc_sw64(ahi + o), umma_desc_sw64(zl + o), idesc, 1);
+            umma_bf16(d_tmem, umma_desc_sw64(ahi + o), umma_desc_sw64(zl + o), idesc, ks != 0);
             umma_bf16(d_tmem, umma_desc_sw64(alo + o), umma_desc_sw64(zh + o), idesc, 1);
+          }
+#pragma unroll
+          for (int ks = 0; ks < 2; ++ks) {
+            const uint32_t o = uint32_t(ks * 32);
+            umma_bf16(d_tmem, umma_desc_sw64(ahi + o), umma_desc_sw64(zh + o), idesc, 1);
           }
         } else {
 #pragma unroll
@@ -434,11 +633,18 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_score_tc(TcK a, const __grid_
             for (int ks = 0; ks < 4; ++ks) {
               const uint32_t ao = uint32_t(at * kAtomBytes + ks * 32);
               const uint32_t bo = uint32_t(at * a.kp * 128 + ks * 32);
-              umma_bf16(d_tmem, umma_desc_sw128(ahi + ao), umma_desc_sw128(zh + bo), idesc,
-                        (at | ks) != 0);
-              umma_bf16(d_tmem, umma_desc_sw128(ahi + ao), umma_desc_sw128(zl + bo), idesc, 1);
+              umma_bf16(d_tmem, umma_desc_sw128(ahi + ao), umma_desc_sw128(zl + bo), idesc, (at | ks) != 0);
               if (MODE == kModeF32)
                 umma_bf16(d_tmem, umma_desc_sw128(alo + ao), umma_desc_sw128(zh + bo), idesc, 1);
+            }
+          }
+#pragma unroll
+          for (int at = 0; at < natom; ++at) {
+#pragma unroll
+            for (int ks = 0; ks < 4; ++ks) {
+              const uint32_t ao = uint32_t(at * kAtomBytes + ks * 32);
+              const uint32_t bo = uint32_t(at * a.kp * 128 + ks * 32);
+              umma_bf16(d_tmem, umma_desc_sw128(ahi + ao), umma_desc_sw128(zh + bo), idesc, 1);
             }
           }
         }
@@ -524,7 +730,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_score_tc(TcK a, const __grid_
           }
         }
         own = reinterpret_cast<const int32_t*>(xs + raw_tile_bytes(MODE, DP))[r];
-        // the stage is in registers now: let the producer refill it
+        // the stage is in registers now: let the producer refill it.  The
+        // refill is an async-proxy (TMA) write after these generic-proxy
+        // reads, so the reads are fenced against it before the release.
+        fence_proxy_async_smem();
         __syncwarp();
         if (lane == 0) mbar_arrive(&B.xempty[j]);
       } else {
@@ -645,6 +854,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_score_tc(TcK a, const __grid_
     // ---------------------------------------------- epilogue warps 10..13
     const int q = warp & 3;       // TMEM lane quarter this warp may access
     const int r = q * 32 + lane;  // tile row = TMEM lane
+    const float rb = tc_cond_radius(a.cl, a.k, gsm, DP, lane);
     float tsum = 0.f;
     for (int t = 0; t < my_tiles; ++t) {
       const int i = t % a.nab, bsel = t & 1, sl = STAGED ? t % kSideSlots : i;
@@ -660,56 +870,39 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_score_tc(TcK a, const __grid_
       const bool row_ok = code != kRowInvalid;
       const int own = code >= 0 ? code : (row_ok && code <= -2 ? -2 - code : -1);  // in-block index
       const float sc = -2.f * side[2 * kTM + r];
-      float best = INFINITY;
-      int kb = -1;
+      const float xn2 = side[r];
       const uint32_t tbase = tmem + uint32_t(bsel * a.acc_cols) + (uint32_t(q * 32) << 16);
-      const float2 sc2 = make_float2(sc, sc);
-      // 64 columns per round trip to TMEM: four loads in flight, one wait
-      for (int c0 = 0; c0 < a.kp; c0 += 64) {
-        uint32_t rv[4][16];
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-          if (c0 + 16 * j < a.kp) tmem_ld16_async(tbase + uint32_t(c0 + 16 * j), rv[j]);
-        tmem_wait_ld();
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          if (c0 + 16 * j >= a.kp) break;
-          reg_fence16(rv[j]);
-          const float4* cb4 = reinterpret_cast<const float4*>(cbs + c0 + 16 * j);
-#pragma unroll
-          for (int q4 = 0; q4 < 4; ++q4) {
-            const float4 cq = cb4[q4];
-            const float2 va = __ffma2_rn(sc2, make_float2(__uint_as_float(rv[j][4 * q4]), __uint_as_float(rv[j][4 * q4 + 1])),
-                                         make_float2(cq.x, cq.y));
-            const float2 vb = __ffma2_rn(sc2, make_float2(__uint_as_float(rv[j][4 * q4 + 2]), __uint_as_float(rv[j][4 * q4 + 3])),
-                                         make_float2(cq.z, cq.w));
-            const float vals[4] = {va.x, va.y, vb.x, vb.y};
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-              const int kk = c0 + 16 * j + 4 * q4 + e;
-              if (SAVE) {
-                if (kk != own && vals[e] < best) {
-                  best = vals[e];
-                  kb = kk;
-                }
-              } else if (kk != own) {
-                best = fminf(best, vals[e]);
-              }
-            }
-          }
-        }
-      }
+      int kb = -1;
+      const float best = tc_lane_min<TRACK>(tbase, a.kp, cbs, sc, own, kb);
+      // The GEMM ranks the clusters; for ill-conditioned rows b_i is then the
+      // nearest cluster's distance in the difference form, like a_i, from the
+      // point's operand row (the A buffer is held until this has been read).
+      const bool exact = row_ok && best < INFINITY && tc_ill_conditioned(xn2, best, rb);
+      if (!TRACK && __any_sync(0xffffffffu, exact)) kb = tc_lane_find(tbase, a.kp, cbs, sc, own, best, exact);
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&B.accempty[bsel]);
+      float dk = best < INFINITY ? xn2 + best : INFINITY;
+      if (exact && kb >= 0) {
+        if (!STAGED) tc_wait(&B.afull[i], (t / a.nab) & 1, abort_flag, a.status);  // TMA-written rows
+        const float4 co = clsm[kb];
+        const float wn = co.y > 0.f ? co.z / co.y : 0.f;  // W_k / n_k
+        dk = wn + tc_row_dist<MODE, DP>(base + L.abuf + i * L.abuf_stride, L.lo_off, r, side[2 * kTM + r], gsm, csm,
+                                        a.zst ? zsm + kb * a.zst : nullptr, a.zf + int64_t(kb0 + kb) * a.dz, a.dz);
+      }
+      if (STAGED) {
+        // the operand rows are read: the converters may rebuild the buffer
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&B.aempty[i]);
+      }
       const int64_t row = (blockIdx.x + int64_t(t) * gridDim.x) * kTM + r;
       if (row < a.n) {
         if (fused) {
           float av = 0.f, bv = INFINITY, sv = 0.f;
           if (row_ok) {
-            const bool has_b = best < INFINITY;
+            const bool has_b = dk < INFINITY;
             av = fmaxf(0.f, a.scale * side[kTM + r]);
-            bv = has_b ? fmaxf(0.f, a.scale * (side[r] + best)) : INFINITY;
+            bv = has_b ? fmaxf(0.f, a.scale * dk) : INFINITY;
             if (code >= 0 && has_b) {
               const float m = fmaxf(av, bv);
               sv = m > 0.f ? (av <= bv ? 1.f - av / bv : bv / av - 1.f) : 0.f;
@@ -719,7 +912,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_score_tc(TcK a, const __grid_
             kb = -1;
           }
           if (a.s_out) a.s_out[row] = sv;
-          if (SAVE) {
+          if (TRACK && a.sa) {
             a.sa[row] = av;
             a.sb[row] = bv;
             a.skstar[row] = kb;
@@ -727,11 +920,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_score_tc(TcK a, const __grid_
           tsum += sv;
         } else {
           const int64_t o = int64_t(blockIdx.y) * a.n + row;
-          a.pmin[o] = row_ok ? best : __int_as_float(0x7fc00000);
-          if (SAVE) a.parg[o] = (row_ok && kb >= 0) ? kb0 + kb : -1;
-          if (own >= 0) a.pown[row] = make_float2(side[kTM + r], side[r]);
+          a.pmin[o] = row_ok ? dk : __int_as_float(0x7fc00000);
+          if (TRACK && a.parg) a.parg[o] = (row_ok && dk < INFINITY) ? kb0 + kb : -1;
+          if (own >= 0) a.pown[row] = side[kTM + r];
         }
       }
+      // BF16: the A buffer (refilled by TMA) also holds the labels of the slot
+      if (!STAGED) fence_proxy_async_smem();
       __syncwarp();
       if (lane == 0) mbar_arrive(STAGED ? &B.sempty[sl] : &B.aempty[i]);
     }
@@ -762,7 +957,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_score_tc(TcK a, const __grid_
 // chunk; cosine needs 1/||x|| before x' exists, so it accumulates x.x, x.g,
 // x.(g + mu'_c), g.g and ||g + mu'_c||^2 and forms ||x' ||^2 and
 // ||x' - mu'_c||^2 from them at the end (all terms are O(1) for unit vectors).
-template <bool SAVE>
+template <bool TRACK>
 __global__ void __launch_bounds__(kTcThreads, 1) k_score_tc_wide(TcK a, const __grid_constant__ TcMaps maps) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* base = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
@@ -950,7 +1145,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_score_tc_wide(TcK a, const __
           x[4 * c4 + 2] = v.z;
           x[4 * c4 + 3] = v.w;
         }
-        // the stage is in registers now: let the producer refill it
+        // the stage is in registers now: let the producer refill it.  The
+        // refill is an async-proxy (TMA) write after these generic-proxy
+        // reads, so the reads are fenced against it before the release.
+        fence_proxy_async_smem();
         __syncwarp();
         if (lane == 0) mbar_arrive(&B.xempty[j]);
 #pragma unroll
@@ -1049,6 +1247,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_score_tc_wide(TcK a, const __
     // ---------------------------------------------- epilogue warps 10..13
     const int q = warp & 3;
     const int r = q * 32 + lane;
+    const float rb = tc_cond_radius(a.cl, a.k, gsm, DP, lane);
     float tsum = 0.f;
     for (int t = 0; t < my_tiles; ++t) {
       const int bsel = t & 1, sl = t % kSideSlots;
@@ -1060,45 +1259,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_score_tc_wide(TcK a, const __
       const bool row_ok = code != kRowInvalid;
       const int own = code >= 0 ? code : (row_ok && code <= -2 ? -2 - code : -1);
       const float sc = -2.f * side[2 * kTM + r];
-      const float xn2 = side[r], aown = side[kTM + r];
-      float best = INFINITY;
-      int kb = -1;
+      const float xn2 = side[r], aown = side[kTM + r], inv = side[2 * kTM + r];
       const uint32_t tbase = tmem + uint32_t(bsel * a.acc_cols) + (uint32_t(q * 32) << 16);
-      const float2 sc2 = make_float2(sc, sc);
-      for (int c0 = 0; c0 < a.kp; c0 += 64) {
-        uint32_t rv[4][16];
-#pragma unroll
-        for (int jj = 0; jj < 4; ++jj)
-          if (c0 + 16 * jj < a.kp) tmem_ld16_async(tbase + uint32_t(c0 + 16 * jj), rv[jj]);
-        tmem_wait_ld();
-#pragma unroll
-        for (int jj = 0; jj < 4; ++jj) {
-          if (c0 + 16 * jj >= a.kp) break;
-          reg_fence16(rv[jj]);
-          const float4* cb4 = reinterpret_cast<const float4*>(cbs + c0 + 16 * jj);
-#pragma unroll
-          for (int q4 = 0; q4 < 4; ++q4) {
-            const float4 cq = cb4[q4];
-            const float2 va = __ffma2_rn(sc2, make_float2(__uint_as_float(rv[jj][4 * q4]), __uint_as_float(rv[jj][4 * q4 + 1])),
-                                         make_float2(cq.x, cq.y));
-            const float2 vb = __ffma2_rn(sc2, make_float2(__uint_as_float(rv[jj][4 * q4 + 2]), __uint_as_float(rv[jj][4 * q4 + 3])),
-                                         make_float2(cq.z, cq.w));
-            const float vals[4] = {va.x, va.y, vb.x, vb.y};
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-              const int kk = c0 + 16 * jj + 4 * q4 + e;
-              if (SAVE) {
-                if (kk != own && vals[e] < best) {
-                  best = vals[e];
-                  kb = kk;
-                }
-              } else if (kk != own) {
-                best = fminf(best, vals[e]);
-              }
-            }
-          }
-        }
-      }
+      int kb = -1;
+      const float best = tc_lane_min<TRACK>(tbase, a.kp, cbs, sc, own, kb);
+      const bool exact = row_ok && best < INFINITY && tc_ill_conditioned(xn2, best, rb);
+      if (!TRACK && __any_sync(0xffffffffu, exact)) kb = tc_lane_find(tbase, a.kp, cbs, sc, own, best, exact);
       tc_fence_before();
       __syncwarp();
       if (lane == 0) {
@@ -1106,13 +1272,21 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_score_tc_wide(TcK a, const __
         mbar_arrive(&B.sempty[sl]);
       }
       const int64_t row = (blockIdx.x + int64_t(t) * gridDim.x) * kTM + r;
+      float dk = best < INFINITY ? xn2 + best : INFINITY;
+      if (exact && kb >= 0 && row < a.n) {
+        // ill-conditioned row: the difference form, with the row read back
+        // from global memory (the chunked A buffers hold only part of it)
+        const float4 co = clsm[kb];
+        const float wn = co.y > 0.f ? co.z / co.y : 0.f;  // W_k / n_k
+        dk = wn + tc_row_dist_global(a.xg + row * a.ldx, a.d, inv, gsm, a.zf + int64_t(kb0 + kb) * a.dz);
+      }
       if (row < a.n) {
         if (fused) {
           float av = 0.f, bv = INFINITY, sv = 0.f;
           if (row_ok) {
-            const bool has_b = best < INFINITY;
+            const bool has_b = dk < INFINITY;
             av = fmaxf(0.f, a.scale * aown);
-            bv = has_b ? fmaxf(0.f, a.scale * (xn2 + best)) : INFINITY;
+            bv = has_b ? fmaxf(0.f, a.scale * dk) : INFINITY;
             if (code >= 0 && has_b) {
               const float m = fmaxf(av, bv);
               sv = m > 0.f ? (av <= bv ? 1.f - av / bv : bv / av - 1.f) : 0.f;
@@ -1122,7 +1296,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_score_tc_wide(TcK a, const __
             kb = -1;
           }
           if (a.s_out) a.s_out[row] = sv;
-          if (SAVE) {
+          if (TRACK && a.sa) {
             a.sa[row] = av;
             a.sb[row] = bv;
             a.skstar[row] = kb;
@@ -1130,9 +1304,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_score_tc_wide(TcK a, const __
           tsum += sv;
         } else {
           const int64_t o = int64_t(blockIdx.y) * a.n + row;
-          a.pmin[o] = row_ok ? best : __int_as_float(0x7fc00000);
-          if (SAVE) a.parg[o] = (row_ok && kb >= 0) ? kb0 + kb : -1;
-          if (own >= 0) a.pown[row] = make_float2(aown, xn2);
+          a.pmin[o] = row_ok ? dk : __int_as_float(0x7fc00000);
+          if (TRACK && a.parg) a.parg[o] = (row_ok && kb >= 0) ? kb0 + kb : -1;
+          if (own >= 0) a.pown[row] = aown;
         }
       }
     }
@@ -1157,7 +1331,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_score_tc_wide(TcK a, const __
 // in order and only a strictly smaller value replaces the best), then Eq. 2
 // with the singleton and max(a, b) = 0 rules, and one partial sum per CTA.
 __global__ void k_tc_combine(int64_t n, int32_t k, int32_t nblk, const int32_t* labels, const float4* cl,
-                             float scale, const float* pmin, const int32_t* parg, const float2* pown,
+                             float scale, const float* pmin, const int32_t* parg, const float* pown,
                              float* s_out, float* sa, float* sb, int32_t* skstar, double* partials) {
   float tsum = 0.f;
   for (int64_t row = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; row < n;
@@ -1176,10 +1350,9 @@ __global__ void k_tc_combine(int64_t n, int32_t k, int32_t nblk, const int32_t* 
       }
     }
     if (!bad) {
-      const float2 pw = pown[row];
       const bool has_b = best < INFINITY;
-      av = fmaxf(0.f, scale * pw.x);
-      bv = has_b ? fmaxf(0.f, scale * (pw.y + best)) : INFINITY;
+      av = fmaxf(0.f, scale * pown[row]);
+      bv = has_b ? fmaxf(0.f, scale * best) : INFINITY;
       if (has_b && cl[own].w > 1.5f) {
         const float m = fmaxf(av, bv);
         sv = m > 0.f ? (av <= bv ? 1.f - av / bv : bv / av - 1.f) : 0.f;
@@ -1209,7 +1382,7 @@ __global__ void k_tc_combine(int64_t n, int32_t k, int32_t nblk, const int32_t* 
 
 // Split centroids and per-cluster constants for the tensor-core kernel:
 //   zh/zl (bf16 [kpad][dp], zero padded) with zh + zl ~ (cs *) mu'_k to ~16 bits,
-//   cb[k] = bias_k + 2 g.mu'_k (+inf for empty clusters and padding).
+//   cb[k] = bias_k + 2 g.(zh + zl)_k (+inf for empty clusters and padding).
 // With FP8 storage the column scales cs are folded into the split values.
 __global__ void k_tc_pack(const float* zf, const float4* cl, const double* g, const float* cs, int32_t k,
                           int32_t d, int32_t dz, int32_t dp, __nv_bfloat16* zh, __nv_bfloat16* zl,
@@ -1221,9 +1394,16 @@ __global__ void k_tc_pack(const float* zf, const float4* cl, const double* g, co
     const float z = (kk < k && c < dz) ? zf[int64_t(kk) * dz + c] : 0.f;
     const float zs = cs ? (c < d ? z * cs[c] : 0.f) : z;
     const __nv_bfloat16 hh = __float2bfloat16_rn(zs);
+    const __nv_bfloat16 ll = __float2bfloat16_rn(zs - __bfloat162float(hh));
     zh[int64_t(kk) * dp + c] = hh;
-    zl[int64_t(kk) * dp + c] = __float2bfloat16_rn(zs - __bfloat162float(hh));
-    if (c < d) dot += g[c] * double(z);
+    zl[int64_t(kk) * dp + c] = ll;
+    // The centring term uses the split value the GEMM actually sees, so the
+    // split's residual enters d_k only through x' = x - g (zero mean), not as
+    // a per-cluster offset g.(mu' - hi - lo).
+    if (c < d) {
+      const double zz = double(__bfloat162float(hh)) + double(__bfloat162float(ll));
+      dot += g[c] * (cs ? (cs[c] != 0.f ? zz / double(cs[c]) : double(z)) : zz);
+    }
   }
   for (int o = 16; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = dot;
@@ -1253,17 +1433,23 @@ int tc_max_d(int32_t dtype) { return dtype == SIL_F32 ? 256 : 128; }
 // Launch plan: cluster-block width kp, ring depths and whether the centroids
 // are staged for the own-cluster term.  Candidates are ranked by a small cost
 // model -- work per point over the G blocks times penalties for shallow rings
-// (a single A buffer serialises conversion and MMA; a single raw stage
-// exposes the TMA latency) and for unstaged centroids -- and the cheapest
-// plan whose shared memory fits is taken.
+// (an A buffer is held from conversion until the epilogue has read its rows
+// back; a single raw stage exposes the TMA latency) and for unstaged
+// centroids -- and the cheapest plan whose shared memory fits is taken.
+// rank = 1 tracks the argmin in the main pass over the accumulators (the
+// kernels built for the backward record); rank = 0 takes the plain minimum
+// and rescans for the index only in warps with an ill-conditioned row.  The
+// model takes rank = 0; data with mostly ill-conditioned rows (many close
+// clusters far from the mean) run faster with rank = 1, which an autotuner
+// finds by measurement.
 struct TcPlan {
-  int kp, nblk, nxs, nab, zst, smem;
+  int kp, nblk, nxs, nab, zst, smem, rank;
 };
 
 // Plans chosen by measurement (sil_tensor_plan_set) for one (dtype, d, k);
 // they take precedence over the cost model.
 struct PlanOverride {
-  int32_t dtype, d, k, kp, nab, nxs, stage_z;
+  int32_t dtype, d, k, kp, nab, nxs, stage_z, rank;
 };
 std::mutex g_plan_mu;
 std::vector<PlanOverride> g_plan_over;
@@ -1288,12 +1474,19 @@ void tc_plan_enumerate(int32_t dtype, int32_t k, int32_t d, F&& visit) {
           // its A-operand reads below ~64), plus a fixed share for conversion,
           // row terms and the per-block results
           double cost = double(nblk) * (std::max(kp, 64) + dp);
-          if (nab < 2) cost *= 1.4;
-          if (staged && nxs < 2) cost *= 1.2;
+          // an A buffer is held from conversion until the epilogue has read
+          // its rows back: one buffer serialises the roles, two overlap them
+          // partly
+          if (nab < 2) cost *= 1.8;
+          if (staged && nab == 2) cost *= 1.08;
+          if (staged && nxs < 2) cost *= 1.05;
           if (staged && nxs == 2) cost *= 1.02;
           if (!staged && nab == 2) cost *= 1.02;
-          if (!zst) cost *= 1.05;
-          visit(TcPlan{kp, nblk, nxs, nab, zst, smem}, cost);
+          if (!zst) cost *= 1.12;  // own-centroid rows from L1/L2 instead of shared memory
+          // equal modelled cost: the model keeps rank = 0 (enumerated first),
+          // and a candidate list pairs the two for each layout
+          visit(TcPlan{kp, nblk, nxs, nab, zst, smem, 0}, cost);
+          visit(TcPlan{kp, nblk, nxs, nab, zst, smem, 1}, cost);
         }
       }
     }
@@ -1311,7 +1504,7 @@ bool tc_plan(int32_t dtype, int32_t k, int32_t d, TcPlan* out) {
       const int zst = o.stage_z ? dz + 4 : 0;
       const int smem = tc_smem(mode, dp, o.kp, o.nxs, o.nab, zst).total;
       if (smem <= kSmemMax) {
-        *out = TcPlan{o.kp, int(cdiv(k, o.kp)), o.nxs, o.nab, zst, smem};
+        *out = TcPlan{o.kp, int(cdiv(k, o.kp)), o.nxs, o.nab, zst, smem, o.rank};
         return true;
       }
     }
@@ -1367,16 +1560,18 @@ int tc_plan_candidates(int32_t dtype, int32_t d, int32_t k, int32_t* plans, int3
   int n = 0;
   for (const auto& c : all) {
     if (n >= max_plans) break;
-    plans[4 * n + 0] = c.second.kp;
-    plans[4 * n + 1] = c.second.nab;
-    plans[4 * n + 2] = c.second.nxs;
-    plans[4 * n + 3] = c.second.zst ? 1 : 0;
+    plans[5 * n + 0] = c.second.kp;
+    plans[5 * n + 1] = c.second.nab;
+    plans[5 * n + 2] = c.second.nxs;
+    plans[5 * n + 3] = c.second.zst ? 1 : 0;
+    plans[5 * n + 4] = c.second.rank;
     ++n;
   }
   return n;
 }
 
-int tc_plan_set(int32_t dtype, int32_t d, int32_t k, int32_t kp, int32_t nab, int32_t nxs, int32_t stage_z) {
+int tc_plan_set(int32_t dtype, int32_t d, int32_t k, int32_t kp, int32_t nab, int32_t nxs, int32_t stage_z,
+                int32_t rank) {
   std::lock_guard<std::mutex> lock(g_plan_mu);
   for (size_t i = 0; i < g_plan_over.size(); ++i)
     if (g_plan_over[i].dtype == dtype && g_plan_over[i].d == d && g_plan_over[i].k == k) {
@@ -1384,13 +1579,14 @@ int tc_plan_set(int32_t dtype, int32_t d, int32_t k, int32_t kp, int32_t nab, in
       break;
     }
   if (kp == 0) return SIL_OK;  // cleared: back to the cost model
-  if (d > tc_max_d(dtype) || kp < 16 || kp > kMaxBlockN || kp % 16 || nab < 1 || nab > 4 || nxs < 1 || nxs > 3)
+  if (d > tc_max_d(dtype) || kp < 16 || kp > kMaxBlockN || kp % 16 || nab < 1 || nab > 4 || nxs < 1 || nxs > 3 ||
+      rank < 0 || rank > 1)
     return SIL_EINVAL;
   const int mode = mode_of(dtype);
   const int zst = stage_z ? int(round_up(d, 4)) + 4 : 0;
   if (tc_smem(mode, tc_dp(d), kp, mode == kModeBF16 ? 1 : nxs, nab, zst).total > kSmemMax)
     return SIL_EUNSUPPORTED;
-  g_plan_over.push_back(PlanOverride{dtype, d, k, kp, nab, mode == kModeBF16 ? 1 : nxs, stage_z ? 1 : 0});
+  g_plan_over.push_back(PlanOverride{dtype, d, k, kp, nab, mode == kModeBF16 ? 1 : nxs, stage_z ? 1 : 0, rank});
   return SIL_OK;
 }
 
@@ -1405,7 +1601,7 @@ size_t tc_partial_bytes(int64_t n, int32_t d, int32_t k, int32_t dtype) {
   TcPlan p;
   if (!tc_plan(dtype, k, d, &p) || p.nblk == 1) return 0;
   const size_t N = size_t(n), G = size_t(p.nblk);
-  return align256(G * N * 4) + align256(G * N * 4) + align256(N * 8);
+  return align256(G * N * 4) + align256(G * N * 4) + align256(N * 4);
 }
 
 cudaError_t launch_score_tc(const ScoreLaunch& s, const double* g, void* pack, void* partial_ws,
@@ -1414,7 +1610,7 @@ cudaError_t launch_score_tc(const ScoreLaunch& s, const double* g, void* pack, v
   if (!tc_plan(s.dtype, s.k, s.d, &plan)) return cudaErrorInvalidValue;
   auto need = [&](int nblk) {
     const size_t N = size_t(s.n), G = size_t(nblk);
-    return nblk > 1 ? align256(G * N * 4) * 2 + align256(N * 8) : size_t(0);
+    return nblk > 1 ? align256(G * N * 4) * 2 + align256(N * 4) : size_t(0);
   };
   if (need(plan.nblk) > partial_bytes) {
     // the workspace was sized for another plan (e.g. a larger k of a batch):
@@ -1475,6 +1671,8 @@ cudaError_t launch_score_tc(const ScoreLaunch& s, const double* g, void* pack, v
   k.nxs = plan.nxs;
   k.nab = plan.nab;
   k.zst = plan.zst;
+  k.xg = mode == kModeF32 ? static_cast<const float*>(s.X) : nullptr;
+  k.ldx = s.ldx;
   k.zf = s.zf;
   k.cl = s.cl;
   k.gf = s.gf;
@@ -1487,12 +1685,15 @@ cudaError_t launch_score_tc(const ScoreLaunch& s, const double* g, void* pack, v
   k.partials = s.partials;
   k.status = status;
   const bool save = s.sa != nullptr;
+  // the kernels built for the backward record track the argmin in the main
+  // pass; without the record they serve rank = 1 plans
+  const bool track = save || plan.rank == 1;
   if (plan.nblk > 1) {
     const size_t N = size_t(s.n), G = size_t(plan.nblk);
     char* p = static_cast<char*>(partial_ws);
     k.pmin = reinterpret_cast<float*>(p);
-    k.parg = reinterpret_cast<int32_t*>(p + align256(G * N * 4));
-    k.pown = reinterpret_cast<float2*>(p + 2 * align256(G * N * 4));
+    k.parg = save ? reinterpret_cast<int32_t*>(p + align256(G * N * 4)) : nullptr;
+    k.pown = reinterpret_cast<float*>(p + 2 * align256(G * N * 4));
   }
   const int64_t ntiles = cdiv(s.n, kTM);
   const int per_block = std::max(1, kNumSMs / plan.nblk);
@@ -1505,22 +1706,22 @@ cudaError_t launch_score_tc(const ScoreLaunch& s, const double* g, void* pack, v
   };
   cudaError_t e;
   if (mode == kModeF32) {
-    if (dp == 256) e = save ? launch(k_score_tc_wide<true>) : launch(k_score_tc_wide<false>);
-    else if (dp == 32) e = save ? launch(k_score_tc<kModeF32, 32, true>) : launch(k_score_tc<kModeF32, 32, false>);
-    else if (dp == 64) e = save ? launch(k_score_tc<kModeF32, 64, true>) : launch(k_score_tc<kModeF32, 64, false>);
-    else e = save ? launch(k_score_tc<kModeF32, 128, true>) : launch(k_score_tc<kModeF32, 128, false>);
+    if (dp == 256) e = track ? launch(k_score_tc_wide<true>) : launch(k_score_tc_wide<false>);
+    else if (dp == 32) e = track ? launch(k_score_tc<kModeF32, 32, true>) : launch(k_score_tc<kModeF32, 32, false>);
+    else if (dp == 64) e = track ? launch(k_score_tc<kModeF32, 64, true>) : launch(k_score_tc<kModeF32, 64, false>);
+    else e = track ? launch(k_score_tc<kModeF32, 128, true>) : launch(k_score_tc<kModeF32, 128, false>);
   } else if (mode == kModeBF16) {
-    if (dp == 64) e = save ? launch(k_score_tc<kModeBF16, 64, true>) : launch(k_score_tc<kModeBF16, 64, false>);
-    else e = save ? launch(k_score_tc<kModeBF16, 128, true>) : launch(k_score_tc<kModeBF16, 128, false>);
+    if (dp == 64) e = track ? launch(k_score_tc<kModeBF16, 64, true>) : launch(k_score_tc<kModeBF16, 64, false>);
+    else e = track ? launch(k_score_tc<kModeBF16, 128, true>) : launch(k_score_tc<kModeBF16, 128, false>);
   } else {
-    e = save ? launch(k_score_tc<kModeFP8, 128, true>) : launch(k_score_tc<kModeFP8, 128, false>);
+    e = track ? launch(k_score_tc<kModeFP8, 128, true>) : launch(k_score_tc<kModeFP8, 128, false>);
   }
   if (e != cudaSuccess) return e;
   if (plan.nblk == 1) {
     *s.n_partials = int(grid.x);
     return cudaSuccess;
   }
-  const int cgrid = int(std::max<int64_t>(1, std::min<int64_t>(cdiv(s.n, 256), int64_t(kNumSMs) * 4)));
+  const int cgrid = int(std::max<int64_t>(1, std::min<int64_t>(cdiv(s.n, 256), kMaxPartials)));
   k_tc_combine<<<cgrid, 256, 0, s.stream>>>(s.n, s.k, plan.nblk, s.labels, s.cl, k.scale, k.pmin,
                                             save ? k.parg : nullptr, k.pown, s.s_out, s.sa, s.sb, s.skstar,
                                             s.partials);

@@ -212,7 +212,8 @@ size_t tc_pack_bytes(int32_t k, int32_t d);
 // stages, staged centroids), and a measured choice for one shape.
 bool tc_plan_query(int32_t dtype, int32_t d, int32_t k, int32_t* block_k, int32_t* n_blocks);
 int tc_plan_candidates(int32_t dtype, int32_t d, int32_t k, int32_t* plans, int32_t max_plans);
-int tc_plan_set(int32_t dtype, int32_t d, int32_t k, int32_t kp, int32_t nab, int32_t nxs, int32_t stage_z);
+int tc_plan_set(int32_t dtype, int32_t d, int32_t k, int32_t kp, int32_t nab, int32_t nxs, int32_t stage_z,
+                int32_t rank);
 // Bytes of the per-block results when k needs several cluster blocks (else 0).
 size_t tc_partial_bytes(int64_t n, int32_t d, int32_t k, int32_t dtype);
 cudaError_t launch_score_tc(const ScoreLaunch& s, const double* g, void* pack, void* partial_ws,

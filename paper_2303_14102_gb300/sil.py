@@ -81,7 +81,7 @@ def load(build_if_stale: bool = True) -> ctypes.CDLL:
             lib.sil_tensor_plan.restype = ctypes.c_int
             lib.sil_tensor_plan_candidates.argtypes = [i32, i32, i32, vp, i32, vp]
             lib.sil_tensor_plan_candidates.restype = ctypes.c_int
-            lib.sil_tensor_plan_set.argtypes = [i32, i32, i32, i32, i32, i32, i32]
+            lib.sil_tensor_plan_set.argtypes = [i32, i32, i32, i32, i32, i32, i32, i32]
             lib.sil_tensor_plan_set.restype = ctypes.c_int
             lib.sil_status_string.argtypes = [i32]
             lib.sil_status_string.restype = ctypes.c_char_p
@@ -337,20 +337,21 @@ _DTYPES = {torch.float32: 0, torch.bfloat16: 1, torch.float8_e4m3fn: 2}
 
 
 def tensor_plan_candidates(dtype: torch.dtype, D: int, K: int, max_plans: int = 8):
-    """Feasible tensor-path plans (block_k, A buffers, X stages, staged centroids), best modelled first."""
+    """Feasible tensor-path plans (block_k, A buffers, X stages, staged centroids, rank pass),
+    best modelled first."""
     lib = load()
-    buf = (ctypes.c_int32 * (4 * max_plans))()
+    buf = (ctypes.c_int32 * (5 * max_plans))()
     n = ctypes.c_int32(0)
     _rc(lib.sil_tensor_plan_candidates(_DTYPES[dtype], D, K, buf, max_plans, ctypes.byref(n)),
         "sil_tensor_plan_candidates")
-    return [tuple(buf[4 * i:4 * i + 4]) for i in range(n.value)]
+    return [tuple(buf[5 * i:5 * i + 5]) for i in range(n.value)]
 
 
 def tensor_plan_set(dtype: torch.dtype, D: int, K: int, plan=None) -> None:
     """Make `plan` (from tensor_plan_candidates) the choice for this shape; None restores the model."""
     lib = load()
-    bk, nab, nxs, stz = plan if plan is not None else (0, 0, 0, 0)
-    _rc(lib.sil_tensor_plan_set(_DTYPES[dtype], D, K, bk, nab, nxs, stz), "sil_tensor_plan_set")
+    bk, nab, nxs, stz, rank = plan if plan is not None else (0, 0, 0, 0, 0)
+    _rc(lib.sil_tensor_plan_set(_DTYPES[dtype], D, K, bk, nab, nxs, stz, rank), "sil_tensor_plan_set")
 
 
 def autotune(X: torch.Tensor, labels: torch.Tensor, K: int, metric: str = "sqeuclidean",
@@ -382,6 +383,19 @@ def autotune(X: torch.Tensor, labels: torch.Tensor, K: int, metric: str = "sqeuc
     best = min(results)[1]
     tensor_plan_set(X.dtype, D, K, best)
     return results
+
+
+def autotune_batched(X: torch.Tensor, labels: torch.Tensor, ks, metric: str = "sqeuclidean",
+                     col_scale: torch.Tensor | None = None, max_plans: int = 4, reps: int = 2):
+    """:func:`autotune` for each distinct k of a batch of labelings (B x N),
+    on the first labeling with that k.  Returns {k: fastest plan}."""
+    best = {}
+    for b, k in enumerate(int(k) for k in ks):
+        if k in best:
+            continue
+        res = autotune(X, labels[b], k, metric, col_scale=col_scale, max_plans=max_plans, reps=reps)
+        best[k] = min(res)[1] if res else None
+    return best
 
 
 def silhouette(X: torch.Tensor, labels: torch.Tensor, K: int, metric: str = "sqeuclidean",

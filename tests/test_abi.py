@@ -135,10 +135,11 @@ def test_tensor_plan_candidates_and_override():
     cands = sil.tensor_plan_candidates(torch.float32, 64, 100, 8)
     assert 1 <= len(cands) <= 8
     assert cands[0][0] == sil.tensor_plan(torch.float32, 64, 100)[0]  # best modelled first
-    for bk, nab, nxs, stz in cands:
-        assert bk % 16 == 0 and 1 <= nab <= 4 and 1 <= nxs <= 3 and stz in (0, 1)
+    for bk, nab, nxs, stz, rank in cands:
+        assert bk % 16 == 0 and 1 <= nab <= 4 and 1 <= nxs <= 3 and stz in (0, 1) and rank in (0, 1)
+    assert cands[0][4] == 0  # the model prefers the plain minimum pass
     try:
-        sil.tensor_plan_set(torch.float32, 64, 100, (48, 2, 2, 0))
+        sil.tensor_plan_set(torch.float32, 64, 100, (48, 2, 2, 0, 1))
         assert sil.tensor_plan(torch.float32, 64, 100) == (48, 3)
         assert sil.tensor_plan(torch.float32, 64, 101) == (112, 1)  # other shapes untouched
     finally:
@@ -147,6 +148,7 @@ def test_tensor_plan_candidates_and_override():
 
 
 def test_tensor_plan_set_rejects_bad_plans(lib):
-    assert lib.sil_tensor_plan_set(0, 64, 100, 40, 2, 2, 0) == sil.SIL_EINVAL      # not a multiple of 16
-    assert lib.sil_tensor_plan_set(0, 64, 100, 256, 4, 3, 1) == sil.SIL_EUNSUPPORTED  # too much shared memory
-    assert lib.sil_tensor_plan_set(0, 300, 100, 64, 2, 2, 0) == sil.SIL_EINVAL     # d > 256
+    assert lib.sil_tensor_plan_set(0, 64, 100, 40, 2, 2, 0, 0) == sil.SIL_EINVAL      # not a multiple of 16
+    assert lib.sil_tensor_plan_set(0, 64, 100, 256, 4, 3, 1, 0) == sil.SIL_EUNSUPPORTED  # too much shared memory
+    assert lib.sil_tensor_plan_set(0, 300, 100, 64, 2, 2, 0, 0) == sil.SIL_EINVAL     # d > 256
+    assert lib.sil_tensor_plan_set(0, 64, 100, 64, 2, 2, 0, 2) == sil.SIL_EINVAL      # rank pass is 0 or 1

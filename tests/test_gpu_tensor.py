@@ -209,3 +209,105 @@ def test_tensor_refuses_ineligible_shapes():
     agg = sil.aggregate(Xt, lt, 3)
     with pytest.raises(sil.SilError):
         sil.score(Xt, lt, 3, agg, path="tensor")
+
+
+@pytest.mark.parametrize("recipe", ["at_scale", "batched_labeling_0", "precision_bf16"])
+def test_tensor_and_simt_agree_on_every_row_at_full_size(recipe):
+    # every row, not a sample: a pipeline hazard that corrupts one row in a
+    # million shows up here
+    if recipe == "at_scale":
+        w = synth.workload_at_scale(device="cuda")
+        X, lab, K = w.X, w.labels, w.K
+    elif recipe == "batched_labeling_0":
+        X, labs, ks = synth.workload_batched(device="cuda", B=1)
+        lab, K = labs[0].contiguous(), ks[0]
+    else:
+        w = synth.workload_precision(device="cuda", N=20_000_000)
+        X, lab, K = synth.to_bf16(w.X), w.labels, w.K
+    agg = sil.aggregate(X, lab, K)
+    rt = sil.score(X, lab, K, agg, want_s=True, save=True, path="tensor")
+    rs = sil.score(X, lab, K, agg, want_s=True, save=True, path="simt")
+    torch.cuda.synchronize()
+    d = (rt.s - rs.s).abs()
+    assert int((d > TOL_SI).sum()) == 0, (recipe, float(d.max()), int(d.argmax()))
+    assert abs(float(rt.S) - float(rs.S)) <= TOL_S
+
+
+# ------------------------------------------------ conditioning and launch plans
+def _close_clusters(N, D, kmin, kmax, B=2):
+    """Voronoi cells of k random points of a Gaussian-blob set: many clusters
+    whose separation b_i is small next to ||x'||^2 (the ill-conditioned case
+    of the expanded distance)."""
+    X, labs, ks = synth.workload_batched(device="cuda", N=N, D=D, B=B, k_low=kmin, k_high=kmax)
+    return X, labs, ks
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16])
+def test_close_clusters_match_the_oracle_without_bias(dtype):
+    # b_i of such rows comes from the difference form, so the error of S is
+    # not the tensor cores' round-towards-zero bias times the cancellation
+    X, labs, ks = _close_clusters(100_000, 64, 250, 450)
+    Xs = X.to(dtype)
+    for b, k in enumerate(ks):
+        lab = labs[b].contiguous()
+        agg = sil.aggregate(Xs, lab, k)
+        r = sil.score(Xs, lab, k, agg, want_s=True, save=True, path="tensor")
+        torch.cuda.synchronize()
+        ref = oracle.linear(dequant(Xs), lab.cpu().numpy(), k)
+        assert abs(float(r.S) - ref["S"]) <= TOL_S, (k, float(r.S) - ref["S"])
+        _, bt, _ = sil.unpack_saved(r.saved, X.shape[0])
+        rel = (bt.cpu().double().numpy() - ref["b"]) / ref["b"]
+        assert abs(float(np.mean(rel))) <= 2e-7, (k, float(np.mean(rel)))
+        assert float((r.s.cpu().double() - torch.from_numpy(ref["s"])).abs().max()) <= TOL_SI
+
+
+@pytest.mark.parametrize("shape", ["close_d32", "blobs_d64", "close_d64_two_blocks"])
+def test_every_plan_gives_the_same_scores(shape):
+    # block widths, ring depths, staged or unstaged centroids and both rank
+    # passes: the same s_i (bit for bit between the two rank passes of one
+    # layout, whose MMAs are identical).  Across block widths a row can differ
+    # where two clusters are nearly tied: the GEMM ranks them to ~1e-6 and
+    # only the winner of each block is recomputed exactly, so a split of the
+    # pair over two blocks recovers the true minimum.
+    if shape == "blobs_d64":
+        w = synth.workload_at_scale(device="cuda", N=60_000)
+        X, lab, K = w.X, w.labels, w.K
+    else:
+        D = 32 if shape == "close_d32" else 64
+        X, labs, ks = _close_clusters(60_000, D, 300, 300 if D == 32 else 500, B=1)
+        lab, K = labs[0].contiguous(), ks[0]
+    D = X.shape[1]
+    agg = sil.aggregate(X, lab, K)
+    plans = sil.tensor_plan_candidates(X.dtype, D, K, 12)
+    assert any(p[4] == 1 for p in plans) and any(p[4] == 0 for p in plans)
+    out = {}
+    try:
+        for p in plans:
+            sil.tensor_plan_set(X.dtype, D, K, p)
+            r = sil.score(X, lab, K, agg, want_s=True, path="tensor")
+            torch.cuda.synchronize()
+            out[p] = (r.s.clone(), float(r.S))
+    finally:
+        sil.tensor_plan_set(X.dtype, D, K, None)
+    s0, S0 = out[plans[0]]
+    for p, (s, S) in out.items():
+        twin = p[:4] + (1 - p[4],)
+        if twin in out:
+            assert torch.equal(s, out[twin][0]), p
+        assert float((s - s0).abs().max()) <= 2e-5, p
+        assert abs(S - S0) <= 1e-7, p  # FP32 partial sums in another grid order
+
+
+def test_autotune_keeps_a_plan_that_scores_correctly():
+    X, labs, ks = _close_clusters(50_000, 32, 150, 150, B=1)
+    lab, K = labs[0].contiguous(), ks[0]
+    try:
+        res = sil.autotune(X, lab, K, max_plans=4, reps=1)
+        assert len(res) == 4 and all(t > 0 for t, _ in res)
+        agg = sil.aggregate(X, lab, K)
+        r = sil.score(X, lab, K, agg, path="tensor")
+        torch.cuda.synchronize()
+        ref = oracle.linear(X.cpu().double().numpy(), lab.cpu().numpy(), K)
+        assert abs(float(r.S) - ref["S"]) <= TOL_S
+    finally:
+        sil.tensor_plan_set(X.dtype, 32, K, None)
