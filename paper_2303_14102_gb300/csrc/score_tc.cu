@@ -221,18 +221,27 @@ __device__ __forceinline__ float tc_row_dist(const unsigned char* ab, int lo_off
   return acc.x + acc.y;
 }
 
-// The same distance with the row read from global memory (FP32, d columns).
+// The same distance with the row read from global memory (FP32, d columns);
+// z may point to shared or global memory.  SPLIT rounds each element to the
+// hi + lo BF16 pair the A buffer would hold, so that both sources give the
+// same bits.
+template <bool SPLIT>
 __device__ __forceinline__ float tc_row_dist_global(const float* xr, int d, float inv, const float* gsm,
                                                     const float* zg) {
+  auto rd = [](float v) {
+    if (!SPLIT) return v;
+    const float hi = __bfloat162float(__float2bfloat16_rn(v));
+    return hi + __bfloat162float(__float2bfloat16_rn(v - hi));
+  };
   float2 acc = make_float2(0.f, 0.f);
   const float2 inv2 = make_float2(inv, inv);
   int c = 0;
   for (; c + 4 <= d; c += 4) {
     const float4 x = __ldg(reinterpret_cast<const float4*>(xr + c));
-    const float4 z = __ldg(reinterpret_cast<const float4*>(zg + c));
+    const float4 z = *reinterpret_cast<const float4*>(zg + c);
     const float4 g = *reinterpret_cast<const float4*>(gsm + c);
-    const float2 ca = __ffma2_rn(make_float2(x.x, x.y), inv2, make_float2(-g.x, -g.y));
-    const float2 cb = __ffma2_rn(make_float2(x.z, x.w), inv2, make_float2(-g.z, -g.w));
+    const float2 ca = __ffma2_rn(make_float2(rd(x.x), rd(x.y)), inv2, make_float2(-g.x, -g.y));
+    const float2 cb = __ffma2_rn(make_float2(rd(x.z), rd(x.w)), inv2, make_float2(-g.z, -g.w));
     const float2 da = __fadd2_rn(ca, make_float2(-z.x, -z.y));
     const float2 db = __fadd2_rn(cb, make_float2(-z.z, -z.w));
     acc = __ffma2_rn(da, da, acc);
@@ -240,7 +249,7 @@ __device__ __forceinline__ float tc_row_dist_global(const float* xr, int d, floa
   }
   float t = acc.x + acc.y;
   for (; c < d; ++c) {
-    const float e = fmaf(__ldg(xr + c), inv, -gsm[c]) - __ldg(zg + c);
+    const float e = fmaf(rd(__ldg(xr + c)), inv, -gsm[c]) - zg[c];
     t = fmaf(e, e, t);
   }
   return t;
@@ -489,6 +498,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_score_tc(TcK a, const __grid_
   constexpr int natom = NARROW ? 1 : DP / 64;
   constexpr int ROWB = NARROW ? 64 : 128;     // bytes of one operand row in an atom
   constexpr bool STAGED = MODE != kModeBF16;  // converters build the A operand
+  // where the epilogue reads an ill-conditioned row back: FP32 plans without
+  // the argmin pass (few such rows) from global memory, so that an A buffer is
+  // free once its MMAs are; the others from the A buffer, held until then
+  constexpr bool ROWS_GLOBAL = MODE == kModeF32 && !TRACK;
   const TcSmem L = tc_smem(MODE, DP, a.kp, a.nxs, a.nab, a.zst);
   const TcBars B = tc_bars(base, L, a.nxs, a.nab);
   volatile int* abort_flag = B.abort_flag;
@@ -508,8 +521,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_score_tc(TcK a, const __grid_
     }
     for (int i = 0; i < a.nab; ++i) {
       mbar_init(&B.afull[i], STAGED ? kConvWarps : 1);  // converters, or the TMA transaction
-      // MMA commit + the 4 epilogue warps, which read the operand rows back
-      mbar_init(&B.aempty[i], 1 + 4);
+      // MMA commit (+ the 4 epilogue warps where they read the operand rows back)
+      mbar_init(&B.aempty[i], ROWS_GLOBAL ? 1 : 1 + 4);
       mbar_init(&B.pfull[i], kConvWarps);  // BF16 mode: the row terms are written
     }
     for (int i = 0; i < 2; ++i) {
@@ -883,19 +896,25 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_score_tc(TcK a, const __grid_
       __syncwarp();
       if (lane == 0) mbar_arrive(&B.accempty[bsel]);
       float dk = best < INFINITY ? xn2 + best : INFINITY;
+      const int64_t row = (blockIdx.x + int64_t(t) * gridDim.x) * kTM + r;
       if (exact && kb >= 0) {
-        if (!STAGED) tc_wait(&B.afull[i], (t / a.nab) & 1, abort_flag, a.status);  // TMA-written rows
         const float4 co = clsm[kb];
         const float wn = co.y > 0.f ? co.z / co.y : 0.f;  // W_k / n_k
-        dk = wn + tc_row_dist<MODE, DP>(base + L.abuf + i * L.abuf_stride, L.lo_off, r, side[2 * kTM + r], gsm, csm,
-                                        a.zst ? zsm + kb * a.zst : nullptr, a.zf + int64_t(kb0 + kb) * a.dz, a.dz);
+        if (ROWS_GLOBAL) {
+          dk = wn + tc_row_dist_global<true>(a.xg + row * a.ldx, a.d, side[2 * kTM + r], gsm,
+                                             a.zst ? zsm + kb * a.zst : a.zf + int64_t(kb0 + kb) * a.dz);
+        } else {
+          if (!STAGED) tc_wait(&B.afull[i], (t / a.nab) & 1, abort_flag, a.status);  // TMA-written rows
+          dk = wn + tc_row_dist<MODE, DP>(base + L.abuf + i * L.abuf_stride, L.lo_off, r, side[2 * kTM + r], gsm,
+                                          csm, a.zst ? zsm + kb * a.zst : nullptr, a.zf + int64_t(kb0 + kb) * a.dz,
+                                          a.dz);
+        }
       }
-      if (STAGED) {
+      if (STAGED && !ROWS_GLOBAL) {
         // the operand rows are read: the converters may rebuild the buffer
         __syncwarp();
         if (lane == 0) mbar_arrive(&B.aempty[i]);
       }
-      const int64_t row = (blockIdx.x + int64_t(t) * gridDim.x) * kTM + r;
       if (row < a.n) {
         if (fused) {
           float av = 0.f, bv = INFINITY, sv = 0.f;
@@ -1278,7 +1297,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_score_tc_wide(TcK a, const __
         // from global memory (the chunked A buffers hold only part of it)
         const float4 co = clsm[kb];
         const float wn = co.y > 0.f ? co.z / co.y : 0.f;  // W_k / n_k
-        dk = wn + tc_row_dist_global(a.xg + row * a.ldx, a.d, inv, gsm, a.zf + int64_t(kb0 + kb) * a.dz);
+        dk = wn + tc_row_dist_global<false>(a.xg + row * a.ldx, a.d, inv, gsm, a.zf + int64_t(kb0 + kb) * a.dz);
       }
       if (row < a.n) {
         if (fused) {
@@ -1474,19 +1493,22 @@ void tc_plan_enumerate(int32_t dtype, int32_t k, int32_t d, F&& visit) {
           // its A-operand reads below ~64), plus a fixed share for conversion,
           // row terms and the per-block results
           double cost = double(nblk) * (std::max(kp, 64) + dp);
-          // an A buffer is held from conversion until the epilogue has read
-          // its rows back: one buffer serialises the roles, two overlap them
-          // partly
-          if (nab < 2) cost *= 1.8;
-          if (staged && nab == 2) cost *= 1.08;
-          if (staged && nxs < 2) cost *= 1.05;
-          if (staged && nxs == 2) cost *= 1.02;
+          if (staged && nxs == 2) cost *= 0.99;  // a second raw stage hides a little TMA latency
           if (!staged && nab == 2) cost *= 1.02;
           if (!zst) cost *= 1.12;  // own-centroid rows from L1/L2 instead of shared memory
-          // equal modelled cost: the model keeps rank = 0 (enumerated first),
-          // and a candidate list pairs the two for each layout
-          visit(TcPlan{kp, nblk, nxs, nab, zst, smem, 0}, cost);
-          visit(TcPlan{kp, nblk, nxs, nab, zst, smem, 1}, cost);
+          for (int rank = 0; rank < 2; ++rank) {
+            // the narrow kernels hold an A buffer until the epilogue has read
+            // its rows back, except FP32 with rank 0 (those rows come from
+            // global memory): then one buffer serialises conversion, MMA and
+            // epilogue and two overlap them only partly
+            const bool held = dp <= 128 && !(mode == kModeF32 && rank == 0);
+            double c = cost;
+            if (nab < 2) c *= held ? 1.8 : 1.4;
+            if (staged && nab == 2) c *= held ? 1.08 : 1.06;  // measured: a third buffer pays ~5 %
+            // rank 0 first: at equal cost the model keeps it, and a candidate
+            // list pairs the two rank passes of a layout where they tie
+            visit(TcPlan{kp, nblk, nxs, nab, zst, smem, rank}, c);
+          }
         }
       }
     }
