@@ -64,9 +64,16 @@ namespace sil {
 namespace {
 
 constexpr int kTM = 128;                   // points per tile = TMEM lanes
-constexpr int kTcThreads = 448;            // 14 warps
+constexpr int kTcThreads = 448;            // 14 warps (one epilogue warpgroup)
 constexpr int kConvWarps = 8;              // warps 2..9
-constexpr int kEpiWarp0 = 2 + kConvWarps;  // warps 10..13
+constexpr int kEpiWarp0 = 2 + kConvWarps;  // warps 10..13 (and 14..17 with two epilogue warpgroups)
+
+// Epilogue warpgroups of the narrow kernel: two for rows of up to 64 columns
+// (each takes every other tile, i.e. one of the two TMEM accumulators, so
+// that the latency-bound epilogue of two tiles overlaps), one otherwise (the
+// converters of 128-column rows need the registers).
+__host__ __device__ constexpr int tc_epi_groups(int dp) { return dp <= 64 ? 2 : 1; }
+__host__ __device__ constexpr int tc_threads(int dp) { return kTcThreads + 128 * (tc_epi_groups(dp) - 1); }
 constexpr int kAtomBytes = kTM * 128;      // one 128-row x 128-byte swizzle column
 constexpr int kMaxBlockN = 256;            // clusters per block (MMA N)
 constexpr int kSmemMax = 227 * 1024;
@@ -285,20 +292,20 @@ __device__ __forceinline__ float tc_cond_radius(const float4* cl, int k, const f
 }
 
 // Minimum over the columns k != own of v_k = cb_k + sc acc_k of this warp's
-// 32 TMEM lanes (acc at tbase), with its index in kb when ARG; 64 columns per
-// round trip to TMEM (four loads in flight, one wait).  Warp-collective.
-template <bool ARG>
+// 32 TMEM lanes (acc at tbase), with its index in kb when ARG; 16 NLD columns
+// per round trip to TMEM (NLD loads in flight, one wait).  Warp-collective.
+template <bool ARG, int NLD>
 __device__ __forceinline__ float tc_lane_min(uint32_t tbase, int kp, const float* cbs, float sc, int own, int& kb) {
   float best = INFINITY;
   const float2 sc2 = make_float2(sc, sc);
-  for (int c0 = 0; c0 < kp; c0 += 64) {
-    uint32_t rv[4][16];
+  for (int c0 = 0; c0 < kp; c0 += 16 * NLD) {
+    uint32_t rv[NLD][16];
 #pragma unroll
-    for (int j = 0; j < 4; ++j)
+    for (int j = 0; j < NLD; ++j)
       if (c0 + 16 * j < kp) tmem_ld16_async(tbase + uint32_t(c0 + 16 * j), rv[j]);
     tmem_wait_ld();
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
+    for (int j = 0; j < NLD; ++j) {
       if (c0 + 16 * j >= kp) break;
       reg_fence16(rv[j]);
       const float4* cb4 = reinterpret_cast<const float4*>(cbs + c0 + 16 * j);
@@ -434,7 +441,7 @@ __host__ __device__ inline TcSmem tc_smem(int mode, int dp, int kp, int nxs, int
   // BF16: one slot per A buffer (TMA writes the labels beside the tile);
   // otherwise a ring of its own, so that an A buffer is free once its MMAs are
   o += (staged ? kSideSlots : nab) * s.side_stride;
-  s.cb = o; o += kp * 4 + 16;  // + 4 floats of block-reduction scratch
+  s.cb = o; o += kp * 4 + 32;  // + 8 floats of block-reduction scratch
   o = (o + 15) & ~15;
   s.gsm = o; o += dp * 4;
   s.csm = o; o += mode == kModeFP8 ? dp * 4 : 0;
@@ -489,7 +496,7 @@ __device__ __forceinline__ bool tc_wait(uint64_t* bar, uint32_t parity, volatile
 }
 
 template <int MODE, int DP, bool TRACK>
-__global__ void __launch_bounds__(kTcThreads, 1) k_score_tc(TcK a, const __grid_constant__ TcMaps maps) {
+__global__ void __launch_bounds__(tc_threads(DP), 1) k_score_tc(TcK a, const __grid_constant__ TcMaps maps) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   // 1024-byte alignment for the swizzled tiles, by offsetting the shared array
   // itself so that every access below stays a shared-space access
@@ -867,9 +874,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_score_tc(TcK a, const __grid_
     // ---------------------------------------------- epilogue warps 10..13
     const int q = warp & 3;       // TMEM lane quarter this warp may access
     const int r = q * 32 + lane;  // tile row = TMEM lane
+    constexpr int EG = tc_epi_groups(DP);
+    const int eg = (warp - kEpiWarp0) >> 2;  // this warp's group takes tiles eg, eg + EG, ...
     const float rb = tc_cond_radius(a.cl, a.k, gsm, DP, lane);
     float tsum = 0.f;
-    for (int t = 0; t < my_tiles; ++t) {
+    for (int t = eg; t < my_tiles; t += EG) {
       const int i = t % a.nab, bsel = t & 1, sl = STAGED ? t % kSideSlots : i;
       if (!tc_wait(&B.accfull[bsel], (t >> 1) & 1, abort_flag, a.status)) break;
       if (STAGED) {
@@ -886,7 +895,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_score_tc(TcK a, const __grid_
       const float xn2 = side[r];
       const uint32_t tbase = tmem + uint32_t(bsel * a.acc_cols) + (uint32_t(q * 32) << 16);
       int kb = -1;
-      const float best = tc_lane_min<TRACK>(tbase, a.kp, cbs, sc, own, kb);
+      // two warpgroups keep half the registers each: two loads in flight
+      const float best = tc_lane_min<TRACK, EG == 2 ? 2 : 4>(tbase, a.kp, cbs, sc, own, kb);
       // The GEMM ranks the clusters; for ill-conditioned rows b_i is then the
       // nearest cluster's distance in the difference form, like a_i, from the
       // point's operand row (the A buffer is held until this has been read).
@@ -950,12 +960,16 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_score_tc(TcK a, const __grid_
       if (lane == 0) mbar_arrive(STAGED ? &B.sempty[sl] : &B.aempty[i]);
     }
     if (fused) {
-      // block partial over the 128 epilogue threads
+      // block partial over the epilogue threads
       for (int o = 16; o > 0; o >>= 1) tsum += __shfl_xor_sync(0xffffffffu, tsum, o);
-      float* red = cbs + a.kp;  // 4 floats of scratch right after cb (within the plan's padding)
-      if (lane == 0) red[q] = tsum;
-      asm volatile("bar.sync 1, 128;" ::: "memory");
-      if (warp == kEpiWarp0 && lane == 0) a.partials[blockIdx.x] = double(red[0]) + red[1] + red[2] + red[3];
+      float* red = cbs + a.kp;  // 8 floats of scratch right after cb (within the plan's padding)
+      if (lane == 0) red[warp - kEpiWarp0] = tsum;
+      asm volatile("bar.sync 1, %0;" ::"n"(128 * EG) : "memory");
+      if (warp == kEpiWarp0 && lane == 0) {
+        double p = 0.0;
+        for (int w = 0; w < 4 * EG; ++w) p += double(red[w]);
+        a.partials[blockIdx.x] = p;
+      }
     }
   }
   __syncthreads();
@@ -1281,7 +1295,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_score_tc_wide(TcK a, const __
       const float xn2 = side[r], aown = side[kTM + r], inv = side[2 * kTM + r];
       const uint32_t tbase = tmem + uint32_t(bsel * a.acc_cols) + (uint32_t(q * 32) << 16);
       int kb = -1;
-      const float best = tc_lane_min<TRACK>(tbase, a.kp, cbs, sc, own, kb);
+      const float best = tc_lane_min<TRACK, 4>(tbase, a.kp, cbs, sc, own, kb);
       const bool exact = row_ok && best < INFINITY && tc_ill_conditioned(xn2, best, rb);
       if (!TRACK && __any_sync(0xffffffffu, exact)) kb = tc_lane_find(tbase, a.kp, cbs, sc, own, best, exact);
       tc_fence_before();
@@ -1720,10 +1734,11 @@ cudaError_t launch_score_tc(const ScoreLaunch& s, const double* g, void* pack, v
   const int64_t ntiles = cdiv(s.n, kTM);
   const int per_block = std::max(1, kNumSMs / plan.nblk);
   const dim3 grid(unsigned(std::min<int64_t>(ntiles, per_block)), unsigned(plan.nblk));
+  const int threads = dp == 256 ? kTcThreads : tc_threads(dp);
   auto launch = [&](auto fn) {
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, plan.smem);
     if (e != cudaSuccess) return e;
-    fn<<<grid, kTcThreads, plan.smem, s.stream>>>(k, maps);
+    fn<<<grid, threads, plan.smem, s.stream>>>(k, maps);
     return cudaGetLastError();
   };
   cudaError_t e;
