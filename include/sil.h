@@ -219,7 +219,9 @@ int sil_tensor_plan(int32_t dtype, int32_t d, int32_t k, int32_t* block_k, int32
  * same results; which is faster depends on how many points that is.
  * sil_tensor_plan_set makes one plan the choice for (dtype, d, k) in this
  * process (block_k = 0 returns the shape to the cost model); it returns
- * SIL_EINVAL for values out of range and SIL_EUNSUPPORTED when the plan does
+ * SIL_EINVAL for values out of range (including an odd number of A-operand
+ * buffers or raw X stages for rows of up to 64 columns, whose kernels split the
+ * tiles between two converter warpgroups) and SIL_EUNSUPPORTED when the plan does
  * not fit in shared memory.  Set plans before sizing the workspace: the
  * number of cluster blocks changes sil_workspace_size.  Host-only; safe to
  * call from several threads.

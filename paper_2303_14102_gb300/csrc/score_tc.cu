@@ -66,20 +66,31 @@ namespace {
 constexpr int kTM = 128;                   // points per tile = TMEM lanes
 constexpr int kTcThreads = 448;            // 14 warps (one epilogue warpgroup)
 constexpr int kConvWarps = 8;              // warps 2..9
-constexpr int kEpiWarp0 = 2 + kConvWarps;  // warps 10..13 (and 14..17 with two epilogue warpgroups)
+constexpr int kEpiWarp0 = 2 + kConvWarps;  // warps 10..13 of the one-group layout
 
-// Epilogue warpgroups of the narrow kernel: two for rows of up to 64 columns
-// (each takes every other tile, i.e. one of the two TMEM accumulators, so
-// that the latency-bound epilogue of two tiles overlaps), one otherwise (the
-// converters of 128-column rows need the registers).
+enum TcMode { kModeF32 = 0, kModeBF16 = 1, kModeFP8 = 2 };
+
+// Warpgroups of the narrow kernel.  For rows of up to 64 columns two epilogue
+// groups of 4 warps, each taking every other tile (and owning one of the two
+// TMEM accumulators), so that the latency-bound epilogue of two tiles
+// overlaps; one otherwise (the converters of 128-column rows need the
+// registers).  FP32 rows of up to 64 columns whose cluster block is at most
+// twice as wide as the row -- conversion (the hi/lo split) outweighs the
+// epilogue there -- also get two converter groups of 8 warps that alternate
+// tiles (26 warps, 72 registers each); with wider blocks the epilogue
+// needs the registers more.
 __host__ __device__ constexpr int tc_epi_groups(int dp) { return dp <= 64 ? 2 : 1; }
-__host__ __device__ constexpr int tc_threads(int dp) { return kTcThreads + 128 * (tc_epi_groups(dp) - 1); }
+__host__ __device__ constexpr int tc_conv_groups(int mode, int dp, int kp) {
+  return mode == kModeF32 && dp <= 64 && kp <= 2 * dp ? 2 : 1;
+}
+__host__ __device__ constexpr int tc_threads(int dp, int cg) {
+  return 32 * (2 + kConvWarps * cg + 4 * tc_epi_groups(dp));
+}
 constexpr int kAtomBytes = kTM * 128;      // one 128-row x 128-byte swizzle column
 constexpr int kMaxBlockN = 256;            // clusters per block (MMA N)
 constexpr int kSmemMax = 227 * 1024;
 constexpr int kSideSlots = 4;  // row-term ring of the modes whose converters write it
 
-enum TcMode { kModeF32 = 0, kModeBF16 = 1, kModeFP8 = 2 };
 
 // Per-row code handed from the converters to the epilogue: the own cluster's
 // index within this CTA's block (>= 0), -2 - index for a singleton own
@@ -495,8 +506,8 @@ __device__ __forceinline__ bool tc_wait(uint64_t* bar, uint32_t parity, volatile
   return true;
 }
 
-template <int MODE, int DP, bool TRACK>
-__global__ void __launch_bounds__(tc_threads(DP), 1) k_score_tc(TcK a, const __grid_constant__ TcMaps maps) {
+template <int MODE, int DP, bool TRACK, int CG>
+__global__ void __launch_bounds__(tc_threads(DP, CG), 1) k_score_tc(TcK a, const __grid_constant__ TcMaps maps) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   // 1024-byte alignment for the swizzled tiles, by offsetting the shared array
   // itself so that every access below stays a shared-space access
@@ -505,6 +516,14 @@ __global__ void __launch_bounds__(tc_threads(DP), 1) k_score_tc(TcK a, const __g
   constexpr int natom = NARROW ? 1 : DP / 64;
   constexpr int ROWB = NARROW ? 64 : 128;     // bytes of one operand row in an atom
   constexpr bool STAGED = MODE != kModeBF16;  // converters build the A operand
+  constexpr int EG = tc_epi_groups(DP);
+  constexpr int EPI0 = 2 + kConvWarps * CG;  // first epilogue warp
+  // the plans never pass odd rings to two converter groups (see
+  // tc_rings_ok); refuse them here too rather than alias mbarrier phases
+  if (CG == 2 && ((a.nab & 1) || (STAGED && (a.nxs & 1)))) {
+    if (threadIdx.x == 0) set_status(a.status, SIL_EUNSUPPORTED);
+    return;
+  }
   // where the epilogue reads an ill-conditioned row back: FP32 plans without
   // the argmin pass (few such rows) from global memory, so that an A buffer is
   // free once its MMAs are; the others from the A buffer, held until then
@@ -677,13 +696,15 @@ __global__ void __launch_bounds__(tc_threads(DP), 1) k_score_tc(TcK a, const __g
         mbar_wait(&B.accfull[u & 1], uint32_t((u >> 1) & 1));
       }
     }
-  } else if (warp < kEpiWarp0) {
-    // ------------------------------------------------ converter warps 2..9
-    // lanes 0-15 and 16-31 of a warp hold the two halves of the same 16 rows
+  } else if (warp < EPI0) {
+    // ------------------------------------------------ converter warps 2..EPI0-1
+    // lanes 0-15 and 16-31 of a warp hold the two halves of the same 16 rows;
+    // group cg takes tiles cg, cg + CG, ...
     constexpr int HP = DP / 2;  // columns per half
     const int h = lane >> 4;
-    const int r = (warp - 2) * 16 + (lane & 15);  // tile row of this thread
-    for (int t = 0; t < my_tiles; ++t) {
+    const int cg = (warp - 2) / kConvWarps;
+    const int r = ((warp - 2) % kConvWarps) * 16 + (lane & 15);  // tile row of this thread
+    for (int t = cg; t < my_tiles; t += CG) {
       const int i = t % a.nab;
       const int64_t row = (blockIdx.x + int64_t(t) * gridDim.x) * kTM + r;
       unsigned char* ab = base + L.abuf + i * L.abuf_stride;
@@ -874,8 +895,7 @@ __global__ void __launch_bounds__(tc_threads(DP), 1) k_score_tc(TcK a, const __g
     // ---------------------------------------------- epilogue warps 10..13
     const int q = warp & 3;       // TMEM lane quarter this warp may access
     const int r = q * 32 + lane;  // tile row = TMEM lane
-    constexpr int EG = tc_epi_groups(DP);
-    const int eg = (warp - kEpiWarp0) >> 2;  // this warp's group takes tiles eg, eg + EG, ...
+    const int eg = (warp - EPI0) >> 2;  // this warp's group takes tiles eg, eg + EG, ...
     const float rb = tc_cond_radius(a.cl, a.k, gsm, DP, lane);
     float tsum = 0.f;
     for (int t = eg; t < my_tiles; t += EG) {
@@ -963,9 +983,9 @@ __global__ void __launch_bounds__(tc_threads(DP), 1) k_score_tc(TcK a, const __g
       // block partial over the epilogue threads
       for (int o = 16; o > 0; o >>= 1) tsum += __shfl_xor_sync(0xffffffffu, tsum, o);
       float* red = cbs + a.kp;  // 8 floats of scratch right after cb (within the plan's padding)
-      if (lane == 0) red[warp - kEpiWarp0] = tsum;
+      if (lane == 0) red[warp - EPI0] = tsum;
       asm volatile("bar.sync 1, %0;" ::"n"(128 * EG) : "memory");
-      if (warp == kEpiWarp0 && lane == 0) {
+      if (warp == EPI0 && lane == 0) {
         double p = 0.0;
         for (int w = 0; w < 4 * EG; ++w) p += double(red[w]);
         a.partials[blockIdx.x] = p;
@@ -1487,6 +1507,17 @@ struct PlanOverride {
 std::mutex g_plan_mu;
 std::vector<PlanOverride> g_plan_over;
 
+// With two converter groups (tiles alternate between them) every slot of a
+// ring must always serve the same group, so that a group never waits on the
+// next use of a slot whose previous use, by the other group, has not
+// completed (an mbarrier parity wait cannot tell the two apart): the A
+// buffers, and the raw stages where the converters read them, come in even
+// numbers.  (The row-term ring has 4 slots and TMEM 2 accumulators.)
+bool tc_rings_ok(int mode, int dp, int kp, int nab, int nxs) {
+  if (dp > 128 || tc_conv_groups(mode, dp, kp) == 1) return true;
+  return nab % 2 == 0 && (mode == kModeBF16 || nxs % 2 == 0);
+}
+
 // Every plan whose shared memory fits, with its modelled cost.
 template <class F>
 void tc_plan_enumerate(int32_t dtype, int32_t k, int32_t d, F&& visit) {
@@ -1499,6 +1530,7 @@ void tc_plan_enumerate(int32_t dtype, int32_t k, int32_t d, F&& visit) {
     const int nblk = int(cdiv(k, kp));
     for (int nab = 1; nab <= 4; ++nab) {
       for (int nxs = 1; nxs <= (staged ? 3 : 1); ++nxs) {
+        if (!tc_rings_ok(mode, dp, kp, nab, nxs)) continue;
         for (int zs = 0; zs < 2; ++zs) {
           const int zst = zs ? dz + 4 : 0;  // padded rows: fewer bank conflicts
           const int smem = tc_smem(mode, dp, kp, nxs, nab, zst).total;
@@ -1507,9 +1539,18 @@ void tc_plan_enumerate(int32_t dtype, int32_t k, int32_t d, F&& visit) {
           // its A-operand reads below ~64), plus a fixed share for conversion,
           // row terms and the per-block results
           double cost = double(nblk) * (std::max(kp, 64) + dp);
-          if (staged && nxs == 2) cost *= 0.99;  // a second raw stage hides a little TMA latency
-          if (!staged && nab == 2) cost *= 1.02;
           if (!zst) cost *= 1.12;  // own-centroid rows from L1/L2 instead of shared memory
+          const bool two = dp <= 128 && tc_conv_groups(mode, dp, kp) == 2;
+          if (two) {
+            // two converter groups alternate tiles: each wants a raw stage and
+            // an A buffer of its own
+            if (staged && nxs < 2) cost *= 1.3;
+            if (nab < 2) cost *= 1.8;
+          } else {
+            if (staged && nxs == 2) cost *= 0.99;  // a second raw stage hides a little TMA latency
+            if (!staged && nab == 2) cost *= 1.05;  // BF16: the A ring is the TMA prefetch depth
+            if (!staged && nab == 3) cost *= 1.03;
+          }
           for (int rank = 0; rank < 2; ++rank) {
             // the narrow kernels hold an A buffer until the epilogue has read
             // its rows back, except FP32 with rank 0 (those rows come from
@@ -1517,8 +1558,8 @@ void tc_plan_enumerate(int32_t dtype, int32_t k, int32_t d, F&& visit) {
             // epilogue and two overlap them only partly
             const bool held = dp <= 128 && !(mode == kModeF32 && rank == 0);
             double c = cost;
-            if (nab < 2) c *= held ? 1.8 : 1.4;
-            if (staged && nab == 2) c *= held ? 1.08 : 1.06;  // measured: a third buffer pays ~5 %
+            if (!two && nab < 2) c *= held ? 1.8 : 1.4;
+            if (!two && staged && nab == 2) c *= held ? 1.08 : 1.06;  // measured: a third buffer pays ~5 %
             // rank 0 first: at equal cost the model keeps it, and a candidate
             // list pairs the two rank passes of a layout where they tie
             visit(TcPlan{kp, nblk, nxs, nab, zst, smem, rank}, c);
@@ -1539,7 +1580,7 @@ bool tc_plan(int32_t dtype, int32_t k, int32_t d, TcPlan* out) {
       if (o.dtype != dtype || o.d != d || o.k != k) continue;
       const int zst = o.stage_z ? dz + 4 : 0;
       const int smem = tc_smem(mode, dp, o.kp, o.nxs, o.nab, zst).total;
-      if (smem <= kSmemMax) {
+      if (smem <= kSmemMax && tc_rings_ok(mode, dp, o.kp, o.nab, o.nxs)) {
         *out = TcPlan{o.kp, int(cdiv(k, o.kp)), o.nxs, o.nab, zst, smem, o.rank};
         return true;
       }
@@ -1620,6 +1661,7 @@ int tc_plan_set(int32_t dtype, int32_t d, int32_t k, int32_t kp, int32_t nab, in
     return SIL_EINVAL;
   const int mode = mode_of(dtype);
   const int zst = stage_z ? int(round_up(d, 4)) + 4 : 0;
+  if (!tc_rings_ok(mode, tc_dp(d), kp, nab, mode == kModeBF16 ? 1 : nxs)) return SIL_EINVAL;
   if (tc_smem(mode, tc_dp(d), kp, mode == kModeBF16 ? 1 : nxs, nab, zst).total > kSmemMax)
     return SIL_EUNSUPPORTED;
   g_plan_over.push_back(PlanOverride{dtype, d, k, kp, nab, mode == kModeBF16 ? 1 : nxs, stage_z ? 1 : 0, rank});
@@ -1734,7 +1776,8 @@ cudaError_t launch_score_tc(const ScoreLaunch& s, const double* g, void* pack, v
   const int64_t ntiles = cdiv(s.n, kTM);
   const int per_block = std::max(1, kNumSMs / plan.nblk);
   const dim3 grid(unsigned(std::min<int64_t>(ntiles, per_block)), unsigned(plan.nblk));
-  const int threads = dp == 256 ? kTcThreads : tc_threads(dp);
+  const int cg = dp == 256 ? 1 : tc_conv_groups(mode, dp, kp);
+  const int threads = dp == 256 ? kTcThreads : tc_threads(dp, cg);
   auto launch = [&](auto fn) {
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, plan.smem);
     if (e != cudaSuccess) return e;
@@ -1743,15 +1786,22 @@ cudaError_t launch_score_tc(const ScoreLaunch& s, const double* g, void* pack, v
   };
   cudaError_t e;
   if (mode == kModeF32) {
-    if (dp == 256) e = track ? launch(k_score_tc_wide<true>) : launch(k_score_tc_wide<false>);
-    else if (dp == 32) e = track ? launch(k_score_tc<kModeF32, 32, true>) : launch(k_score_tc<kModeF32, 32, false>);
-    else if (dp == 64) e = track ? launch(k_score_tc<kModeF32, 64, true>) : launch(k_score_tc<kModeF32, 64, false>);
-    else e = track ? launch(k_score_tc<kModeF32, 128, true>) : launch(k_score_tc<kModeF32, 128, false>);
+    if (dp == 256) {
+      e = track ? launch(k_score_tc_wide<true>) : launch(k_score_tc_wide<false>);
+    } else if (dp == 32) {
+      if (cg == 2) e = track ? launch(k_score_tc<kModeF32, 32, true, 2>) : launch(k_score_tc<kModeF32, 32, false, 2>);
+      else e = track ? launch(k_score_tc<kModeF32, 32, true, 1>) : launch(k_score_tc<kModeF32, 32, false, 1>);
+    } else if (dp == 64) {
+      if (cg == 2) e = track ? launch(k_score_tc<kModeF32, 64, true, 2>) : launch(k_score_tc<kModeF32, 64, false, 2>);
+      else e = track ? launch(k_score_tc<kModeF32, 64, true, 1>) : launch(k_score_tc<kModeF32, 64, false, 1>);
+    } else {
+      e = track ? launch(k_score_tc<kModeF32, 128, true, 1>) : launch(k_score_tc<kModeF32, 128, false, 1>);
+    }
   } else if (mode == kModeBF16) {
-    if (dp == 64) e = track ? launch(k_score_tc<kModeBF16, 64, true>) : launch(k_score_tc<kModeBF16, 64, false>);
-    else e = track ? launch(k_score_tc<kModeBF16, 128, true>) : launch(k_score_tc<kModeBF16, 128, false>);
+    if (dp == 64) e = track ? launch(k_score_tc<kModeBF16, 64, true, 1>) : launch(k_score_tc<kModeBF16, 64, false, 1>);
+    else e = track ? launch(k_score_tc<kModeBF16, 128, true, 1>) : launch(k_score_tc<kModeBF16, 128, false, 1>);
   } else {
-    e = track ? launch(k_score_tc<kModeFP8, 128, true>) : launch(k_score_tc<kModeFP8, 128, false>);
+    e = track ? launch(k_score_tc<kModeFP8, 128, true, 1>) : launch(k_score_tc<kModeFP8, 128, false, 1>);
   }
   if (e != cudaSuccess) return e;
   if (plan.nblk == 1) {

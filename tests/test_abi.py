@@ -149,6 +149,11 @@ def test_tensor_plan_candidates_and_override():
 
 def test_tensor_plan_set_rejects_bad_plans(lib):
     assert lib.sil_tensor_plan_set(0, 64, 100, 40, 2, 2, 0, 0) == sil.SIL_EINVAL      # not a multiple of 16
-    assert lib.sil_tensor_plan_set(0, 64, 100, 256, 4, 3, 1, 0) == sil.SIL_EUNSUPPORTED  # too much shared memory
+    assert lib.sil_tensor_plan_set(0, 64, 100, 256, 4, 2, 1, 0) == sil.SIL_EUNSUPPORTED  # too much shared memory
+    # two converter groups alternate tiles: odd rings would hand one slot to both
+    assert lib.sil_tensor_plan_set(0, 64, 100, 112, 3, 2, 1, 0) == sil.SIL_EINVAL
+    assert lib.sil_tensor_plan_set(0, 64, 100, 112, 2, 1, 1, 0) == sil.SIL_EINVAL
+    assert lib.sil_tensor_plan_set(0, 128, 100, 64, 1, 1, 0, 0) == sil.SIL_OK     # one group: any depth
+    assert lib.sil_tensor_plan_set(0, 128, 100, 0, 0, 0, 0, 0) == sil.SIL_OK      # back to the model
     assert lib.sil_tensor_plan_set(0, 300, 100, 64, 2, 2, 0, 0) == sil.SIL_EINVAL     # d > 256
     assert lib.sil_tensor_plan_set(0, 64, 100, 64, 2, 2, 0, 2) == sil.SIL_EINVAL      # rank pass is 0 or 1
