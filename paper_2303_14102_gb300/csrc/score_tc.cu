@@ -30,23 +30,26 @@
 // point range -- the G CTAs of a range read the same tiles at about the same
 // time, so the repeats are served by L2 -- and writes, per point, the
 // distance to the nearest cluster of its block (and its index when the
-// backward record is wanted).  The
-// CTA whose block holds the point's own cluster also writes a_i and ||x'||^2.
-// k_tc_combine then takes the minimum over the blocks and finishes s_i.
+// backward record is wanted).  The CTA whose block holds the point's own
+// cluster also writes a_i.  k_tc_combine then takes the minimum over the
+// blocks and finishes s_i.
 //
-// One persistent CTA per SM, 14 warps:
+// One persistent CTA per SM, warp-specialised:
 //   warp 0       TMA producer (X tiles, labels; the split centroids once)
 //   warp 1       TMEM allocation + single-thread tcgen05.mma issue
-//   warps 2-9    converters: two threads per tile row (one per half) --
-//                FP32 -> BF16 hi/lo or FP8 -> BF16 in the 128-byte-swizzled
-//                K-major layout, ||x'||^2 and the exact a_i, with the block's
-//                centroids, the global centre and the cluster constants staged
-//                in shared memory
-//   warps 10-13  epilogue: tcgen05.ld, masked running minimum, s_i, sums
-// Ring buffers: raw X stages (MODE 0 and 2), A buffers, and two TMEM
-// accumulators, each guarded by mbarriers.  Every wait is bounded
-// (SIL_ETIMEOUT); on a timeout all roles stop, in-flight copies and MMAs are
-// waited for (bounded) and TMEM is freed before the CTA exits.
+//   converters   one or two groups of 8 warps, two threads per tile row (one
+//                per half) -- FP32 -> BF16 hi/lo or FP8 -> BF16 in the
+//                swizzled K-major layout, ||x'||^2 and the exact a_i, with the
+//                block's centroids, the global centre and the cluster
+//                constants staged in shared memory
+//   epilogue     one or two groups of 4 warps: tcgen05.ld, masked running
+//                minimum, b_i in the difference form where needed, s_i, sums
+// With two groups of a role, group g takes tiles g, g + 2, ... (see
+// tc_epi_groups / tc_conv_groups).  Ring buffers: raw X stages (MODE 0 and
+// 2), A buffers, a ring of row-term slots and two TMEM accumulators, each
+// guarded by mbarriers.  Every wait is bounded (SIL_ETIMEOUT); on a timeout
+// all roles stop, in-flight copies and MMAs are waited for (bounded) and TMEM
+// is freed before the CTA exits.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_fp8.h>
@@ -65,7 +68,7 @@ namespace {
 
 constexpr int kTM = 128;                   // points per tile = TMEM lanes
 constexpr int kTcThreads = 448;            // 14 warps (one epilogue warpgroup)
-constexpr int kConvWarps = 8;              // warps 2..9
+constexpr int kConvWarps = 8;              // warps per converter group
 constexpr int kEpiWarp0 = 2 + kConvWarps;  // warps 10..13 of the one-group layout
 
 enum TcMode { kModeF32 = 0, kModeBF16 = 1, kModeFP8 = 2 };
@@ -892,7 +895,7 @@ __global__ void __launch_bounds__(tc_threads(DP, CG), 1) k_score_tc(TcK a, const
       if (lane == 0) mbar_arrive(STAGED ? &B.sfull[sl] : &B.pfull[i]);
     }
   } else {
-    // ---------------------------------------------- epilogue warps 10..13
+    // ---------------------------------------------- epilogue warps EPI0..
     const int q = warp & 3;       // TMEM lane quarter this warp may access
     const int r = q * 32 + lane;  // tile row = TMEM lane
     const int eg = (warp - EPI0) >> 2;  // this warp's group takes tiles eg, eg + EG, ...
