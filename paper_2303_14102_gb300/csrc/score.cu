@@ -32,22 +32,25 @@ namespace {
 __global__ void k_fin_global(const unsigned long long* count, const double* s1, int32_t k,
                              int32_t d, int32_t dz, double* g, float* gf, uint32_t* status) {
   __shared__ double part[32][33];
-  __shared__ unsigned long long ntot;
-  __shared__ int nnon;
+  __shared__ unsigned long long wn[32];
+  __shared__ int wnon[32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-  if (threadIdx.x == 0) {
-    ntot = 0;
-    nnon = 0;
-  }
-  __syncthreads();
+  // total count and non-empty clusters: warp sums, then one thread (no
+  // 64-bit shared atomics on one word from every thread)
   unsigned long long my = 0;
   int mynon = 0;
   for (int kk = threadIdx.x; kk < k; kk += blockDim.x) {
     my += count[kk];
     mynon += count[kk] > 0;
   }
-  atomicAdd(&ntot, my);
-  atomicAdd(&nnon, mynon);
+  for (int o = 16; o > 0; o >>= 1) {
+    my += __shfl_xor_sync(0xffffffffu, my, o);
+    mynon += __shfl_xor_sync(0xffffffffu, mynon, o);
+  }
+  if (lane == 0) {
+    wn[warp] = my;
+    wnon[warp] = mynon;
+  }
   const int c = blockIdx.x * 32 + lane;
   // four independent partial sums per lane keep several loads in flight
   double s[4] = {0.0, 0.0, 0.0, 0.0};
@@ -60,6 +63,12 @@ __global__ void k_fin_global(const unsigned long long* count, const double* s1, 
   }
   part[warp][lane] = (s[0] + s[1]) + (s[2] + s[3]);
   __syncthreads();
+  unsigned long long ntot = 0;
+  int nnon = 0;
+  for (int w = 0; w < nwarp; ++w) {
+    ntot += wn[w];
+    nnon += wnon[w];
+  }
   if (warp == 0 && c < dz) {
     double t = 0.0;
     for (int w = 0; w < nwarp; ++w) t += part[w][lane];
@@ -419,10 +428,17 @@ __global__ void __launch_bounds__(64) k_score_simt_wide(ScoreK a) {
 // S = sum of the partials / n in a fixed order; NaN when a flag was raised.
 __global__ void k_reduce_S(const double* partials, int32_t np, int64_t n, const uint32_t* ws_status,
                            uint32_t* user_status, double* S_out) {
-  __shared__ double red[256];
-  double t = 0.0;
-  for (int i = threadIdx.x; i < np; i += blockDim.x) t += partials[i];
-  red[threadIdx.x] = t;
+  __shared__ double red[1024];
+  // four independent sums per thread keep the loads of up to kMaxPartials
+  // partials in flight (a fixed order for a given np: deterministic)
+  double t4[4] = {0.0, 0.0, 0.0, 0.0};
+  const int stride = int(blockDim.x);
+  int i = threadIdx.x;
+  for (; i + 3 * stride < np; i += 4 * stride)
+#pragma unroll
+    for (int u = 0; u < 4; ++u) t4[u] += partials[i + u * stride];
+  for (; i < np; i += stride) t4[0] += partials[i];
+  red[threadIdx.x] = (t4[0] + t4[1]) + (t4[2] + t4[3]);
   __syncthreads();
   for (int s = blockDim.x / 2; s > 0; s >>= 1) {
     if (int(threadIdx.x) < s) red[threadIdx.x] += red[threadIdx.x + s];
@@ -541,7 +557,7 @@ cudaError_t launch_score_simt(ScoreLaunch& s) {
 
 cudaError_t launch_reduce_S(const double* partials, int32_t np, int64_t n, const uint32_t* ws_status,
                             uint32_t* user_status, double* S_out, cudaStream_t stream) {
-  k_reduce_S<<<1, 256, 0, stream>>>(partials, np, n, ws_status, user_status, S_out);
+  k_reduce_S<<<1, 1024, 0, stream>>>(partials, np, n, ws_status, user_status, S_out);
   return cudaGetLastError();
 }
 
