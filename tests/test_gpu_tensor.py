@@ -242,18 +242,22 @@ def _close_clusters(N, D, kmin, kmax, B=2):
     return X, labs, ks
 
 
-@pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16])
-def test_close_clusters_match_the_oracle_without_bias(dtype):
+@pytest.mark.parametrize("metric", METRICS)
+@pytest.mark.parametrize("dtype,D", [(torch.float32, 64), (torch.bfloat16, 64), (torch.float32, 32),
+                                     (torch.float32, 160)])
+def test_close_clusters_match_the_oracle_without_bias(dtype, D, metric):
     # b_i of such rows comes from the difference form, so the error of S is
-    # not the tensor cores' round-towards-zero bias times the cancellation
-    X, labs, ks = _close_clusters(100_000, 64, 250, 450)
+    # not the tensor cores' round-towards-zero bias times the cancellation.
+    # D = 160 runs the chunked kernel, which reads such rows back from
+    # global memory; D = 32 the 64-byte-swizzled one.
+    X, labs, ks = _close_clusters(100_000 if D <= 64 else 40_000, D, 250, 450)
     Xs = X.to(dtype)
     for b, k in enumerate(ks):
         lab = labs[b].contiguous()
-        agg = sil.aggregate(Xs, lab, k)
-        r = sil.score(Xs, lab, k, agg, want_s=True, save=True, path="tensor")
+        agg = sil.aggregate(Xs, lab, k, metric)
+        r = sil.score(Xs, lab, k, agg, metric, want_s=True, save=True, path="tensor")
         torch.cuda.synchronize()
-        ref = oracle.linear(dequant(Xs), lab.cpu().numpy(), k)
+        ref = oracle.linear(dequant(Xs), lab.cpu().numpy(), k, metric)
         assert abs(float(r.S) - ref["S"]) <= TOL_S, (k, float(r.S) - ref["S"])
         _, bt, _ = sil.unpack_saved(r.saved, X.shape[0])
         rel = (bt.cpu().double().numpy() - ref["b"]) / ref["b"]
