@@ -419,8 +419,18 @@ def main():
     else:
         kname, kbytes, kms = "k_gather_reduce_tma (pass 1)", bytes_pass1, ms_pass1
     achieved = kbytes / (kms / 1e3) / 1e9
+    # DRAM bytes (read + write) per launch from one ncu capture of the same
+    # kernels on this recipe at N = 2e6 (profiles/k_gather_reduce_tma_k_score_tc_at_scale_n2e6.md),
+    # scaled by rows; valid while those kernels are unchanged
+    traffic = None
+    per_row = {"k_score_tc (pass 2, tcgen05)": (520.155904e6 + 3.573760e6) / 2e6,
+               "k_gather_reduce_tma (pass 1)": (520.275712e6 + 3.623168e6) / 2e6}
+    if (D, K) == (64, 100) and X.dtype == torch.float32 and kname in per_row:
+        traffic = per_row[kname] * N
     roof = {"kernel": kname, "bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
-            "frac": achieved / pk["hbm_gbs"], "traffic": None,
+            "frac": achieved / pk["hbm_gbs"], "traffic": traffic,
+            "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum at N = 2e6, scaled by rows"
+                              if traffic is not None else None,
             "peak_source": f"{pk['source']} copy bandwidth (burst)",
             "algorithmic": f"N*(4D+4) = {kbytes:.3e} B per launch",
             "timing": "CUDA events around the pass on the launching stream, mean over steps "
