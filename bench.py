@@ -261,7 +261,17 @@ def variant_lines(dev, steps, budget_s, pk_sustained):
             step()
             n = max(1, min(steps, 3))
             s = timed(step, n, torch.cuda.current_stream())
-            out[f"fwd_bwd_grad_{metric}"] = {"ms": s / n * 1e3, "N": 1_000_000, "D": 256, "K": 1000}
+            # the backward alone (dS/dX from the saved a_i, b_i, k*_i): two
+            # reads of X and one write of dX are its algorithmic bytes
+            bw = []
+            for _ in range(n):
+                Xg = X.detach().requires_grad_(True)
+                S = silhouette_loss(Xg, lab, w.K, metric)
+                bw.append(timed(S.backward, 1, torch.cuda.current_stream()))
+            tb = statistics.median(bw)
+            nbytes = 3.0 * X.shape[0] * X.shape[1] * 4
+            out[f"fwd_bwd_grad_{metric}"] = {"ms": s / n * 1e3, "bwd_ms": tb * 1e3, "bwd_hbm_gbs": nbytes / tb / 1e9,
+                                             "N": 1_000_000, "D": 256, "K": 1000}
         del X, lab, w
         torch.cuda.empty_cache()
     # batched labelings (N=2e6, D=32, B=256, k ~ U{2..512}): every labeling's
@@ -483,6 +493,16 @@ def main():
             fn()
             s = timed(fn, args.steps, stream)
             variants[name] = {"points_per_s": N * args.steps / s, "ms": s / args.steps * 1e3}
+        # pass 2 on the CUDA cores (FP32 FFMA against Z in shared memory), the
+        # path the tensor-core kernel replaces at this K, for comparison
+        agg_s = sil.aggregate(X, lab, K, status=status)
+        fn = lambda: sil.score(X, lab, K, agg_s, path="simt", status=status)
+        fn()
+        s = timed(fn, args.steps, stream)
+        variants["sqeuclidean_fp32_simt_pass2"] = {
+            "ms": s / args.steps * 1e3, "hbm_gbs": N * (4 * D + 4) / (s / args.steps) / 1e9,
+            "fp32_tflops": 2.0 * N * K * D / (s / args.steps) / 1e12}
+        del agg_s
         Xb = X.to(torch.bfloat16)
         fn = lambda: sil.silhouette(Xb, lab, K, status=status)  # noqa: E731
         rb = fn()
