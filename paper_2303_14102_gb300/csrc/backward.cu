@@ -101,6 +101,7 @@ struct GradK {
   const double* grad_S;
   float* dX;
   int64_t lddx;
+  int32_t vec_out;  // dX rows 16-byte aligned
 };
 
 // One warp per row of dX.
@@ -129,18 +130,34 @@ __global__ void k_bw_grad(GradK a) {
     const float* Wc = a.Wf + int64_t(c) * a.dz;
     if (!a.cosine) {
       const float scale = float(gsd) * 2.f * inv_n;
+      const float an = al * nc, bn = has_k ? be * nk : 0.f;
       for (int l0 = 4 * lane; l0 < a.dz; l0 += 128) {
+        // the per-cluster vectors are dz long (zero padded, 16-byte rows):
+        // one 16-byte load each
         const float4 x = load4<DT>(a.X, m, l0, a.d, a.ldx, a.cs, a.vec);
-        const float xv[4] = {x.x, x.y, x.z, x.w};
+        const float4 g4 = __ldg(reinterpret_cast<const float4*>(a.gf + l0));
+        const float4 r4 = __ldg(reinterpret_cast<const float4*>(rc + l0));
+        const float4 w4 = __ldg(reinterpret_cast<const float4*>(Wc + l0));
+        const float4 c4 = __ldg(reinterpret_cast<const float4*>(zc + l0));
+        const float4 k4 = __ldg(reinterpret_cast<const float4*>(zk + l0));
+        const float xv[4] = {x.x, x.y, x.z, x.w}, gv[4] = {g4.x, g4.y, g4.z, g4.w};
+        const float rv[4] = {r4.x, r4.y, r4.z, r4.w}, wv[4] = {w4.x, w4.y, w4.z, w4.w};
+        const float cv[4] = {c4.x, c4.y, c4.z, c4.w}, kv[4] = {k4.x, k4.y, k4.z, k4.w};
+        float o[4];
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-          const int l = l0 + j;
-          if (l >= a.d) break;
-          const float xc = xv[j] - a.gf[l];
-          float v = Cc * (xv[j] - rc[l]) - Wc[l];
-          v = fmaf(al * nc, xc - zc[l], v);
-          if (has_k) v = fmaf(be * nk, xc - zk[l], v);
-          out[l] = scale * v;
+          const float xc = xv[j] - gv[j];
+          float v = Cc * (xv[j] - rv[j]) - wv[j];
+          v = fmaf(an, xc - cv[j], v);
+          v = fmaf(bn, xc - kv[j], v);
+          o[j] = scale * v;
+        }
+        if (a.vec_out && l0 + 3 < a.d) {
+          *reinterpret_cast<float4*>(out + l0) = make_float4(o[0], o[1], o[2], o[3]);
+        } else {
+#pragma unroll
+          for (int j = 0; j < 4; ++j)
+            if (l0 + j < a.d) out[l0 + j] = o[j];
         }
       }
     } else {
@@ -152,34 +169,50 @@ __global__ void k_bw_grad(GradK a) {
       for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
       const float inv = ss > 0.f ? rsqrtf(ss) : 0.f;
       // g_l = -(1/N)[al nc muh_c + be nk muh_k + W_c + C_c rhat_c],  muh = mu' + g
+      // (16-byte loads of the dz-long, zero-padded per-cluster vectors)
+      const float an = al * nc, bn = has_k ? be * nk : 0.f;
+      auto gvec = [&](int l0, float (&gv)[4]) {
+        const float4 g4 = __ldg(reinterpret_cast<const float4*>(a.gf + l0));
+        const float4 r4 = __ldg(reinterpret_cast<const float4*>(rc + l0));
+        const float4 w4 = __ldg(reinterpret_cast<const float4*>(Wc + l0));
+        const float4 c4 = __ldg(reinterpret_cast<const float4*>(zc + l0));
+        const float4 k4 = __ldg(reinterpret_cast<const float4*>(zk + l0));
+        const float G[4] = {g4.x, g4.y, g4.z, g4.w}, R[4] = {r4.x, r4.y, r4.z, r4.w};
+        const float W[4] = {w4.x, w4.y, w4.z, w4.w}, C[4] = {c4.x, c4.y, c4.z, c4.w};
+        const float Kv[4] = {k4.x, k4.y, k4.z, k4.w};
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          float g = fmaf(Cc, R[j], W[j]);
+          g = fmaf(an, C[j] + G[j], g);
+          g = fmaf(bn, Kv[j] + G[j], g);
+          gv[j] = -g * inv_n;
+        }
+      };
       float proj = 0.f;
       for (int l0 = 4 * lane; l0 < a.dz; l0 += 128) {
         const float4 x = load4<DT>(a.X, m, l0, a.d, a.ldx, a.cs, a.vec);
         const float xv[4] = {x.x, x.y, x.z, x.w};
+        float gv[4];
+        gvec(l0, gv);
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          const int l = l0 + j;
-          if (l >= a.d) break;
-          float g = fmaf(Cc, rc[l], Wc[l]);
-          g = fmaf(al * nc, zc[l] + a.gf[l], g);
-          if (has_k) g = fmaf(be * nk, zk[l] + a.gf[l], g);
-          proj = fmaf(xv[j] * inv, -g * inv_n, proj);
-        }
+        for (int j = 0; j < 4; ++j)
+          if (l0 + j < a.d) proj = fmaf(xv[j] * inv, gv[j], proj);
       }
       for (int o = 16; o > 0; o >>= 1) proj += __shfl_xor_sync(0xffffffffu, proj, o);
       const float sc = float(gsd) * inv;
       for (int l0 = 4 * lane; l0 < a.dz; l0 += 128) {
         const float4 x = load4<DT>(a.X, m, l0, a.d, a.ldx, a.cs, a.vec);
         const float xv[4] = {x.x, x.y, x.z, x.w};
+        float gv[4], o[4];
+        gvec(l0, gv);
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          const int l = l0 + j;
-          if (l >= a.d) break;
-          float g = fmaf(Cc, rc[l], Wc[l]);
-          g = fmaf(al * nc, zc[l] + a.gf[l], g);
-          if (has_k) g = fmaf(be * nk, zk[l] + a.gf[l], g);
-          g = -g * inv_n;
-          out[l] = sc * (g - xv[j] * inv * proj);
+        for (int j = 0; j < 4; ++j) o[j] = sc * (gv[j] - xv[j] * inv * proj);
+        if (a.vec_out && l0 + 3 < a.d) {
+          *reinterpret_cast<float4*>(out + l0) = make_float4(o[0], o[1], o[2], o[3]);
+        } else {
+#pragma unroll
+          for (int j = 0; j < 4; ++j)
+            if (l0 + j < a.d) out[l0 + j] = o[j];
         }
       }
     }
@@ -232,6 +265,7 @@ cudaError_t launch_backward_grad(const BackLaunch& b, const float* Wf, const flo
   g.grad_S = b.grad_S;
   g.dX = b.dX;
   g.lddx = b.lddx;
+  g.vec_out = (reinterpret_cast<uintptr_t>(b.dX) % 16 == 0) && (b.lddx % 4 == 0);
   const unsigned grid = unsigned(std::min<int64_t>(cdiv(b.n, 8), int64_t(kNumSMs) * 16));
   switch (b.dtype) {
     case SIL_F32: k_bw_grad<SIL_F32><<<grid, 256, 0, b.stream>>>(g); break;
