@@ -132,6 +132,12 @@ int sil_aggregate(const void* X, int32_t dtype, int64_t n, int32_t d, int64_t ld
  * sil_saved_size(n) bytes, nullable) receives a_i, b_i and the argmin of b_i
  * (lowest index on ties) for sil_score_backward.  N x K distances are never
  * stored.  path selects the pass-2 kernel (SIL_PATH_AUTO recommended).
+ * Accuracy (FP32 arithmetic, FP64 aggregates and S): the tensor-core path
+ * ranks the clusters by the expanded distance ||x'||^2 + bias_k - 2 x'.mu'_k;
+ * for points where that form is ill-conditioned (the bound
+ * (||x|| + ||mu'||)^2 / d above 6) b_i is recomputed from the nearest
+ * cluster in the difference form ||x' - mu'_k||^2 + W_k / n_k, so that the
+ * rounding of the tensor-core sums does not bias S.
  */
 int sil_score(const void* X, int32_t dtype, int64_t n, int32_t d, int64_t ldx,
               const float* col_scale, const int32_t* labels, int32_t k, int32_t dist,
