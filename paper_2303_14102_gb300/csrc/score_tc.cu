@@ -922,7 +922,9 @@ __global__ void __launch_bounds__(tc_threads(DP, CG), 1) k_score_tc(TcK a, const
       const float best = tc_lane_min<TRACK, EG == 2 ? 2 : 4>(tbase, a.kp, cbs, sc, own, kb);
       // The GEMM ranks the clusters; for ill-conditioned rows b_i is then the
       // nearest cluster's distance in the difference form, like a_i, from the
-      // point's operand row (the A buffer is held until this has been read).
+      // point's operand row: its A buffer (held until this has been read), or,
+      // for FP32 plans without the argmin pass, the row read back from global
+      // memory and rounded to the same hi + lo bits.
       const bool exact = row_ok && best < INFINITY && tc_ill_conditioned(xn2, best, rb);
       if (!TRACK && __any_sync(0xffffffffu, exact)) kb = tc_lane_find(tbase, a.kp, cbs, sc, own, best, exact);
       tc_fence_before();
