@@ -448,8 +448,7 @@ def main():
     # kernels on this recipe at N = 2e6 (profiles/k_gather_reduce_tma_k_score_tc_at_scale_n2e6.md),
     # scaled by rows; valid while those kernels are unchanged
     traffic = None
-    per_row = {"k_score_tc (pass 2, tcgen05)": (520.155904e6 + 3.573760e6) / 2e6,
-               "k_gather_reduce_tma (pass 1)": (520.275712e6 + 3.623168e6) / 2e6}
+    per_row = {"k_score_tc (pass 2, tcgen05)": (520.155904e6 + 3.573760e6) / 2e6}
     if (D, K) == (64, 100) and X.dtype == torch.float32 and kname in per_row:
         traffic = per_row[kname] * N
     roof = {"kernel": kname, "bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
