@@ -34,7 +34,9 @@ def rel_err(g, ref):
 
 
 @pytest.mark.parametrize("metric", METRICS)
-@pytest.mark.parametrize("N,D,K", [(2000, 6, 5), (3001, 33, 9), (1500, 130, 6), (2500, 40, 300)])
+# D = 256 fills both 128-column segments a lane holds; D = 300 takes the re-read path
+@pytest.mark.parametrize("N,D,K", [(2000, 6, 5), (3001, 33, 9), (1500, 130, 6), (2500, 40, 300), (1200, 256, 7),
+                                   (800, 300, 5)])
 def test_grad_against_oracle(metric, N, D, K):
     X, lab = case(200 + N + D, N, D, K, metric, empty=False, singleton=True)
     g = gpu_grad(X, lab, K, metric)
