@@ -134,10 +134,11 @@ int sil_aggregate(const void* X, int32_t dtype, int64_t n, int32_t d, int64_t ld
  * stored.  path selects the pass-2 kernel (SIL_PATH_AUTO recommended).
  * Accuracy (FP32 arithmetic, FP64 aggregates and S): the tensor-core path
  * ranks the clusters by the expanded distance ||x'||^2 + bias_k - 2 x'.mu'_k;
- * for points where that form is ill-conditioned (the bound
- * (||x|| + ||mu'||)^2 / d above 6) b_i is recomputed from the nearest
- * cluster in the difference form ||x' - mu'_k||^2 + W_k / n_k, so that the
- * rounding of the tensor-core sums does not bias S.
+ * for points where that form is ill-conditioned ((||x'|| + a bound on
+ * ||mu'_k||)^2 above 6 times the point's smallest expanded distance) b_i is
+ * recomputed from the nearest cluster in the difference form
+ * ||x' - mu'_k||^2 + W_k / n_k, so that the rounding of the tensor-core sums
+ * does not bias S.
  */
 int sil_score(const void* X, int32_t dtype, int64_t n, int32_t d, int64_t ldx,
               const float* col_scale, const int32_t* labels, int32_t k, int32_t dist,
@@ -208,7 +209,9 @@ int sil_score_noalloc(const void* X, int32_t dtype, int64_t n, int32_t d, int64_
  * partition of them).  Host-only arithmetic: no device is touched and the
  * answer does not say whether the current device can run the path.  Returns
  * SIL_OK, SIL_EINVAL (null outputs, bad dtype, d or k <= 0) or
- * SIL_EUNSUPPORTED (no plan fits in shared memory, e.g. d > 128).
+ * SIL_EUNSUPPORTED (no plan fits in shared memory: d > 256 for float32
+ * storage, whose rows wider than 128 columns are taken in 64-column chunks,
+ * or d > 128 for BF16 and FP8).
  */
 int sil_tensor_plan(int32_t dtype, int32_t d, int32_t k, int32_t* block_k, int32_t* n_blocks);
 

@@ -105,6 +105,14 @@ def test_binding_refuses_cpu_tensors():
         sil.aggregate(X, torch.zeros(4, dtype=torch.int32), 2)
 
 
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    # no fallback: without libsil.so the binding raises instead of computing elsewhere
+    monkeypatch.setattr(sil, "_lib", None)
+    monkeypatch.setattr(_build, "LIB", str(tmp_path / "libsil.so"))
+    with pytest.raises(RuntimeError, match="libsil.so not found"):
+        sil.load(build_if_stale=False)
+
+
 def test_tensor_plan_is_host_arithmetic():
     import torch
     # one block covers k <= 256 when it fits; k = 1000 in BF16 at d = 128 takes
