@@ -11,6 +11,8 @@ Entry points mirror the C names:
   score_backward(X, labels, K, agg, ...)-> dX                  sil_score_backward
   score_batched(X, labels, ks, ...)     -> S[B]                sil_score_batched
   silhouette(X, labels, K, ...)         -> S (aggregate + score)
+  silhouette_chunked(X_host, labels_host, K, ...)
+                                        -> S of host-resident data streamed in row chunks
 Results stay on the device and nothing synchronises; ``check_status`` reads
 the device status word (one sync) and raises on a data error.
 """
@@ -405,3 +407,115 @@ def silhouette(X: torch.Tensor, labels: torch.Tensor, K: int, metric: str = "sqe
     agg = aggregate(X, labels, K, metric, col_scale=col_scale, status=status)
     return score(X, labels, K, agg, metric, col_scale=col_scale, want_s=want_s, path=path,
                  status=status)
+
+
+# ----------------------------------------------------------- out of core
+def row_chunks(N: int, chunk_rows: int) -> list[tuple[int, int]]:
+    """[start, stop) ranges of at most ``chunk_rows`` rows covering rows 0..N-1 in order."""
+    if chunk_rows <= 0:
+        raise ValueError("chunk_rows must be positive")
+    if N < 0:
+        raise ValueError("N must be non-negative")
+    return [(a, min(a + chunk_rows, N)) for a in range(0, N, chunk_rows)]
+
+
+def combine_chunk_scores(S_chunks, n_chunks) -> float:
+    """S of all rows from the means of disjoint row chunks.
+
+    S is the mean of s_i over every row (Eq. 2 averaged over the N points), so
+    with S_c the mean over chunk c of n_c rows, S = sum_c n_c S_c / sum_c n_c.
+    """
+    S_chunks, n_chunks = list(S_chunks), list(n_chunks)
+    if len(S_chunks) != len(n_chunks) or not n_chunks:
+        raise ValueError("one row count per chunk score, at least one chunk")
+    total = sum(int(n) for n in n_chunks)
+    if total <= 0:
+        raise ValueError("no rows")
+    return float(sum(float(S) * int(n) for S, n in zip(S_chunks, n_chunks)) / total)
+
+
+@dataclasses.dataclass
+class ChunkedScore:
+    S: float                         # the Silhouette of all rows
+    s: torch.Tensor | None           # float32[N] on the host (pinned), or None
+    chunks: int                      # row chunks streamed per pass
+
+
+def silhouette_chunked(X_host: torch.Tensor, labels_host: torch.Tensor, K: int,
+                       metric: str = "sqeuclidean", chunk_rows: int = 1 << 22, device=None,
+                       col_scale: torch.Tensor | None = None, want_s: bool = False) -> ChunkedScore:
+    """S (and optionally every s_i) of data held in HOST memory, streamed through the GPU.
+
+    For datasets larger than the device, or held by the host anyway.  The
+    aggregates are sums over rows (Eq. 6, 8, 16), so pass 1 adds every chunk's
+    into one set (SIL_AGG_ACCUMULATE), like the per-worker partial sums the
+    paper merges; pass 2 streams the chunks again and scores each against the
+    aggregates of ALL rows (a_i, b_i of a point depend only on them), and S is
+    the row-weighted mean of the chunk means.  Each chunk is copied from host
+    memory on a copy stream into one of two device buffers, so the copy of
+    chunk c+1 overlaps the kernels of chunk c (pinned host tensors make the
+    copies asynchronous).  Every step of both passes runs in libsil's kernels;
+    this function only moves chunks and adds up n_c * S_c on the host.  It
+    synchronises once, at the end, and raises SilError on a data error.
+    """
+    if X_host.is_cuda or labels_host.is_cuda:
+        raise ValueError("silhouette_chunked streams host tensors; use silhouette() for device data")
+    if X_host.dim() != 2 or X_host.stride(1) != 1:
+        raise ValueError("X_host must be a 2-D tensor with unit column stride")
+    if labels_host.dtype != torch.int32 or labels_host.dim() != 1 or labels_host.stride(0) != 1:
+        raise ValueError("labels_host must be a contiguous 1-D int32 tensor")
+    N, D = X_host.shape
+    if labels_host.numel() != N:
+        raise ValueError("one label per row")
+    if N == 0:
+        raise ValueError("no rows")
+    chunks = row_chunks(N, chunk_rows)
+    device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+    load()
+    rows = min(chunk_rows, N)
+    Xd = [torch.empty(rows, D, dtype=X_host.dtype, device=device) for _ in range(2)]
+    ld = [torch.empty(rows, dtype=torch.int32, device=device) for _ in range(2)]
+    agg = (torch.zeros(K, dtype=torch.int64, device=device),
+           torch.zeros(K, D, dtype=torch.float64, device=device),
+           torch.zeros(K, dtype=torch.float64, device=device))
+    status = new_status(device)
+    S_host = torch.empty(len(chunks), dtype=torch.float64).pin_memory()
+    s_host = torch.empty(N, dtype=torch.float32).pin_memory() if want_s else None
+    compute = torch.cuda.current_stream(device)
+    copy_stream = torch.cuda.Stream(device)
+    copied = [torch.cuda.Event() for _ in range(2)]
+    consumed = [torch.cuda.Event() for _ in range(2)]
+    for ev in consumed:
+        ev.record(compute)
+
+    def stage(i, a, b):
+        # chunk i into buffer i % 2 once the kernels that last read it are done
+        buf = i % 2
+        copy_stream.wait_event(consumed[buf])
+        with torch.cuda.stream(copy_stream):
+            Xd[buf][:b - a].copy_(X_host[a:b], non_blocking=True)
+            ld[buf][:b - a].copy_(labels_host[a:b], non_blocking=True)
+            copied[buf].record(copy_stream)
+        compute.wait_event(copied[buf])
+        return Xd[buf][:b - a], ld[buf][:b - a], buf
+
+    try:
+        with torch.cuda.device(device):
+            for i, (a, b) in enumerate(chunks):  # pass 1: one set of aggregates over all chunks
+                x, lab, buf = stage(i, a, b)
+                aggregate(x, lab, K, metric, col_scale=col_scale, out=agg, accumulate=i > 0, status=status)
+                consumed[buf].record(compute)
+            for i, (a, b) in enumerate(chunks):  # pass 2: every chunk against all rows' aggregates
+                x, lab, buf = stage(len(chunks) + i, a, b)
+                r = score(x, lab, K, agg, metric, col_scale=col_scale, want_s=want_s, status=status)
+                S_host[i].copy_(r.S, non_blocking=True)
+                if want_s:
+                    s_host[a:b].copy_(r.s, non_blocking=True)
+                consumed[buf].record(compute)
+    finally:
+        # also when a call raised: no copy may still target the buffers freed on return
+        copy_stream.synchronize()
+        compute.synchronize()
+    check_status(status, "silhouette_chunked")
+    S = combine_chunk_scores(S_host.tolist(), [b - a for a, b in chunks])
+    return ChunkedScore(S=S, s=s_host, chunks=len(chunks))
