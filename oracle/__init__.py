@@ -12,8 +12,11 @@ autograd lives in ``oracle.torch_ref``.
 
 Passages followed (Sec./Eq. of the paper):
   aggregate     Eq. 5-6 (Psi), Eq. 8 (Y), Eq. 15-16 (Omega)
-  bruteforce    Eq. 1-3 and the mean S of Sec. II; distances Eq. 4 / Eq. 12
-  linear        Eq. 10-11 (squared Euclidean), Eq. 17-18 (cosine)
+  bruteforce    Eq. 1-3 and the mean S of Sec. II; distances Eq. 4 / Eq. 12,
+                the plain Euclidean distance, and the Limitations section's
+                approximation of it (square root of each mean squared distance)
+  linear        Eq. 10-11 (squared Euclidean; then the square root of each
+                mean for the approximation), Eq. 17-18 (cosine)
   linear_grad   dS/dX of the linear form, labels fixed (no counterpart in
                 the paper; derivation in the design notes)
 """
@@ -33,7 +36,9 @@ _lock = threading.Lock()
 _lib = None
 
 OK, EINVAL, ELABEL, EDEGENERATE, EZERONORM = 0, 1, 2, 3, 4
-METRICS = {"sqeuclidean": 0, "cosine": 1}
+# "euclidean": the plain distance (quadratic form only); "euclidean_rms": the
+# square root of each point-to-cluster mean squared distance (Limitations)
+METRICS = {"sqeuclidean": 0, "cosine": 1, "euclidean": 2, "euclidean_rms": 3}
 
 
 def build(force: bool = False) -> str:

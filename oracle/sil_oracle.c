@@ -19,9 +19,16 @@
  *                      (Omega, sum of normalised vectors) for cosine.
  *   oracle_bruteforce  Sec. II Eq. 1-2 and the mean S; Sec. III Eq. 3 with
  *                      the pairwise distance of Eq. 4 (squared Euclidean) or
- *                      Eq. 12 (cosine distance 1 - cs).  O(N^2 D).
+ *                      Eq. 12 (cosine distance 1 - cs).  O(N^2 D).  Also the
+ *                      plain Euclidean distance (Sec. II names it; the
+ *                      Limitations section says the linear method cannot
+ *                      give it exactly) and the approximation that section
+ *                      suggests: the square root of each point-to-cluster
+ *                      mean of squared distances (RMS).
  *   oracle_linear      Sec. III-A Eq. 10-11 and Sec. III-B Eq. 17-18: every
- *                      point scored from the per-cluster aggregates only.
+ *                      point scored from the per-cluster aggregates only;
+ *                      for the RMS approximation, Eq. 10-11 followed by the
+ *                      square root of each mean.
  *   oracle_linear_grad dS/dX of the linear form with labels fixed (the
  *                      derivation is written out in the design notes: the
  *                      paper has no backward pass).
@@ -53,6 +60,8 @@
 
 #define METRIC_SQEUCLIDEAN 0
 #define METRIC_COSINE 1
+#define METRIC_EUCLIDEAN 2     /* exact ||x - y||: quadratic form only */
+#define METRIC_EUCLIDEAN_RMS 3 /* sqrt of the mean squared distance to a cluster */
 
 int oracle_num_threads(void) {
 #ifdef _OPENMP
@@ -81,20 +90,34 @@ static int check_norms(const double* X, int64_t N, int32_t D) {
   return ORACLE_OK;
 }
 
-/* Pairwise distance: Eq. 4 left-hand side (squared Euclidean) or 1 - cs with
+static int metric_ok(int metric) { return metric >= METRIC_SQEUCLIDEAN && metric <= METRIC_EUCLIDEAN_RMS; }
+
+/* Pairwise distance: Eq. 4 left-hand side (squared Euclidean, also what the
+ * RMS approximation averages), its square root (Euclidean), or 1 - cs with
  * cs from Eq. 12 (cosine). */
 static double pair_distance(const double* x, const double* y, int32_t D, int metric) {
-  if (metric == METRIC_SQEUCLIDEAN) {
+  if (metric != METRIC_COSINE) {
     double s = 0.0;
     for (int32_t l = 0; l < D; ++l) {
       double t = x[l] - y[l];
       s += t * t;
     }
-    return s;
+    return metric == METRIC_EUCLIDEAN ? sqrt(s) : s;
   }
   double dot = 0.0;
   for (int32_t l = 0; l < D; ++l) dot += x[l] * y[l];
   return 1.0 - dot / (row_norm(x, D) * row_norm(y, D));
+}
+
+/* Mean distance from a point to a cluster, from the summed distance and the
+ * number of members it runs over (Eq. 3, Eq. 11, Eq. 18).  The RMS
+ * approximation then takes the square root of that mean of squared distances
+ * (a mean of squares is >= 0: a negative rounding residue of the expanded
+ * Eq. 10 counts as 0). */
+static double cluster_mean(double summed, double members, int metric) {
+  double m = summed / members;
+  if (metric == METRIC_EUCLIDEAN_RMS) return m > 0.0 ? sqrt(m) : 0.0;
+  return m;
 }
 
 /* Eq. 1 / Eq. 2 with the readings above. */
@@ -117,7 +140,7 @@ static double silhouette_of(double a, double b) {
  */
 int oracle_aggregate(const double* X, int64_t N, int32_t D, const int32_t* labels,
                      int32_t K, int metric, int64_t* count, double* s1, double* s2) {
-  if (N < 0 || D <= 0 || K <= 0) return ORACLE_EINVAL;
+  if (N < 0 || D <= 0 || K <= 0 || !metric_ok(metric)) return ORACLE_EINVAL;
   int st = check_labels(labels, N, K);
   if (st) return st;
   if (metric == METRIC_COSINE && (st = check_norms(X, N, D))) return st;
@@ -184,7 +207,7 @@ static int count_nonempty(const int64_t* count, int32_t K) {
 int oracle_bruteforce(const double* X, int64_t N, int32_t D, const int32_t* labels,
                       int32_t K, int metric, double* s, double* a, double* b,
                       int32_t* kstar, double* S_out) {
-  if (N < 0 || D <= 0 || K <= 0) return ORACLE_EINVAL;
+  if (N < 0 || D <= 0 || K <= 0 || !metric_ok(metric)) return ORACLE_EINVAL;
   int st = check_labels(labels, N, K);
   if (st) return st;
   if (metric == METRIC_COSINE && (st = check_norms(X, N, D))) return st;
@@ -201,12 +224,12 @@ int oracle_bruteforce(const double* X, int64_t N, int32_t D, const int32_t* labe
       sums[labels[j]] += pair_distance(xi, X + j * D, D, metric);
     }
     int32_t c = labels[i];
-    double ai = count[c] > 1 ? sums[c] / (double)(count[c] - 1) : 0.0;
+    double ai = count[c] > 1 ? cluster_mean(sums[c], (double)(count[c] - 1), metric) : 0.0;
     double bi = INFINITY;
     int32_t kb = -1;
     for (int32_t k = 0; k < K; ++k) {
       if (k == c || count[k] == 0) continue;
-      double m = sums[k] / (double)count[k];
+      double m = cluster_mean(sums[k], (double)count[k], metric);
       if (m < bi) { bi = m; kb = k; }
     }
     double si = (count[c] > 1 && kb >= 0) ? silhouette_of(ai, bi) : 0.0;
@@ -236,7 +259,8 @@ int oracle_linear(const double* X, int64_t N, int32_t D, const int32_t* labels, 
                   int metric, const int64_t* count, const double* s1, const double* s2,
                   const int64_t* idx, int64_t M, double* s, double* a, double* b,
                   int32_t* kstar) {
-  if (N < 0 || D <= 0 || K <= 0) return ORACLE_EINVAL;
+  /* the plain Euclidean distance has no aggregate form (Limitations) */
+  if (N < 0 || D <= 0 || K <= 0 || !metric_ok(metric) || metric == METRIC_EUCLIDEAN) return ORACLE_EINVAL;
   if (!idx) M = N;
   int st = ORACLE_OK;
   for (int64_t q = 0; q < M; ++q) {
@@ -261,14 +285,14 @@ int oracle_linear(const double* X, int64_t N, int32_t D, const int32_t* labels, 
       double dot = 0.0;
       for (int32_t l = 0; l < D; ++l) dot += s1[(size_t)k * D + l] * x[l];
       double numer;
-      if (metric == METRIC_SQEUCLIDEAN)
+      if (metric != METRIC_COSINE)
         numer = (double)count[k] * xi_sq + s2[k] - 2.0 * dot; /* Eq. 10 */
       else
         numer = (double)count[k] - dot * inv_norm; /* Eq. 17 */
       if (k == c) {
-        ai = count[c] > 1 ? numer / (double)(count[c] - 1) : 0.0;
+        ai = count[c] > 1 ? cluster_mean(numer, (double)(count[c] - 1), metric) : 0.0;
       } else {
-        double m = numer / (double)count[k]; /* Eq. 11 / Eq. 18 */
+        double m = cluster_mean(numer, (double)count[k], metric); /* Eq. 11 / Eq. 18 */
         if (m < bi) { bi = m; kb = k; }
       }
     }
@@ -307,6 +331,7 @@ static void silhouette_partials(double a, double b, double* dsa, double* dsb) {
 int oracle_linear_grad(const double* X, int64_t N, int32_t D, const int32_t* labels,
                        int32_t K, int metric, double gS, double* dX) {
   if (N <= 0 || D <= 0 || K <= 0) return ORACLE_EINVAL;
+  if (metric != METRIC_SQEUCLIDEAN && metric != METRIC_COSINE) return ORACLE_EINVAL;
   int64_t* count = (int64_t*)calloc((size_t)K, sizeof(int64_t));
   double* s1 = (double*)calloc((size_t)K * D, sizeof(double));
   double* s2 = (double*)calloc((size_t)K, sizeof(double));

@@ -24,8 +24,8 @@ HERE = os.path.dirname(__file__)
 SRC = os.path.join(os.path.dirname(HERE), "oracle", "sil_oracle.c")
 
 MUTANTS = {
-    "own_cluster_over_n": ("ai = count[c] > 1 ? numer / (double)(count[c] - 1) : 0.0;",
-                           "ai = count[c] > 1 ? numer / (double)count[c] : 0.0;"),
+    "own_cluster_over_n": ("ai = count[c] > 1 ? cluster_mean(numer, (double)(count[c] - 1), metric) : 0.0;",
+                           "ai = count[c] > 1 ? cluster_mean(numer, (double)count[c], metric) : 0.0;"),
     "drop_psi": ("numer = (double)count[k] * xi_sq + s2[k] - 2.0 * dot;",
                  "numer = (double)count[k] * xi_sq - 2.0 * dot;"),
     "cross_term_sign": ("numer = (double)count[k] * xi_sq + s2[k] - 2.0 * dot;",
@@ -36,8 +36,15 @@ MUTANTS = {
                             "numer = (double)count[k] - dot;"),
     "aggregate_index": ("s1_t[((size_t)t * K + k) * D + l] += v;",
                         "s1_t[((size_t)t * K + k) * D + 0] += v;"),
-    "bruteforce_self_in_a": ("ai = count[c] > 1 ? sums[c] / (double)(count[c] - 1) : 0.0;",
-                             "ai = count[c] > 1 ? sums[c] / (double)count[c] : 0.0;"),
+    "bruteforce_self_in_a": ("ai = count[c] > 1 ? cluster_mean(sums[c], (double)(count[c] - 1), metric) : 0.0;",
+                             "ai = count[c] > 1 ? cluster_mean(sums[c], (double)count[c], metric) : 0.0;"),
+    "rms_no_square_root": ("if (metric == METRIC_EUCLIDEAN_RMS) return m > 0.0 ? sqrt(m) : 0.0;",
+                           "if (metric == METRIC_EUCLIDEAN_RMS) return m;"),
+    "rms_root_of_the_sum": ("if (metric == METRIC_EUCLIDEAN_RMS) return m > 0.0 ? sqrt(m) : 0.0;",
+                            "if (metric == METRIC_EUCLIDEAN_RMS) return summed > 0.0 ? sqrt(summed) / members : 0.0;"),
+    "euclidean_no_square_root": ("return metric == METRIC_EUCLIDEAN ? sqrt(s) : s;", "return s;"),
+    "rms_linear_takes_cosine_form": ("if (metric != METRIC_COSINE)\n        numer",
+                                     "if (metric == METRIC_SQEUCLIDEAN)\n        numer"),
     "cosine_one_norm": ("return 1.0 - dot / (row_norm(x, D) * row_norm(y, D));",
                         "return 1.0 - dot / row_norm(x, D);"),
     "grad_alpha_denominator": ("alpha[i] = dsa / (double)(count[c] - 1);",
@@ -64,19 +71,21 @@ def _failed_pins(lib):
         g = json.load(open(path))
         X, lab = np.array(g["X"], float), np.array(g["labels"], np.int32)
         s_ref = np.array([float(Fraction(v)) for v in g["s"]])
-        for form in ("bruteforce", "linear"):
+        for form in g.get("forms", ("bruteforce", "linear")):
             try:
                 r = getattr(oracle, form)(X, lab, g["K"], g["metric"], lib=lib)
                 if not np.allclose(r["s"], s_ref, rtol=0, atol=1e-12):
                     failed.append(f"golden:{os.path.basename(path)}:{form}")
             except ValueError:
                 failed.append(f"golden:{os.path.basename(path)}:{form}:raised")
-    for metric in ("sqeuclidean", "cosine"):
+    for metric in ("sqeuclidean", "cosine", "euclidean_rms"):
         X, lab = _case(5, 80, 4, 5, metric)
         bf = oracle.bruteforce(X, lab, 5, metric, lib=lib)
         li = oracle.linear(X, lab, 5, metric, lib=lib)
         if not np.allclose(bf["s"], li["s"], rtol=0, atol=1e-10):
             failed.append(f"linear_vs_bruteforce:{metric}")
+        if metric == "euclidean_rms":
+            continue
         count, s1, s2 = oracle.aggregate(X, lab, 5, metric, lib=lib)
         V = X / np.linalg.norm(X, axis=1, keepdims=True) if metric == "cosine" else X
         if not np.allclose(s1, np.eye(5)[lab].T @ V, rtol=1e-12, atol=1e-12):

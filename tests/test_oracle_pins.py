@@ -47,6 +47,8 @@ def small_case(seed, N=60, D=3, K=4, metric="sqeuclidean", empty=True, singleton
 @pytest.mark.parametrize("form", ["bruteforce", "linear"])
 def test_golden_hand_worked(path, form):
     g = json.load(open(path))
+    if form not in g.get("forms", ["bruteforce", "linear"]):
+        pytest.skip(f"{g['metric']} has no {form} form")
     X = np.array(g["X"], dtype=np.float64)
     lab = np.array(g["labels"], dtype=np.int32)
     r = getattr(oracle, form)(X, lab, g["K"], g["metric"])
@@ -88,7 +90,7 @@ def test_linear_subset_indexing():
 
 
 # ----------------------------------------------- independent library routine
-@pytest.mark.parametrize("metric", ["sqeuclidean", "cosine"])
+@pytest.mark.parametrize("metric", ["sqeuclidean", "cosine", "euclidean"])
 @pytest.mark.parametrize("seed", [11, 12])
 def test_matches_sklearn(metric, seed):
     skm = pytest.importorskip("sklearn.metrics")
@@ -279,3 +281,75 @@ def test_grad_invariants():
     Xc, labc = _tie_free(45, "cosine", N=300, D=5, K=6)
     gc = oracle.linear_grad(Xc, labc, 6, "cosine")
     np.testing.assert_allclose((Xc * gc).sum(1), 0.0, atol=1e-13)  # per-row scale invariance
+
+
+# ------------------------------------- Euclidean distance and its RMS approximation
+# The Limitations section: the plain Euclidean distance has no aggregate form;
+# the square root of each point-to-cluster mean of squared distances (RMS)
+# approximates it.  The exact form is pinned to scikit-learn above and to a
+# hand-worked example (tests/golden); the approximation to the quadratic
+# definition, to Jensen's inequality and to a case where it is exact.
+@pytest.mark.parametrize("seed,N,D,K", [(21, 60, 2, 3), (22, 150, 5, 6), (23, 31, 1, 5), (24, 120, 3, 9)])
+def test_rms_linear_equals_bruteforce(seed, N, D, K):
+    X, lab = small_case(seed, N, D, K)
+    bf = oracle.bruteforce(X, lab, K, "euclidean_rms")
+    li = oracle.linear(X, lab, K, "euclidean_rms")
+    np.testing.assert_allclose(li["a"], bf["a"], rtol=1e-10, atol=1e-11)
+    np.testing.assert_allclose(li["b"], bf["b"], rtol=1e-10, atol=1e-11)
+    np.testing.assert_allclose(li["s"], bf["s"], rtol=0, atol=1e-11)
+    np.testing.assert_array_equal(li["kstar"], bf["kstar"])
+    assert abs(li["S"] - bf["S"]) < 1e-12
+
+
+@pytest.mark.parametrize("seed", [31, 32])
+def test_rms_bounds_the_euclidean_means_from_above(seed):
+    # sqrt(mean d^2) >= mean d for every cluster (Jensen), hence for a_i and
+    # for the minimum b_i
+    X, lab = small_case(seed, 120, 4, 5)
+    rms = oracle.bruteforce(X, lab, 5, "euclidean_rms")
+    euc = oracle.bruteforce(X, lab, 5, "euclidean")
+    assert np.all(rms["a"] >= euc["a"] - 1e-12)
+    assert np.all(rms["b"] >= euc["b"] - 1e-12)
+    assert np.any(rms["b"] > euc["b"] + 1e-3)  # and it is an approximation
+
+
+def test_rms_is_exact_when_every_mean_runs_over_one_point():
+    # one two-point cluster among singletons: every mean a scored point takes
+    # is over a single distance, so RMS and plain Euclidean agree
+    rng = np.random.default_rng(41)
+    X = rng.normal(size=(9, 3))
+    lab = np.array([0, 0, 1, 2, 3, 4, 5, 6, 7], dtype=np.int32)
+    rms = oracle.bruteforce(X, lab, 8, "euclidean_rms")
+    euc = oracle.bruteforce(X, lab, 8, "euclidean")
+    np.testing.assert_allclose(rms["s"], euc["s"], rtol=0, atol=1e-14)
+    assert np.count_nonzero(euc["s"]) == 2
+    np.testing.assert_allclose(oracle.linear(X, lab, 8, "euclidean_rms")["s"], euc["s"], rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("seed", [51, 52])
+def test_rms_score_is_a_monotone_function_of_the_squared_score(seed):
+    # with r = a/b of the squared means, s_sq = 1 - r and s_rms = 1 - sqrt(r)
+    # (a <= b); s_sq = 1/r - 1 and s_rms = 1/sqrt(r) - 1 (a > b): same sign,
+    # smaller magnitude
+    X, lab = small_case(seed, 100, 3, 5)
+    sq = oracle.linear(X, lab, 5, "sqeuclidean")["s"]
+    rms = oracle.linear(X, lab, 5, "euclidean_rms")["s"]
+    expect = np.where(sq >= 0, 1 - np.sqrt(np.clip(1 - sq, 0, None)), np.sqrt(1 + sq) - 1)
+    np.testing.assert_allclose(rms, expect, rtol=0, atol=1e-12)
+    assert np.all(np.abs(rms) <= np.abs(sq) + 1e-15)
+
+
+@pytest.mark.parametrize("metric", ["euclidean", "euclidean_rms"])
+def test_euclidean_forms_are_translation_and_scale_invariant(metric):
+    X, lab = small_case(61, 80, 3, 4)
+    S = oracle.bruteforce(X, lab, 4, metric)["S"]
+    assert abs(oracle.bruteforce(X + 7.5, lab, 4, metric)["S"] - S) < 1e-12
+    assert abs(oracle.bruteforce(3.0 * X, lab, 4, metric)["S"] - S) < 1e-12
+
+
+def test_exact_euclidean_has_no_linear_form():
+    X, lab = small_case(62, 20, 2, 3)
+    with pytest.raises(ValueError):
+        oracle.linear(X, lab, 3, "euclidean")
+    with pytest.raises(ValueError):
+        oracle.linear_grad(X, lab, 3, "euclidean_rms")
