@@ -59,8 +59,15 @@ extern "C" {
 #endif
 
 /* Distance measures of Sec. III-A (squared Euclidean, Eq. 4) and Sec. III-B
- * (cosine distance 1 - cs, Eq. 12). */
-typedef enum { SIL_SQEUCLIDEAN = 0, SIL_COSINE = 1 } sil_distance_t;
+ * (cosine distance 1 - cs, Eq. 12), and SIL_EUCLIDEAN_RMS, the approximation
+ * of the Euclidean Silhouette that the Limitations section suggests: a_i and
+ * b_i are the square roots of the point-to-cluster MEAN SQUARED Euclidean
+ * distances (root mean square, >= the mean Euclidean distance), so that b_i's
+ * cluster and everything before Eq. 2 are those of SIL_SQEUCLIDEAN (same
+ * aggregates, same passes).  The exact Euclidean Silhouette has no aggregate
+ * form.  sil_score_backward returns SIL_EUNSUPPORTED for SIL_EUCLIDEAN_RMS,
+ * and its saved record holds the squared means. */
+typedef enum { SIL_SQEUCLIDEAN = 0, SIL_COSINE = 1, SIL_EUCLIDEAN_RMS = 2 } sil_distance_t;
 
 /* Storage type of X. */
 typedef enum { SIL_F32 = 0, SIL_BF16 = 1, SIL_FP8_E4M3 = 2 } sil_dtype_t;

@@ -33,4 +33,6 @@ class SilhouetteFn(torch.autograd.Function):
 def silhouette_loss(X: torch.Tensor, labels: torch.Tensor, K: int, metric: str = "sqeuclidean",
                     col_scale: torch.Tensor | None = None) -> torch.Tensor:
     """Differentiable Silhouette S of X (0-d float64 tensor)."""
+    if metric not in ("sqeuclidean", "cosine"):
+        raise ValueError(f"no gradient for metric {metric!r}")
     return SilhouetteFn.apply(X, labels, K, metric, col_scale)

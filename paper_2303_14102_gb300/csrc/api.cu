@@ -57,7 +57,7 @@ int check_common(const void* X, int32_t dtype, int64_t n, int32_t d, int64_t ldx
                  const int32_t* labels, int32_t k, int32_t dist) {
   if (n < 0 || d <= 0 || k <= 0 || ldx < d) return SIL_EINVAL;
   if (dtype < SIL_F32 || dtype > SIL_FP8_E4M3) return SIL_EINVAL;
-  if (dist != SIL_SQEUCLIDEAN && dist != SIL_COSINE) return SIL_EINVAL;
+  if (dist != SIL_SQEUCLIDEAN && dist != SIL_COSINE && dist != SIL_EUCLIDEAN_RMS) return SIL_EINVAL;
   if (n > 0 && (X == nullptr || labels == nullptr)) return SIL_EINVAL;
   if (dtype == SIL_FP8_E4M3 && cs == nullptr) return SIL_EINVAL;
   if (k > (1 << 22) || d > (1 << 16)) return SIL_EUNSUPPORTED;
@@ -245,6 +245,7 @@ int sil_score_backward(const void* X, int32_t dtype, int64_t n, int32_t d, int64
                        void* ws, size_t ws_bytes, uint32_t* dev_status, void* stream) {
   SIL_TRY(check_common(X, dtype, n, d, ldx, col_scale, labels, k, dist));
   if (!count || !s1 || !s2 || (n > 0 && !dX) || lddx < d) return SIL_EINVAL;
+  if (dist == SIL_EUCLIDEAN_RMS) return SIL_EUNSUPPORTED;  // no gradient for the approximation
   SIL_TRY(check_ws(ws, ws_bytes, n, d, k, dtype, dist, 1));
   const WsLayout L = ws_layout(n, d, k, dtype, dist, 1);
   cudaStream_t st = static_cast<cudaStream_t>(stream);

@@ -81,7 +81,7 @@ extern "C" int sil_score_noalloc(const void* X, int32_t dtype, int64_t n, int32_
   using namespace sil;
   if (n < 0 || d <= 0 || k <= 0 || ldx < d) return SIL_EINVAL;
   if (dtype < SIL_F32 || dtype > SIL_FP8_E4M3) return SIL_EINVAL;
-  if (dist != SIL_SQEUCLIDEAN && dist != SIL_COSINE) return SIL_EINVAL;
+  if (dist != SIL_SQEUCLIDEAN && dist != SIL_COSINE && dist != SIL_EUCLIDEAN_RMS) return SIL_EINVAL;
   if (n > 0 && (X == nullptr || labels == nullptr)) return SIL_EINVAL;
   if (dtype == SIL_FP8_E4M3 && col_scale == nullptr) return SIL_EINVAL;
   if (!count || !s1 || !s2) return SIL_EINVAL;

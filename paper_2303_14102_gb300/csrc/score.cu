@@ -138,6 +138,7 @@ struct ScoreK {
   const float4* cl;
   const float* gf;
   int32_t cosine;
+  int32_t rms;  // Eq. 2 on the square roots of a and b (approximate Euclidean)
   float scale;
   int32_t vec;
   float* s_out;
@@ -149,11 +150,8 @@ struct ScoreK {
   int32_t kc;  // clusters per shared-memory chunk
 };
 
-__device__ __forceinline__ float silhouette_value(float a, float b, bool defined) {
-  if (!defined) return 0.f;
-  const float m = fmaxf(a, b);
-  if (!(m > 0.f)) return 0.f;
-  return a <= b ? 1.f - a / b : b / a - 1.f;
+__device__ __forceinline__ float silhouette_value(float a, float b, bool defined, bool rms) {
+  return defined ? sil_eq2(a, b, rms) : 0.f;
 }
 
 __device__ __forceinline__ void block_partial(float v, double* out) {
@@ -303,7 +301,7 @@ __global__ void __launch_bounds__(kScoreThreads) k_score_simt(ScoreK a) {
         av = fmaxf(0.f, a.scale * fmaf(co.y, ss, co.z));
         kb = kbest[j];
         bv = kb >= 0 ? fmaxf(0.f, a.scale * (xn2[j] + best[j])) : INFINITY;
-        sv = silhouette_value(av, bv, co.w > 1.5f && kb >= 0);
+        sv = silhouette_value(av, bv, co.w > 1.5f && kb >= 0, a.rms);
       }
       if (a.s_out) a.s_out[p] = sv;
       if (a.sa) {
@@ -411,7 +409,7 @@ __global__ void __launch_bounds__(64) k_score_simt_wide(ScoreK a) {
         av = fmaxf(0.f, a.scale * fmaf(co.y, s2, co.z));
         kb = kbest;
         bv = kb >= 0 ? fmaxf(0.f, a.scale * (n2 + best)) : INFINITY;
-        sv = silhouette_value(av, bv, co.w > 1.5f && kb >= 0);
+        sv = silhouette_value(av, bv, co.w > 1.5f && kb >= 0, a.rms);
       }
       if (a.s_out) a.s_out[p] = sv;
       if (a.sa) {
@@ -536,6 +534,7 @@ cudaError_t launch_score_simt(ScoreLaunch& s) {
   k.cl = s.cl;
   k.gf = s.gf;
   k.cosine = s.dist == SIL_COSINE;
+  k.rms = s.dist == SIL_EUCLIDEAN_RMS;
   k.scale = s.dist == SIL_COSINE ? 0.5f : 1.f;
   k.vec = vec_ok_s(s.X, s.dtype, s.ldx);
   k.s_out = s.s_out;

@@ -389,6 +389,7 @@ struct TcK {
   int32_t acc_cols;  // TMEM columns per accumulator (power of two >= kp)
   int32_t dz;
   int32_t cosine;
+  int32_t rms;  // Eq. 2 on the square roots of a and b (approximate Euclidean)
   float scale;
   int32_t nxs;  // raw X stages (MODE 0, 2)
   int32_t nab;  // A buffers
@@ -958,8 +959,7 @@ __global__ void __launch_bounds__(tc_threads(DP, CG), 1) k_score_tc(TcK a, const
             av = fmaxf(0.f, a.scale * side[kTM + r]);
             bv = has_b ? fmaxf(0.f, a.scale * dk) : INFINITY;
             if (code >= 0 && has_b) {
-              const float m = fmaxf(av, bv);
-              sv = m > 0.f ? (av <= bv ? 1.f - av / bv : bv / av - 1.f) : 0.f;
+              sv = sil_eq2(av, bv, a.rms != 0);
             }
             if (!has_b) kb = -1;
           } else {
@@ -1346,8 +1346,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_score_tc_wide(TcK a, const __
             av = fmaxf(0.f, a.scale * aown);
             bv = has_b ? fmaxf(0.f, a.scale * dk) : INFINITY;
             if (code >= 0 && has_b) {
-              const float m = fmaxf(av, bv);
-              sv = m > 0.f ? (av <= bv ? 1.f - av / bv : bv / av - 1.f) : 0.f;
+              sv = sil_eq2(av, bv, a.rms != 0);
             }
             if (!has_b) kb = -1;
           } else {
@@ -1389,8 +1388,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_score_tc_wide(TcK a, const __
 // in order and only a strictly smaller value replaces the best), then Eq. 2
 // with the singleton and max(a, b) = 0 rules, and one partial sum per CTA.
 __global__ void k_tc_combine(int64_t n, int32_t k, int32_t nblk, const int32_t* labels, const float4* cl,
-                             float scale, const float* pmin, const int32_t* parg, const float* pown,
-                             float* s_out, float* sa, float* sb, int32_t* skstar, double* partials) {
+                             float scale, int32_t rms, const float* pmin, const int32_t* parg,
+                             const float* pown, float* s_out, float* sa, float* sb, int32_t* skstar,
+                             double* partials) {
   float tsum = 0.f;
   for (int64_t row = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; row < n;
        row += int64_t(gridDim.x) * blockDim.x) {
@@ -1412,8 +1412,7 @@ __global__ void k_tc_combine(int64_t n, int32_t k, int32_t nblk, const int32_t* 
       av = fmaxf(0.f, scale * pown[row]);
       bv = has_b ? fmaxf(0.f, scale * best) : INFINITY;
       if (has_b && cl[own].w > 1.5f) {
-        const float m = fmaxf(av, bv);
-        sv = m > 0.f ? (av <= bv ? 1.f - av / bv : bv / av - 1.f) : 0.f;
+        sv = sil_eq2(av, bv, rms != 0);
       }
       if (!has_b) kb = -1;
     } else {
@@ -1750,6 +1749,7 @@ cudaError_t launch_score_tc(const ScoreLaunch& s, const double* g, void* pack, v
   k.acc_cols = pow2_at_least(kp);
   k.dz = dz;
   k.cosine = s.dist == SIL_COSINE;
+  k.rms = s.dist == SIL_EUCLIDEAN_RMS;
   k.scale = s.dist == SIL_COSINE ? 0.5f : 1.f;
   k.nxs = plan.nxs;
   k.nab = plan.nab;
@@ -1814,7 +1814,7 @@ cudaError_t launch_score_tc(const ScoreLaunch& s, const double* g, void* pack, v
     return cudaSuccess;
   }
   const int cgrid = int(std::max<int64_t>(1, std::min<int64_t>(cdiv(s.n, 256), kMaxPartials)));
-  k_tc_combine<<<cgrid, 256, 0, s.stream>>>(s.n, s.k, plan.nblk, s.labels, s.cl, k.scale, k.pmin,
+  k_tc_combine<<<cgrid, 256, 0, s.stream>>>(s.n, s.k, plan.nblk, s.labels, s.cl, k.scale, k.rms, k.pmin,
                                             save ? k.parg : nullptr, k.pown, s.s_out, s.sa, s.sb, s.skstar,
                                             s.partials);
   *s.n_partials = cgrid;

@@ -27,6 +27,20 @@ __host__ __device__ inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 
 __host__ __device__ inline int64_t round_up(int64_t a, int64_t b) { return cdiv(a, b) * b; }
 inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
+// Eq. 2 from a point's mean distances a (own cluster) and b (nearest other
+// cluster), both >= 0: 0 when max(a, b) = 0.  With rms set, a and b are means
+// of squared Euclidean distances and Eq. 2 takes their square roots -- the
+// approximation of the Euclidean Silhouette that the Limitations section
+// suggests (the square root of each point-to-cluster mean distance).
+__device__ __forceinline__ float sil_eq2(float a, float b, bool rms) {
+  if (rms) {
+    a = sqrtf(fmaxf(a, 0.f));
+    b = sqrtf(fmaxf(b, 0.f));
+  }
+  const float m = fmaxf(a, b);
+  return m > 0.f ? (a <= b ? 1.f - a / b : b / a - 1.f) : 0.f;
+}
+
 // Per-cluster constants for pass 2, one float4 per cluster:
 //   x = bias  = ||mu'_k||^2 + W_k/n_k   (+inf when n_k = 0)
 //   y = an    = n_k / (n_k - 1)          (0 when n_k < 2)

@@ -30,7 +30,9 @@ from . import _build
 SIL_OK, SIL_EINVAL, SIL_ELABEL, SIL_EDEGENERATE, SIL_EZERONORM = 0, 1, 2, 4, 8
 SIL_ECUDA, SIL_ETIMEOUT, SIL_EWORKSPACE, SIL_EUNSUPPORTED = 16, 32, 64, 128
 SIL_AGG_ACCUMULATE = 1
-METRICS = {"sqeuclidean": 0, "cosine": 1}
+# "euclidean_rms": the square root of each point-to-cluster mean squared
+# Euclidean distance in Eq. 2 (the approximation of the Limitations section)
+METRICS = {"sqeuclidean": 0, "cosine": 1, "euclidean_rms": 2}
 PATHS = {"auto": 0, "simt": 1, "tensor": 2}
 EXPORTED = ("sil_workspace_size", "sil_saved_size", "sil_aggregate", "sil_score",
             "sil_score_backward", "sil_score_batched", "sil_tensor_plan", "sil_tensor_plan_candidates",

@@ -105,6 +105,21 @@ def test_binding_refuses_cpu_tensors():
         sil.aggregate(X, torch.zeros(4, dtype=torch.int32), 2)
 
 
+def test_euclidean_rms_is_a_distance_code_without_a_backward_pass(lib):
+    assert _agg(lib, dist=3) == sil.SIL_EINVAL
+    vp = ctypes.c_void_p
+    rc = lib.sil_score_backward(vp(16), 0, 10, 4, 4, None, vp(16), 3, sil.METRICS["euclidean_rms"], vp(16),
+                                vp(16), vp(16), None, None, vp(16), 4, vp(256), 1 << 30, None, None)
+    assert rc == sil.SIL_EUNSUPPORTED
+
+
+def test_autograd_refuses_the_rms_approximation():
+    import torch
+    from paper_2303_14102_gb300.autograd import silhouette_loss
+    with pytest.raises(ValueError, match="no gradient"):
+        silhouette_loss(torch.zeros(4, 2), torch.zeros(4, dtype=torch.int32), 2, "euclidean_rms")
+
+
 def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     # no fallback: without libsil.so the binding raises instead of computing elsewhere
     monkeypatch.setattr(sil, "_lib", None)
