@@ -502,8 +502,11 @@ def main():
     del Xd, ld
     variants = {}
     if args.variants and rank == 0:
-        # same workload, cosine and BF16 storage
-        for name, fn in (("cosine_fp32", lambda: sil.silhouette(X, lab, K, "cosine", status=status)),):
+        # same workload: cosine, the approximate Euclidean form (square roots of
+        # the mean squared distances in Eq. 2), and BF16 storage
+        for name, fn in (("cosine_fp32", lambda: sil.silhouette(X, lab, K, "cosine", status=status)),
+                         ("euclidean_rms_fp32",
+                          lambda: sil.silhouette(X, lab, K, "euclidean_rms", status=status))):
             fn()
             s = timed(fn, args.steps, stream)
             variants[name] = {"points_per_s": N * args.steps / s, "ms": s / args.steps * 1e3}
