@@ -180,3 +180,28 @@ def test_tensor_plan_set_rejects_bad_plans(lib):
     assert lib.sil_tensor_plan_set(0, 128, 100, 0, 0, 0, 0, 0) == sil.SIL_OK      # back to the model
     assert lib.sil_tensor_plan_set(0, 300, 100, 64, 2, 2, 0, 0) == sil.SIL_EINVAL     # d > 256
     assert lib.sil_tensor_plan_set(0, 64, 100, 64, 2, 2, 0, 2) == sil.SIL_EINVAL      # rank pass is 0 or 1
+
+
+@pytest.mark.parametrize("dtype_name", ["float32", "bfloat16", "float8_e4m3fn"])
+def test_every_candidate_plan_is_one_the_library_accepts(dtype_name):
+    # the enumerator and the validator must agree on every shape: a plan the
+    # cost model ranks but the kernels cannot run safely (an odd ring shared by
+    # two converter groups) must never be offered
+    import torch
+    dt = getattr(torch, dtype_name)
+    ds = [1, 8, 31, 32, 33, 63, 64, 65, 100, 128] + ([129, 200, 256] if dt == torch.float32 else [])
+    for d in ds:
+        for k in (1, 2, 15, 16, 17, 100, 255, 256, 257, 1000, 4096):
+            cands = sil.tensor_plan_candidates(dt, d, k, 64)
+            assert cands, (dtype_name, d, k)
+            assert sil.tensor_plan(dt, d, k)[0] == cands[0][0]
+            try:
+                for plan in cands:
+                    bk, nab, nxs, stz, rank = plan
+                    assert bk % 16 == 0 and 16 <= bk <= 256 and nab >= 1 and nxs >= 1
+                    assert stz in (0, 1) and rank in (0, 1)
+                    sil.tensor_plan_set(dt, d, k, plan)  # raises SilError if refused
+                    bk2, nb = sil.tensor_plan(dt, d, k)
+                    assert bk2 == bk and (nb - 1) * bk < k <= nb * bk, (dtype_name, d, k, plan)
+            finally:
+                sil.tensor_plan_set(dt, d, k, None)
