@@ -247,6 +247,19 @@ int sil_tensor_plan_candidates(int32_t dtype, int32_t d, int32_t k, int32_t* pla
 int sil_tensor_plan_set(int32_t dtype, int32_t d, int32_t k, int32_t block_k, int32_t a_buffers,
                         int32_t x_stages, int32_t stage_centroids, int32_t rank_pass);
 
+/*
+ * Self-test of the library's failure detection, with no data and no
+ * workspace: one small kernel waits on mbarriers that nothing completes,
+ * through the same bounded waits the pass-1 and pass-2 kernels use, and
+ * reports how each wait ended.  dev_out (device uint32[3], zeroed by the
+ * caller) receives: [0] SIL_ETIMEOUT from the pass-2 wait once its limit
+ * (1 s) passed; [1] SIL_ETIMEOUT from the pass-1 wait likewise; [2] 1 if a
+ * second pass-2 wait, started half a limit later, gave up on the first one's
+ * abort signal before its own limit.  The kernel runs about one second and
+ * leaves the context usable.  Returns SIL_EINVAL for a NULL dev_out.
+ */
+int sil_selftest_bounded_wait(uint32_t* dev_out, void* stream);
+
 /* Human-readable name of a return code or of one status flag. */
 const char* sil_status_string(int32_t status);
 

@@ -385,6 +385,11 @@ int sil_tensor_plan_set(int32_t dtype, int32_t d, int32_t k, int32_t block_k, in
   return tc_plan_set(dtype, d, k, block_k, a_buffers, x_stages, stage_centroids, rank_pass);
 }
 
+int sil_selftest_bounded_wait(uint32_t* dev_out, void* stream) {
+  if (dev_out == nullptr) return SIL_EINVAL;
+  return cu(launch_selftest_wait(dev_out, static_cast<cudaStream_t>(stream)));
+}
+
 const char* sil_status_string(int32_t status) {
   switch (status) {
     case SIL_OK: return "SIL_OK";

@@ -510,6 +510,42 @@ __device__ __forceinline__ bool tc_wait(uint64_t* bar, uint32_t parity, volatile
   return true;
 }
 
+// Self-test of failure detection without a fault: one CTA waits on mbarriers
+// that nothing completes, through the production waits.  Warp 0 runs tc_wait
+// (the pass-2 roles' wait), which must give up after kWaitTimeoutNs with
+// SIL_ETIMEOUT and raise the shared abort flag; warp 1 runs mbar_wait (the
+// pass-1 row gather's wait), which must return false; warp 2 starts its
+// tc_wait half a limit later and must leave on warp 0's abort, before its own
+// limit.  out[3]: the bits of warps 0 and 1, and 1 from warp 2 if it left on
+// the abort.  Shared memory and `out` only; every loop ends on the global
+// timer, the sleep loop also after a fixed number of rounds.
+__global__ void k_selftest_wait(uint32_t* out) {
+  __shared__ __align__(8) uint64_t bars[2];
+  __shared__ int abort_flag;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    mbar_init(&bars[0], 1);
+    mbar_init(&bars[1], 1);
+    abort_flag = 0;
+  }
+  fence_mbar_init();
+  __syncthreads();
+  if (lane == 0 && warp == 0) {
+    tc_wait(&bars[0], 0, &abort_flag, out);
+  } else if (lane == 0 && warp == 1) {
+    if (!mbar_wait(&bars[1], 0)) set_status(out + 1, SIL_ETIMEOUT);
+  } else if (lane == 0 && warp == 2) {
+    const uint64_t t0 = globaltimer_ns();
+    // half a limit (a sleep may end early: the time bound ends the loop; the
+    // round count only guards against a timer that does not advance)
+    for (int i = 0; i < 1000000 && globaltimer_ns() - t0 < kWaitTimeoutNs / 2; ++i) __nanosleep(100000);
+    const uint64_t t1 = globaltimer_ns();
+    const bool done = tc_wait(&bars[0], 0, &abort_flag, out + 2);
+    if (!done && globaltimer_ns() - t1 < kWaitTimeoutNs) atomicOr(out + 2, 1u);
+  }
+  __syncthreads();
+}
+
 template <int MODE, int DP, bool TRACK, int CG>
 __global__ void __launch_bounds__(tc_threads(DP, CG), 1) k_score_tc(TcK a, const __grid_constant__ TcMaps maps) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -1622,6 +1658,11 @@ bool tc_eligible(int32_t dtype, int64_t n, int32_t d, int64_t ldx, int32_t k, co
   if (cudaGetDevice(&dev) != cudaSuccess) return false;
   if (cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev) != cudaSuccess) return false;
   return major == 10;
+}
+
+cudaError_t launch_selftest_wait(uint32_t* out, cudaStream_t stream) {
+  k_selftest_wait<<<1, 96, 0, stream>>>(out);
+  return cudaGetLastError();
 }
 
 bool tc_plan_query(int32_t dtype, int32_t d, int32_t k, int32_t* block_k, int32_t* n_blocks) {

@@ -230,6 +230,8 @@ int tc_plan_set(int32_t dtype, int32_t d, int32_t k, int32_t kp, int32_t nab, in
                 int32_t rank);
 // Bytes of the per-block results when k needs several cluster blocks (else 0).
 size_t tc_partial_bytes(int64_t n, int32_t d, int32_t k, int32_t dtype);
+// One CTA whose waits run out on purpose (failure-detection self-test), out[3].
+cudaError_t launch_selftest_wait(uint32_t* out, cudaStream_t stream);
 cudaError_t launch_score_tc(const ScoreLaunch& s, const double* g, void* pack, void* partial_ws,
                             size_t partial_bytes, uint32_t* status);
 // S = sum(partials)/n, NaN when the workspace status word is non-zero; the

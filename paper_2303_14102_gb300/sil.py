@@ -36,7 +36,8 @@ METRICS = {"sqeuclidean": 0, "cosine": 1, "euclidean_rms": 2}
 PATHS = {"auto": 0, "simt": 1, "tensor": 2}
 EXPORTED = ("sil_workspace_size", "sil_saved_size", "sil_aggregate", "sil_score",
             "sil_score_backward", "sil_score_batched", "sil_tensor_plan", "sil_tensor_plan_candidates",
-            "sil_tensor_plan_set", "sil_status_string", "sil_version")
+            "sil_tensor_plan_set", "sil_score_noalloc", "sil_selftest_bounded_wait", "sil_status_string",
+            "sil_version")
 
 _lock = threading.Lock()
 _lib = None
@@ -87,6 +88,8 @@ def load(build_if_stale: bool = True) -> ctypes.CDLL:
             lib.sil_tensor_plan_candidates.restype = ctypes.c_int
             lib.sil_tensor_plan_set.argtypes = [i32, i32, i32, i32, i32, i32, i32, i32]
             lib.sil_tensor_plan_set.restype = ctypes.c_int
+            lib.sil_selftest_bounded_wait.argtypes = [vp, vp]
+            lib.sil_selftest_bounded_wait.restype = ctypes.c_int
             lib.sil_status_string.argtypes = [i32]
             lib.sil_status_string.restype = ctypes.c_char_p
             lib.sil_version.restype = i32
@@ -409,6 +412,18 @@ def silhouette(X: torch.Tensor, labels: torch.Tensor, K: int, metric: str = "sqe
     agg = aggregate(X, labels, K, metric, col_scale=col_scale, status=status)
     return score(X, labels, K, agg, metric, col_scale=col_scale, want_s=want_s, path=path,
                  status=status)
+
+
+def selftest_bounded_wait(device=None) -> tuple[int, int, int]:
+    """Failure-detection self-test (about one second, no data): how the
+    library's bounded kernel waits end when nothing completes them -- the three
+    words of sil_selftest_bounded_wait (expected: SIL_ETIMEOUT, SIL_ETIMEOUT, 1)."""
+    lib = load()
+    dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+    out = torch.zeros(3, dtype=torch.int32, device=dev)
+    _rc(lib.sil_selftest_bounded_wait(_ptr(out), _stream_handle(dev)), "sil_selftest_bounded_wait")
+    torch.cuda.synchronize(dev)
+    return tuple(int(v) & 0xFFFFFFFF for v in out.cpu().tolist())
 
 
 # ----------------------------------------------------------- out of core

@@ -205,3 +205,7 @@ def test_every_candidate_plan_is_one_the_library_accepts(dtype_name):
                     assert bk2 == bk and (nb - 1) * bk < k <= nb * bk, (dtype_name, d, k, plan)
             finally:
                 sil.tensor_plan_set(dt, d, k, None)
+
+
+def test_selftest_refuses_a_null_status_array(lib):
+    assert lib.sil_selftest_bounded_wait(None, None) == sil.SIL_EINVAL
