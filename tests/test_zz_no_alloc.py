@@ -4,8 +4,9 @@ plugin whose host forbids allocation on its hot path).
 
 It must give the same result as sil_score on the same inputs, and keep doing
 so on back-to-back calls, although every call reuses the one scratch array
-inside the library.  This file is collected last so that a run stopping at
-its first failure has run every other test first.
+inside the library.  This file is collected after every parity file (only
+the bounded-wait self-test follows it) so that a run stopping at its first
+failure has run the others first.
 """
 import ctypes
 
