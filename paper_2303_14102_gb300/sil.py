@@ -15,6 +15,11 @@ Entry points mirror the C names:
                                         -> S of host-resident data streamed in row chunks
 Results stay on the device and nothing synchronises; ``check_status`` reads
 the device status word (one sync) and raises on a data error.
+
+Every call runs on the current stream of the tensors' device and, except
+``score_noalloc``, uses one grow-only workspace per device: issue calls that
+may overlap on ONE stream (or order their streams with events), as with a
+library handle's workspace.
 """
 from __future__ import annotations
 
@@ -137,18 +142,22 @@ def _rc(rc: int, what: str):
 
 
 class _Workspace:
-    """Grow-only device workspace per device (one per process)."""
+    """Grow-only device workspace per device (one per process).  A grown
+    buffer replaces the old one through torch's caching allocator, which
+    reuses the old memory only in the order of the stream it was taken on."""
 
     def __init__(self):
         self._buf = {}
+        self._lock = threading.Lock()
 
     def get(self, device, nbytes: int) -> torch.Tensor:
         key = torch.device(device).index
-        buf = self._buf.get(key)
-        if buf is None or buf.numel() < nbytes:
-            buf = torch.empty(max(nbytes, 1 << 20), dtype=torch.uint8, device=device)
-            self._buf[key] = buf
-        return buf
+        with self._lock:
+            buf = self._buf.get(key)
+            if buf is None or buf.numel() < nbytes:
+                buf = torch.empty(max(nbytes, 1 << 20), dtype=torch.uint8, device=device)
+                self._buf[key] = buf
+            return buf
 
 
 _WS = _Workspace()
