@@ -82,7 +82,7 @@ typedef enum {
   SIL_ECUDA = 16,        /* a CUDA launch or memset failed */
   SIL_ETIMEOUT = 32,     /* device flag: a bounded wait inside a kernel gave up */
   SIL_EWORKSPACE = 64,   /* ws is NULL, misaligned or smaller than required */
-  SIL_EUNSUPPORTED = 128 /* valid arguments this build does not serve */
+  SIL_EUNSUPPORTED = 128 /* valid arguments this library does not serve */
 } sil_status_t;
 
 /* Pass-2 implementation choice for sil_score. */
@@ -193,7 +193,7 @@ int sil_score_batched(const void* X, int32_t dtype, int64_t n, int32_t d, int64_
  * Same arguments and results as sil_score (SIMT pass 2 only), minus ws and
  * ws_bytes.  Its scratch is one fixed device array inside the library
  * (about 1.1 MB, sized for k <= SIL_NOALLOC_MAX_K and d <= SIL_NOALLOC_MAX_D)
- * that the driver reserves on every device that loads the library and keeps
+ * that the CUDA driver reserves on every device that loads the library and keeps
  * until the process exits; the call itself allocates nothing.  Larger k or d
  * return SIL_EUNSUPPORTED with nothing enqueued.  The first call on a device
  * looks up the array's device address (with that device current), so make

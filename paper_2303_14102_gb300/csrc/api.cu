@@ -400,7 +400,7 @@ const char* sil_status_string(int32_t status) {
     case SIL_ECUDA: return "SIL_ECUDA: CUDA launch or memset failed";
     case SIL_ETIMEOUT: return "SIL_ETIMEOUT: a bounded device wait gave up";
     case SIL_EWORKSPACE: return "SIL_EWORKSPACE: workspace missing, misaligned or too small";
-    case SIL_EUNSUPPORTED: return "SIL_EUNSUPPORTED: not served by this build";
+    case SIL_EUNSUPPORTED: return "SIL_EUNSUPPORTED: not served by this library";
     default: return "unknown status";
   }
 }

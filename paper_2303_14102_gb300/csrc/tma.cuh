@@ -107,7 +107,7 @@ __device__ __forceinline__ void tma_gather4(void* dst, const CUtensorMap* map, i
 
 // ------------------------------------------------------------------- host
 // Encode a row-major 2-D tensor map (inner = columns) or a 1-D map.  Return
-// false when the driver entry point is unavailable or rejects the layout.
+// false when the CUDA driver entry point is unavailable or rejects the layout.
 bool encode_tmap_2d(CUtensorMap* map, const void* base, CUtensorMapDataType type, int esz,
                     uint64_t inner, uint64_t outer, uint64_t row_stride_bytes, uint32_t box_inner,
                     uint32_t box_outer, CUtensorMapSwizzle swizzle);

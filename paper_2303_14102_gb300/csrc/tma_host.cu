@@ -1,5 +1,5 @@
-// Host-side tensor-map encoding through the driver entry point (no link-time
-// dependency on libcuda: the runtime hands out the driver function).
+// Host-side tensor-map encoding through the CUDA driver entry point (no
+// link-time dependency on libcuda: the runtime hands out the driver function).
 #include <cudaTypedefs.h>
 
 #include <mutex>

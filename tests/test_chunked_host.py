@@ -1,4 +1,4 @@
-"""Host logic of the out-of-core driver (no GPU): the row partition, and the
+"""Host logic of the out-of-core streaming call (no GPU): the row partition, and the
 combination of per-chunk means into S, pinned against the oracle."""
 import numpy as np
 import pytest
@@ -50,7 +50,7 @@ def test_combine_rejects_bad_input():
         sil.combine_chunk_scores([0.5], [1, 2])
 
 
-def test_driver_checks_arguments_before_touching_a_device():
+def test_streaming_call_checks_arguments_before_touching_a_device():
     X = torch.zeros(10, 3)
     with pytest.raises(ValueError, match="int32"):
         sil.silhouette_chunked(X, torch.zeros(10, dtype=torch.int64), 2)

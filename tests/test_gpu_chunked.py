@@ -1,4 +1,4 @@
-"""Out-of-core driver: data held in host memory, streamed through the GPU in
+"""Out-of-core streaming: data held in host memory, streamed through the GPU in
 row chunks (pass 1 accumulating one set of aggregates, pass 2 scoring every
 chunk against them), gives the oracle's S and s_i and the resident call's."""
 import numpy as np
