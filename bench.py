@@ -153,10 +153,23 @@ def cpu_oracle_sample(X_host, labels_host, K, metric="sqeuclidean", target_s=12.
         if dt * 3 > target_s or M >= X_host.shape[0]:
             break
         M = min(X_host.shape[0], int(M * max(2.0, target_s / max(dt, 1e-3) * 0.8)))
-    return {"value": M / dt, "unit": "points/s", "cores": oracle.num_threads(), "kind": "oracle",
+    cores = oracle.num_threads()
+    # the same on one thread, beside the paper's single-thread timings
+    m1 = min(M, 200_000)
+    X1, l1 = X_host[:m1].astype(np.float64), labels_host[:m1]
+    oracle.set_num_threads(1)
+    try:
+        t0 = time.perf_counter()
+        oracle.linear(X1, l1, K, metric)
+        d1 = time.perf_counter() - t0
+    finally:
+        oracle.set_num_threads(cores)
+    return {"value": M / dt, "unit": "points/s", "cores": cores, "kind": "oracle",
             "sample": f"first {M} rows of the workload as a dataset of their own: FP64 aggregates "
                       f"(Eq. 6/8) + linear scoring (Eq. 11) of every sampled point, {dt:.2f} s",
-            "S_sample": r["S"]}
+            "S_sample": r["S"],
+            "single_thread": {"value": m1 / d1, "unit": "points/s", "cores": 1,
+                              "sample": f"first {m1} rows, the same oracle on one thread, {d1:.2f} s"}}
 
 
 def run_reference(args):

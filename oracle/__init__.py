@@ -58,6 +58,8 @@ def bind(path: str):
                       ctypes.POINTER(ctypes.c_int64))
     i64, i32, ci = ctypes.c_int64, ctypes.c_int32, ctypes.c_int
     lib.oracle_num_threads.restype = ci
+    lib.oracle_set_num_threads.argtypes = [ci]
+    lib.oracle_set_num_threads.restype = None
     lib.oracle_aggregate.argtypes = [dp, i64, i32, ip32, i32, ci, ip64, dp, dp]
     lib.oracle_aggregate.restype = ci
     lib.oracle_bruteforce.argtypes = [dp, i64, i32, ip32, i32, ci, dp, dp, dp, ip32, dp]
@@ -96,6 +98,11 @@ def _prep(X, labels):
 def num_threads() -> int:
     """OpenMP threads the oracle uses."""
     return int(_load().oracle_num_threads())
+
+
+def set_num_threads(n: int) -> None:
+    """Run the oracle's loops on ``n`` threads from now on (1: single thread)."""
+    _load().oracle_set_num_threads(int(n))
 
 
 def aggregate(X, labels, K: int, metric: str = "sqeuclidean", lib=None):

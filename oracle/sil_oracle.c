@@ -71,6 +71,15 @@ int oracle_num_threads(void) {
 #endif
 }
 
+/* Threads of the OpenMP loops below from now on (n >= 1; 1 = one thread). */
+void oracle_set_num_threads(int n) {
+#ifdef _OPENMP
+  if (n > 0) omp_set_num_threads(n);
+#else
+  (void)n;
+#endif
+}
+
 static int check_labels(const int32_t* labels, int64_t N, int32_t K) {
   for (int64_t i = 0; i < N; ++i)
     if (labels[i] < 0 || labels[i] >= K) return ORACLE_ELABEL;

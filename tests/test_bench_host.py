@@ -69,3 +69,18 @@ def test_reference_arm_under_torchrun_prints_from_rank_zero_only():
     assert len(lines) == 1, r.stdout[-2000:]
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["n_gpus"] == 2
+
+
+def test_cpu_baseline_reports_all_cores_and_one_thread():
+    import numpy as np
+    import oracle
+    from paper_2303_14102_gb300 import synth
+    w = synth.workload_at_scale(N=30_000)
+    cores = oracle.num_threads()
+    cb = bench.cpu_oracle_sample(w.X.numpy(), w.labels.numpy(), w.K, target_s=0.5)
+    assert cb["kind"] == "oracle" and cb["cores"] == cores and cb["value"] > 0
+    one = cb["single_thread"]
+    assert one["cores"] == 1 and one["value"] > 0 and one["unit"] == "points/s"
+    assert oracle.num_threads() == cores  # the thread count is put back
+    ref = oracle.linear(w.X.numpy().astype(np.float64), w.labels.numpy(), w.K)
+    assert abs(cb["S_sample"] - ref["S"]) < 1e-12
