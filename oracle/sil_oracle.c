@@ -42,7 +42,10 @@
  *   - fewer than two non-empty clusters: S is NaN, status ORACLE_EDEGENERATE;
  *   - ties in the argmin for b_i go to the lowest cluster index;
  *   - a == b takes the a <= b branch of Eq. 2 (both give 0);
- *   - Eq. 15 normalises by the norm of X_i (the printed ||X|| is a typo).
+ *   - Eq. 15 normalises by the norm of X_i (the printed ||X|| is a typo);
+ *   - the Euclidean approximation of the Limitations section takes the square
+ *     root of each point-to-cluster mean of SQUARED distances (own cluster
+ *     over n_c - 1 as above); a negative rounding residue of that mean is 0.
  */
 #include <math.h>
 #include <stdint.h>
