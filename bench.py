@@ -35,6 +35,88 @@ WORKLOAD = {"workload": "at_scale Gaussian blobs, sq-Euclidean", "N": 10_000_000
             "sizes": "rank-Zipf(1.1)", "storage": "fp32"}
 
 
+def bench_config(N, D, world):
+    """The `config` object of both arms' lines (the same workload)."""
+    return dict(WORKLOAD, N=N, parallelism="replicas" if world > 1 else "single",
+                l2=f"inputs ({N * (4 * D + 4) / 1e9:.2f} GB) larger than L2 (129 MB); no flush")
+
+
+def oracle_full(X64, labels, K, metric, S_gpu):
+    """|S_gpu - S| with S the FP64 oracle's linear form over every row."""
+    import oracle
+    ref = oracle.linear(X64, labels, K, metric)
+    return {"dS_vs_oracle": abs(S_gpu - ref["S"]), "oracle_S": ref["S"], "rows": int(X64.shape[0]),
+            "kind": "FP64 linear form over all rows"}
+
+
+def oracle_sampled(X_dev, labels_dev, K, metric, s_gpu, S_gpu, col_scale=None, rows=20_000, seed=2030):
+    """Error against the FP64 oracle where its linear form over every row would take minutes:
+    FP64 aggregates of all rows, then the oracle's s_i of `rows` seeded rows against the GPU's.
+    S_gpu is the mean of the GPU's s_i, so its distance from the oracle's full-N S is the mean of
+    the per-row differences, which the paired sample estimates (bound = |mean| + 5 standard errors)."""
+    import numpy as np
+    import torch
+    import oracle
+    N, D = X_dev.shape
+
+    def deq(t):
+        x = t.detach().cpu().to(torch.float64)
+        if col_scale is not None:
+            x = x * col_scale.detach().cpu().to(torch.float64)[None, :]
+        return x.numpy()
+
+    count = np.zeros(K, np.int64)
+    s1 = np.zeros((K, D), np.float64)
+    s2 = np.zeros(K, np.float64)
+    step = 4_000_000
+    for lo in range(0, N, step):
+        hi = min(N, lo + step)
+        part = oracle.aggregate(deq(X_dev[lo:hi]), labels_dev[lo:hi].cpu().numpy(), K, metric)
+        count += part[0]
+        s1 += part[1]
+        s2 += part[2]
+    idx = np.sort(np.random.default_rng(seed).choice(N, min(rows, N), replace=False))
+    it = torch.as_tensor(idx, device=X_dev.device)
+    sub = oracle.linear(deq(X_dev[it]), labels_dev[it].cpu().numpy(), K, metric, agg=(count, s1, s2),
+                        idx=np.arange(idx.shape[0]))
+    diff = s_gpu[it].detach().cpu().double().numpy() - sub["s"]
+    se = float(np.std(diff)) / np.sqrt(diff.size)
+    return {"dS_vs_oracle": abs(float(np.mean(diff))) + 5 * se, "max_abs_ds_i": float(np.abs(diff).max()),
+            "mean_ds_i": float(np.mean(diff)), "se_mean_ds_i": se,
+            "S_minus_mean_s_i": abs(S_gpu - float(s_gpu.double().mean())), "rows": int(N),
+            "rows_scored_by_oracle": int(idx.size),
+            "kind": "bound |mean| + 5 SE of paired per-row differences (FP64 aggregates of all rows)"}
+
+
+TRAFFIC_RECORD = os.path.join(ROOT, "profiles", "dram_traffic.json")
+
+
+def source_digest(paths):
+    """sha256 over the named source files (repository-relative), in order."""
+    import hashlib
+    h = hashlib.sha256()
+    for p in paths:
+        with open(os.path.join(ROOT, p), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def measured_traffic(kname, N, D, K, dtype):
+    """DRAM bytes (read + write) of one launch of the dominant kernel, from the
+    committed ncu capture of the same kernel on this recipe, scaled by rows --
+    only while the kernel's sources are byte-identical to those captured."""
+    import torch
+    if not os.path.exists(TRAFFIC_RECORD):
+        return None, "no ncu capture recorded"
+    rec = json.load(open(TRAFFIC_RECORD)).get(kname.split(" ")[0])
+    if rec is None or (D, K) != (rec["D"], rec["K"]) or dtype != torch.float32:
+        return None, "no ncu capture of this kernel on this recipe"
+    if source_digest(rec["sources"]) != rec["sha256"]:
+        return None, "kernel sources changed since the ncu capture"
+    return rec["dram_bytes"] / rec["rows"] * N, (f"ncu dram__bytes_read.sum + dram__bytes_write.sum of one "
+                                                 f"launch at N = {rec['rows']}, scaled by rows ({rec['profile']})")
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -195,11 +277,12 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "points/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": dict(WORKLOAD, sample_rows=M),
+            "data": "synthetic", "config": bench_config(WORKLOAD["N"], WORKLOAD["D"], world),
             "cpu_baseline": {"value": v, "unit": "points/s", "cores": oracle.num_threads(),
                              "kind": "oracle",
-                             "sample": f"{M} points of the at_scale recipe per step: FP64 aggregates + "
-                                       f"linear scoring on the host cores"},
+                             "sample": f"each step scores the first {M} points of the at_scale recipe as a "
+                                       f"dataset of their own: FP64 aggregates + linear scoring on the host "
+                                       f"cores; points/s is rows scored / time"},
             "e2e": {"value": v, "unit": "points/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -251,12 +334,14 @@ def variant_lines(dev, steps, budget_s, pk_sustained):
             n = max(1, min(steps, 3))
             t1 = timed(lambda: sil.aggregate(Xs, lab, K, col_scale=sc, out=agg, status=st), n, stream) / n
             t2 = timed(lambda: sil.score(Xs, lab, K, agg, col_scale=sc, status=st), n, stream) / n
-            r = sil.score(Xs, lab, K, agg, col_scale=sc, status=st)
+            r = sil.score(Xs, lab, K, agg, col_scale=sc, want_s=True, status=st)
             torch.cuda.synchronize()
             sil.check_status(st, "precision " + name)
+            check = oracle_sampled(Xs, lab, K, "sqeuclidean", r.s, float(r.S.item()), col_scale=sc)
             plan = sil.tensor_plan(Xs.dtype, Xs.shape[1], K)
             entry = {"points_per_s": N / (t1 + t2), "ms": (t1 + t2) * 1e3, "pass1_ms": t1 * 1e3,
-                     "pass2_ms": t2 * 1e3, "S": float(r.S.item()),
+                     "pass2_ms": t2 * 1e3, "S": float(r.S.item()), "dS_vs_oracle": check["dS_vs_oracle"],
+                     "oracle_check": check,
                      "pass1_hbm_gbs": Xs.numel() * Xs.element_size() / t1 / 1e9 + N * 4 / t1 / 1e9,
                      "pass2_useful_tflops": 2.0 * N * K * Xs.shape[1] / t2 / 1e12}
             if plan is not None:
@@ -268,6 +353,7 @@ def variant_lines(dev, steps, budget_s, pk_sustained):
                               "pass2_tensor_frac_of_measured_bf16": mma_flops / t2 / 1e12
                               / pk_sustained})
             res[name] = entry
+            del r
         if "fp32" in res:
             for name in ("bf16", "fp8_e4m3"):
                 if name in res:
@@ -296,8 +382,11 @@ def variant_lines(dev, steps, budget_s, pk_sustained):
                 bw.append(timed(S.backward, 1, torch.cuda.current_stream()))
             tb = statistics.median(bw)
             nbytes = 3.0 * X.shape[0] * X.shape[1] * 4
+            rf = sil.silhouette(X, lab, w.K, metric, want_s=True)  # the forward's kernels, with s_i kept
+            check = oracle_sampled(X, lab, w.K, metric, rf.s, float(rf.S.item()))
             out[f"fwd_bwd_grad_{metric}"] = {"ms": s / n * 1e3, "bwd_ms": tb * 1e3, "bwd_hbm_gbs": nbytes / tb / 1e9,
-                                             "N": 1_000_000, "D": 256, "K": 1000}
+                                             "N": 1_000_000, "D": 256, "K": 1000,
+                                             "dS_vs_oracle": check["dS_vs_oracle"], "oracle_check": check}
         del X, lab, w
         torch.cuda.empty_cache()
     # batched labelings (N=2e6, D=32, B=256, k ~ U{2..512}): every labeling's
@@ -313,7 +402,19 @@ def variant_lines(dev, steps, budget_s, pk_sustained):
         g = sil.BatchedGraph(X, labs, ks)
         g.run()
         s = timed(g.run, max(1, min(steps, 3)), torch.cuda.current_stream()) / max(1, min(steps, 3))
+        S_all = g.run().cpu().numpy()
+        import numpy as np
+        import oracle
+        X64 = X.cpu().double().numpy()
+        order = np.argsort(ks)
+        picks = sorted({0, int(order[len(ks) // 2]), len(ks) - 1})
+        dS = {int(b): abs(float(S_all[b]) - oracle.linear(X64, labs[b].cpu().numpy(), ks[b])["S"]) for b in picks}
+        del X64
         out["batched"] = {"labelings_per_s": len(ks) / s, "point_labelings_per_s": len(ks) * X.shape[0] / s,
+                          "dS_vs_oracle": max(dS.values()),
+                          "oracle_check": {"labelings": {str(b): {"k": ks[b], "dS": v} for b, v in dS.items()},
+                                           "kind": "FP64 linear form over all rows of the first, median-k "
+                                                   "and last labelings"},
                           "ms": s * 1e3, "ms_without_graph": s_loop * 1e3, "N": X.shape[0], "D": 32,
                           "B": len(ks), "sum_k": int(sum(ks)), "launch": "one CUDA graph per step",
                           "autotune": {"shapes": len(tuned), "seconds": t_tune,
@@ -432,9 +533,10 @@ def main():
         clk.mark(False)
         barrier(world)
         t = e0.elapsed_time(e1) / 1e3
-        # per-pass split (same launches, events between the two calls)
+        # per-pass split (same launches, events between the two calls), over
+        # at least half a second of steps so that the split is steady
         split = []
-        for _ in range(args.steps):
+        for _ in range(max(args.steps, int(0.5 / max(t / args.steps, 1e-6)) + 1)):
             step(record=split)
     clocks = clk.summary()
     t = max_over_ranks(t, world)
@@ -457,17 +559,9 @@ def main():
     else:
         kname, kbytes, kms = "k_gather_reduce_tma (pass 1)", bytes_pass1, ms_pass1
     achieved = kbytes / (kms / 1e3) / 1e9
-    # DRAM bytes (read + write) per launch from one ncu capture of the same
-    # kernels on this recipe at N = 2e6 (profiles/k_gather_reduce_tma_k_score_tc_at_scale_n2e6.md),
-    # scaled by rows; valid while those kernels are unchanged
-    traffic = None
-    per_row = {"k_score_tc (pass 2, tcgen05)": (520.155904e6 + 3.573760e6) / 2e6}
-    if (D, K) == (64, 100) and X.dtype == torch.float32 and kname in per_row:
-        traffic = per_row[kname] * N
+    traffic, traffic_source = measured_traffic(kname, N, D, K, X.dtype)
     roof = {"kernel": kname, "bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
-            "frac": achieved / pk["hbm_gbs"], "traffic": traffic,
-            "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum at N = 2e6, scaled by rows"
-                              if traffic is not None else None,
+            "frac": achieved / pk["hbm_gbs"], "traffic": traffic, "traffic_source": traffic_source,
             "peak_source": f"{pk['source']} copy bandwidth (burst)",
             "algorithmic": f"N*(4D+4) = {kbytes:.3e} B per launch",
             "timing": "CUDA events around the pass on the launching stream, mean over steps "
@@ -517,34 +611,45 @@ def main():
     if args.variants and rank == 0:
         # same workload: cosine, the approximate Euclidean form (square roots of
         # the mean squared distances in Eq. 2), and BF16 storage
-        for name, fn in (("cosine_fp32", lambda: sil.silhouette(X, lab, K, "cosine", status=status)),
-                         ("euclidean_rms_fp32",
-                          lambda: sil.silhouette(X, lab, K, "euclidean_rms", status=status))):
-            fn()
+        X64 = X.cpu().double().numpy()
+        lab_h = lab.cpu().numpy()
+        head_check = oracle_full(X64, lab_h, K, "sqeuclidean", S_val)
+        for name, metric in (("cosine_fp32", "cosine"), ("euclidean_rms_fp32", "euclidean_rms")):
+            fn = lambda: sil.silhouette(X, lab, K, metric, status=status)  # noqa: E731
+            rv = fn()
             s = timed(fn, args.steps, stream)
-            variants[name] = {"points_per_s": N * args.steps / s, "ms": s / args.steps * 1e3}
+            Sv = float(rv.S.item())
+            chk = oracle_full(X64, lab_h, K, metric, Sv)
+            variants[name] = {"points_per_s": N * args.steps / s, "ms": s / args.steps * 1e3, "S": Sv,
+                              "dS_vs_oracle": chk["dS_vs_oracle"], "oracle_check": chk}
         # pass 2 on the CUDA cores (FP32 FFMA against Z in shared memory), the
         # path the tensor-core kernel replaces at this K, for comparison
         agg_s = sil.aggregate(X, lab, K, status=status)
         fn = lambda: sil.score(X, lab, K, agg_s, path="simt", status=status)
-        fn()
+        rs = fn()
         s = timed(fn, args.steps, stream)
+        Ss = float(rs.S.item())
         variants["sqeuclidean_fp32_simt_pass2"] = {
             "ms": s / args.steps * 1e3, "hbm_gbs": N * (4 * D + 4) / (s / args.steps) / 1e9,
-            "fp32_tflops": 2.0 * N * K * D / (s / args.steps) / 1e12}
-        del agg_s
+            "fp32_tflops": 2.0 * N * K * D / (s / args.steps) / 1e12, "S": Ss,
+            "dS_vs_oracle": abs(Ss - head_check["oracle_S"])}
+        del agg_s, X64
         Xb = X.to(torch.bfloat16)
         fn = lambda: sil.silhouette(Xb, lab, K, status=status)  # noqa: E731
         rb = fn()
         s = timed(fn, args.steps, stream)
+        Sb = float(rb.S.item())
+        chk = oracle_full(Xb.cpu().double().numpy(), lab_h, K, "sqeuclidean", Sb)  # the stored BF16 values
         variants["sqeuclidean_bf16"] = {"points_per_s": N * args.steps / s, "ms": s / args.steps * 1e3,
-                                        "S": float(rb.S.item()), "S_fp32": S_val,
-                                        "dS_vs_fp32": abs(float(rb.S.item()) - S_val)}
+                                        "S": Sb, "S_fp32": S_val, "dS_vs_fp32": abs(Sb - S_val),
+                                        "dS_vs_oracle": chk["dS_vs_oracle"], "oracle_check": chk}
         del Xb
         torch.cuda.empty_cache()
         variants.update(variant_lines(dev, args.steps, budget_s=150.0,
                                       pk_sustained=pk["bf16_tflops_sustained"]))
 
+    if rank == 0 and not args.variants:
+        head_check = oracle_full(X.cpu().double().numpy(), lab.cpu().numpy(), K, "sqeuclidean", S_val)
     cpu = None
     if rank == 0 and world >= 1 and not args.no_cpu_baseline and args.gpus == 1:
         cpu = cpu_oracle_sample(X.cpu().numpy(), lab.cpu().numpy(), K)
@@ -558,9 +663,9 @@ def main():
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": t / args.steps * 1e3,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                 "data": "synthetic",
-                "config": dict(WORKLOAD, N=N, parallelism="replicas" if world > 1 else "single",
-                               l2=f"inputs ({N * (4 * D + 4) / 1e9:.2f} GB) larger than L2 (129 MB); no flush"),
-                "S": S_val, "passes": pass_info, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+                "config": bench_config(N, D, world),
+                "S": S_val, "dS_vs_oracle": head_check["dS_vs_oracle"], "oracle_check": head_check,
+                "passes": pass_info, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
                 "clocks": clocks, "gpu_launches": launches_per_step * args.steps,
                 "variants": variants}
         print(json.dumps(line))

@@ -89,7 +89,13 @@ typedef enum {
 typedef enum {
   SIL_PATH_AUTO = 0,   /* library picks from (k, d, dtype) */
   SIL_PATH_SIMT = 1,   /* FP32 FFMA with the centroids staged in shared memory */
-  SIL_PATH_TENSOR = 2  /* tcgen05 tensor-core GEMM with a fused epilogue */
+  SIL_PATH_TENSOR = 2, /* tcgen05 tensor-core GEMM with a fused epilogue: for
+                          float32 rows of 32..64 columns the TF32-ranked kernel
+                          (exact FP32 recompute of the candidates), otherwise
+                          the split-precision kernel below */
+  SIL_PATH_TENSOR_SPLIT = 3 /* the split-precision tensor-core kernel (BF16 hi/lo
+                               operands, ~FP32-accurate GEMM) for every shape it
+                               serves */
 } sil_path_t;
 
 /* Flags of sil_aggregate. */
@@ -193,13 +199,19 @@ int sil_score_batched(const void* X, int32_t dtype, int64_t n, int32_t d, int64_
  * Same arguments and results as sil_score (SIMT pass 2 only), minus ws and
  * ws_bytes.  Its scratch is one fixed device array inside the library
  * (about 1.1 MB, sized for k <= SIL_NOALLOC_MAX_K and d <= SIL_NOALLOC_MAX_D)
- * that the CUDA driver reserves on every device that loads the library and keeps
- * until the process exits; the call itself allocates nothing.  Larger k or d
- * return SIL_EUNSUPPORTED with nothing enqueued.  The first call on a device
- * looks up the array's device address (with that device current), so make
- * it before any stream capture starts.  All calls on a device share the
- * array: calls whose GPU work overlaps race and must be ordered by the
- * caller.  Each call clears what must start at zero and rewrites the rest.
+ * that stays reserved until the process exits.  The CUDA driver reserves it
+ * when it loads that part of the library on a device: with lazy module
+ * loading (the default of current drivers) during the first call on the
+ * device, with CUDA_MODULE_LOADING=EAGER when the library is loaded.  So a
+ * caller whose memory budget is fixed later makes one call at start-up;
+ * after it, calls on that device allocate nothing.  Larger k or d return
+ * SIL_EUNSUPPORTED with nothing enqueued.  The first call on a device (and
+ * the first after its context is destroyed and re-created, e.g. by
+ * cudaDeviceReset) looks up the array's device address with that device
+ * current, so make it before any stream capture starts.  All calls on a
+ * device share the array: calls whose GPU work overlaps race and must be
+ * ordered by the caller.  Each call clears what must start at zero and
+ * rewrites the rest.
  */
 int sil_score_noalloc(const void* X, int32_t dtype, int64_t n, int32_t d, int64_t ldx,
                       const float* col_scale, const int32_t* labels, int32_t k, int32_t dist,

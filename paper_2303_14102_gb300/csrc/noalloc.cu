@@ -8,24 +8,35 @@
 // and plugins whose host application forbids allocation on its hot path.  For
 // them this entry point keeps its scratch -- the centred centroids, the
 // per-cluster constants, the global centre, the per-CTA partial sums and the
-// status word -- in one fixed, file-scope device array that the CUDA driver
-// reserves when it loads this library and keeps until the process exits, on
-// every device that loads it.  The entry point itself calls no cudaMalloc,
-// cudaFree or allocating library routine.
+// status word -- in one fixed, file-scope device array.  The entry point
+// itself calls no cudaMalloc, cudaFree or allocating library routine.
+//
+// When the memory is reserved: the CUDA driver reserves the array when it
+// loads this file's module on a device.  With lazy module loading (the
+// default of current CUDA drivers) that is the first sil_score_noalloc call
+// on the device, whose address lookup loads the module; with
+// CUDA_MODULE_LOADING=EAGER it is when the library is loaded.  A caller whose
+// memory budget is fixed later should therefore make one call at start-up;
+// after it, calls on that device reserve nothing more, and the array stays
+// until the process exits.
 //
 // Limits and rules:
 //   - k <= SIL_NOALLOC_MAX_K (1024) and d <= SIL_NOALLOC_MAX_D (256); larger
 //     sizes return SIL_EUNSUPPORTED before anything is enqueued.  The array is
 //     sized for exactly that: about 1.1 MB.
-//   - The first call on a device looks the array's device address up (with
-//     that device current) and caches it; make that first call before any
-//     stream capture begins.
+//   - The first call on a device (and the first after the device's context
+//     was destroyed and re-created, e.g. by cudaDeviceReset, which gives the
+//     array a new address) looks the array's device address up with that
+//     device current and caches it per context; make that first call before
+//     any stream capture begins.
 //   - Every call on a device uses the same array.  Two calls whose work
 //     overlaps on the GPU (different streams, or different host threads
 //     without ordering) race on it and give wrong results; order them.
 //   - The array keeps the previous call's contents.  The only part that must
 //     start at zero, the status word, is cleared by each call; everything
 //     else is fully rewritten before it is read.
+#include <cuda.h>
+
 #include <mutex>
 
 #include "sil_internal.cuh"
@@ -53,17 +64,41 @@ static __device__ __align__(256) unsigned char g_sil_noalloc_scratch[kScratchByt
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 void* g_dev_ptr[kMaxDevices] = {};
+CUcontext g_dev_ctx[kMaxDevices] = {};
 
-// Device address of the scratch on the current device (looked up once).
+// The current CUDA context, through the driver entry point the runtime hands
+// out (no link-time dependency on the driver library); nullptr if unknown.
+CUcontext current_context() {
+  using Fn = CUresult (*)(CUcontext*);
+  static Fn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<Fn>(p);
+  });
+  CUcontext c = nullptr;
+  if (fn == nullptr || fn(&c) != CUDA_SUCCESS) return nullptr;
+  return c;
+}
+
+// Device address of the scratch on the current device, looked up once per
+// device and context (a re-created context gets the array at a new address).
 int scratch_address(unsigned char** out) {
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return SIL_ECUDA;
+  // nullptr before the runtime has made a context current: the lookup below
+  // then creates the primary context and the next call looks up once more
+  const CUcontext ctx = current_context();
   std::lock_guard<std::mutex> lock(g_mu);
-  if (g_dev_ptr[dev] == nullptr) {
+  if (g_dev_ptr[dev] == nullptr || ctx == nullptr || ctx != g_dev_ctx[dev]) {
     void* p = nullptr;
     if (cudaGetSymbolAddress(&p, g_sil_noalloc_scratch) != cudaSuccess || p == nullptr)
       return SIL_ECUDA;
     g_dev_ptr[dev] = p;
+    g_dev_ctx[dev] = ctx;
   }
   *out = static_cast<unsigned char*>(g_dev_ptr[dev]);
   return SIL_OK;

@@ -185,9 +185,15 @@ def test_precision_workload_full_size_sampled(storage):
     assert float(np.abs(s_gpu[idx] - sub["s"]).max()) <= TOL_SI
     # S is the FP64 mean of the s_i the kernel wrote ...
     assert abs(S_gpu - float(np.mean(s_gpu))) <= 1e-6
-    # ... and the oracle's sample mean estimates it to within its standard error
-    se = float(np.std(sub["s"])) / np.sqrt(idx.shape[0])
-    assert abs(S_gpu - sub["S"]) <= 1e-4 + 5 * se
+    # ... so its distance from the oracle's S over all 1e8 rows is the mean of
+    # the per-row differences s_i - s_i(oracle).  The sampled rows estimate
+    # that mean; the pairing cancels the spread of s_i itself, so five
+    # standard errors of the differences bound it far below the 1e-4 stated
+    # for the low-precision forms.  (The oracle's linear form over all 1e8
+    # rows at K = 1000 would take minutes of host time.)
+    diff = s_gpu[idx] - sub["s"]
+    se = float(np.std(diff)) / np.sqrt(diff.size)
+    assert abs(float(np.mean(diff))) + 5 * se <= 1e-4
 
 
 def test_fp32_d128_k256_uses_two_cluster_blocks():
