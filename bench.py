@@ -88,7 +88,7 @@ def oracle_sampled(X_dev, labels_dev, K, metric, s_gpu, S_gpu, col_scale=None, r
             "kind": "bound |mean| + 5 SE of paired per-row differences (FP64 aggregates of all rows)"}
 
 
-TRAFFIC_RECORD = os.path.join(ROOT, "profiles", "dram_traffic.json")
+TRAFFIC_RECORD = os.path.join(ROOT, "profiles", "dram_traffic_at_scale.json")
 
 
 def source_digest(paths):
@@ -300,8 +300,14 @@ def timed(fn, steps, stream):
     return ev0.elapsed_time(ev1) / 1e3
 
 
-def variant_lines(dev, steps, budget_s, pk_sustained):
+def num_sms_of(dev):
+    import torch
+    return torch.cuda.get_device_properties(dev).multi_processor_count
+
+
+def variant_lines(dev, steps, budget_s, pk_sustained, pk_sm_mhz):
     """Secondary measurements, each bounded in time."""
+    import numpy as np
     import torch
     from paper_2303_14102_gb300 import sil, synth
     from paper_2303_14102_gb300.autograd import silhouette_loss
@@ -387,6 +393,34 @@ def variant_lines(dev, steps, budget_s, pk_sustained):
             out[f"fwd_bwd_grad_{metric}"] = {"ms": s / n * 1e3, "bwd_ms": tb * 1e3, "bwd_hbm_gbs": nbytes / tb / 1e9,
                                              "N": 1_000_000, "D": 256, "K": 1000,
                                              "dS_vs_oracle": check["dS_vs_oracle"], "oracle_check": check}
+        del X, lab, w
+        torch.cuda.empty_cache()
+    # the exact (non-squared) Euclidean Silhouette by the quadratic method on
+    # the at_scale recipe at 20,000 points (the size the oracle's brute force
+    # checks in seconds); bound by the FP32 pipe: 3 D flop per pair (difference,
+    # square, sum) plus a square root
+    if left() > 0:
+        import oracle
+        w = synth.workload_at_scale(device=dev, N=20_000)
+        X, lab, K = w.X, w.labels, w.K
+        N, D = X.shape
+        fn = lambda: sil.score_euclidean(X, lab, K)  # noqa: E731
+        r = sil.score_euclidean(X, lab, K, want_s=True)
+        n = max(3, min(steps, 20))
+        fn()
+        s = timed(fn, n, torch.cuda.current_stream()) / n
+        ref = oracle.bruteforce(X.cpu().double().numpy(), lab.cpu().numpy(), K, "euclidean")
+        Se = float(r.S.item())
+        flops = 3.0 * D * N * N
+        peak = num_sms_of(dev) * 128 * 2 * pk_sm_mhz * 1e6 / 1e12
+        out["euclidean_exact_bruteforce"] = {
+            "ms": s * 1e3, "points_per_s": N / s, "pairs_per_s": N * N / s, "N": N, "D": D, "K": K, "S": Se,
+            "dS_vs_oracle": abs(Se - ref["S"]),
+            "max_abs_ds_i_vs_oracle": float(np.abs(r.s.cpu().double().numpy() - ref["s"]).max()),
+            "roofline": {"bound": "alu", "achieved": flops / s / 1e12, "peak": peak, "unit": "TFLOP/s",
+                         "frac": flops / s / 1e12 / peak,
+                         "peak_source": "derived: SMs x 128 FP32 lanes x 2 flop x max SM clock",
+                         "algorithmic": "3 D flop per ordered pair (N^2 pairs)"}}
         del X, lab, w
         torch.cuda.empty_cache()
     # batched labelings (N=2e6, D=32, B=256, k ~ U{2..512}): every labeling's
@@ -633,6 +667,15 @@ def main():
             "ms": s / args.steps * 1e3, "hbm_gbs": N * (4 * D + 4) / (s / args.steps) / 1e9,
             "fp32_tflops": 2.0 * N * K * D / (s / args.steps) / 1e12, "S": Ss,
             "dS_vs_oracle": abs(Ss - head_check["oracle_S"])}
+        # pass 2 on the TF32-ranked tensor-core kernel (exact FP32 recompute of
+        # a_i and of every candidate inside the TF32 error band)
+        fn = lambda: sil.score(X, lab, K, agg_s, path="tensor_tf32", status=status)  # noqa: E731
+        rt = fn()
+        s = timed(fn, args.steps, stream)
+        St = float(rt.S.item())
+        variants["sqeuclidean_fp32_tf32_pass2"] = {
+            "ms": s / args.steps * 1e3, "hbm_gbs": N * (4 * D + 4) / (s / args.steps) / 1e9, "S": St,
+            "dS_vs_oracle": abs(St - head_check["oracle_S"])}
         del agg_s, X64
         Xb = X.to(torch.bfloat16)
         fn = lambda: sil.silhouette(Xb, lab, K, status=status)  # noqa: E731
@@ -646,7 +689,7 @@ def main():
         del Xb
         torch.cuda.empty_cache()
         variants.update(variant_lines(dev, args.steps, budget_s=150.0,
-                                      pk_sustained=pk["bf16_tflops_sustained"]))
+                                      pk_sustained=pk["bf16_tflops_sustained"], pk_sm_mhz=pk["sm_max_mhz"]))
 
     if rank == 0 and not args.variants:
         head_check = oracle_full(X.cpu().double().numpy(), lab.cpu().numpy(), K, "sqeuclidean", S_val)

@@ -19,6 +19,8 @@
  *                       minimum over the other clusters, s_i and the mean S
  *   sil_score_backward  dS/dX with labels fixed (no counterpart in the paper)
  *   sil_score_batched   S for many labelings of the same points
+ *   sil_score_euclidean the exact (non-squared) Euclidean Silhouette by the
+ *                       quadratic method of Sec. II, for moderate n
  *
  * Conventions shared by every entry point
  *   - Every pointer named as "device" must be memory the current CUDA device
@@ -89,13 +91,13 @@ typedef enum {
 typedef enum {
   SIL_PATH_AUTO = 0,   /* library picks from (k, d, dtype) */
   SIL_PATH_SIMT = 1,   /* FP32 FFMA with the centroids staged in shared memory */
-  SIL_PATH_TENSOR = 2, /* tcgen05 tensor-core GEMM with a fused epilogue: for
-                          float32 rows of 32..64 columns the TF32-ranked kernel
-                          (exact FP32 recompute of the candidates), otherwise
-                          the split-precision kernel below */
-  SIL_PATH_TENSOR_SPLIT = 3 /* the split-precision tensor-core kernel (BF16 hi/lo
-                               operands, ~FP32-accurate GEMM) for every shape it
-                               serves */
+  SIL_PATH_TENSOR = 2, /* tcgen05 tensor-core GEMM with a fused epilogue: the
+                          split-precision kernel (BF16 hi/lo operands, a
+                          ~FP32-accurate GEMM) */
+  SIL_PATH_TENSOR_TF32 = 3 /* float32 rows of 32..64 columns only: clusters
+                              ranked by a TF32 GEMM on the rows as stored, then
+                              a_i and every cluster inside the GEMM's provable
+                              error band recomputed exactly in FP32 */
 } sil_path_t;
 
 /* Flags of sil_aggregate. */
@@ -184,6 +186,29 @@ int sil_score_batched(const void* X, int32_t dtype, int64_t n, int32_t d, int64_
                       const int32_t* k_host, int32_t batch, int32_t dist, double* S_out,
                       void* ws, size_t ws_bytes, uint32_t* dev_status, void* stream);
 
+/*
+ * The exact Euclidean Silhouette (d(x, y) = ||x - y||, not squared) by the
+ * standard quadratic method of Sec. II (Eq. 1-3 evaluated pair by pair), for
+ * the metric the linear method cannot serve exactly (Limitations section;
+ * SIL_EUCLIDEAN_RMS is that section's linear-time approximation).  O(n^2 d)
+ * work: meant for up to ~1e5 points.  For point i with label c:
+ *   a_i = sum over the other members j of c of ||x_i - x_j|| / (n_c - 1)
+ *   b_i = min over non-empty k != c of sum over j in k of ||x_i - x_j|| / n_k
+ *   s_i and S as in sil_score (s_out, S_out, saved with the same layout).
+ * Each distance is formed in FP32 from the coordinate differences (no
+ * expanded-form cancellation); per-cluster sums are FP32 over runs of at most
+ * 64 points and FP64 across them.  The rows are counting-sorted by label and
+ * gathered into FP32 inside the workspace (sil_euclidean_workspace_size
+ * bytes, 256-byte aligned).  d <= 128, otherwise SIL_EUNSUPPORTED.  A label
+ * outside [0, k) sets SIL_ELABEL (its row gets s_i = 0) and fewer than two
+ * non-empty clusters SIL_EDEGENERATE; either makes S NaN.  No aggregates are
+ * needed: the call is self-contained.
+ */
+size_t sil_euclidean_workspace_size(int64_t n, int32_t d, int32_t k);
+int sil_score_euclidean(const void* X, int32_t dtype, int64_t n, int32_t d, int64_t ldx, const float* col_scale,
+                        const int32_t* labels, int32_t k, float* s_out, double* S_out, void* saved, void* ws,
+                        size_t ws_bytes, uint32_t* dev_status, void* stream);
+
 /* Largest sizes sil_score_noalloc serves. */
 #define SIL_NOALLOC_MAX_K 1024
 #define SIL_NOALLOC_MAX_D 256
@@ -235,7 +260,20 @@ int sil_score_noalloc(const void* X, int32_t dtype, int64_t n, int32_t d, int64_
 int sil_tensor_plan(int32_t dtype, int32_t d, int32_t k, int32_t* block_k, int32_t* n_blocks);
 
 /*
- * Launch plans of the tensor-core pass 2 for one storage type and shape, for
+ * Which tensor-core kernels serve this storage type and shape (on 16-byte
+ * aligned X, labels and row stride; other inputs take the SIMT kernel): bit
+ * SIL_TENSOR_KERNEL_SPLIT for the split-precision kernel that SIL_PATH_AUTO
+ * and SIL_PATH_TENSOR run and whose launch plans the functions below
+ * describe, bit SIL_TENSOR_KERNEL_TF32 for the kernel of SIL_PATH_TENSOR_TF32.
+ * Host-only arithmetic; invalid arguments give 0.
+ */
+#define SIL_TENSOR_KERNEL_SPLIT 1
+#define SIL_TENSOR_KERNEL_TF32 2
+int sil_tensor_kernel(int32_t dtype, int32_t d, int32_t k);
+
+/*
+ * Launch plans of the split-precision tensor-core pass 2 (SIL_PATH_AUTO and
+ * SIL_PATH_TENSOR) for one storage type and shape, for
  * an autotuner.  sil_tensor_plan_candidates writes up to max_plans feasible
  * plans (host int32[max_plans][5]: block_k, A-operand buffers, raw X stages,
  * 1 if the centroids are staged in shared memory for the own-cluster term,

@@ -788,7 +788,7 @@ cudaError_t launch_gather_t(GatherK g, int64_t E, int slices, cudaStream_t st) {
   cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kGatherThreads, 0);
   if (e != cudaSuccess) return e;
   per_sm = std::max(1, per_sm);
-  const int64_t ctas = std::max<int64_t>(1, int64_t(kNumSMs) * per_sm / slices);
+  const int64_t ctas = std::max<int64_t>(1, int64_t(num_sms()) * per_sm / slices);
   const int64_t warps = ctas * (kGatherThreads / 32);
   g.wchunk = round_up(std::max<int64_t>(128, cdiv(E, warps * 4)), 32);
   g.nitems = cdiv(E, g.wchunk);
@@ -805,10 +805,10 @@ cudaError_t launch_gather_tma_t(GatherK g, const CUtensorMap& map, int64_t E, in
   auto fn = k_gather_reduce_tma<DT, CPL, WEIGHTED, COS>;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  const int64_t wtot = int64_t(kNumSMs) * warps;
+  const int64_t wtot = int64_t(num_sms()) * warps;
   g.wchunk = round_up(std::max<int64_t>(256, cdiv(E, wtot * 2)), 32);
   g.nitems = cdiv(E, g.wchunk);
-  const unsigned grid = unsigned(std::max<int64_t>(1, std::min<int64_t>(kNumSMs, cdiv(g.nitems, warps))));
+  const unsigned grid = unsigned(std::max<int64_t>(1, std::min<int64_t>(num_sms(), cdiv(g.nitems, warps))));
   fn<<<grid, warps * 32, smem, st>>>(g, map);
   return cudaGetLastError();
 }
@@ -847,12 +847,26 @@ cudaError_t launch_invnorm(const void* X, int32_t dtype, int64_t n, int32_t d, i
   if (n == 0) return cudaSuccess;
   const int esz = elem_bytes(dtype);
   const bool vec = (reinterpret_cast<uintptr_t>(X) % (4 * esz) == 0) && (ldx % 4 == 0);
-  const unsigned grid = unsigned(std::min<int64_t>(cdiv(n, 8), int64_t(kNumSMs) * 16));
+  const unsigned grid = unsigned(std::min<int64_t>(cdiv(n, 8), int64_t(num_sms()) * 16));
   switch (dtype) {
     case SIL_F32: k_invnorm<SIL_F32><<<grid, 256, 0, stream>>>(X, n, d, ldx, cs, vec, invnorm, status); break;
     case SIL_BF16: k_invnorm<SIL_BF16><<<grid, 256, 0, stream>>>(X, n, d, ldx, cs, vec, invnorm, status); break;
     default: k_invnorm<SIL_FP8_E4M3><<<grid, 256, 0, stream>>>(X, n, d, ldx, cs, vec, invnorm, status); break;
   }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_label_sort(const int32_t* labels, int64_t n, int32_t k, uint32_t* bcount, uint32_t* bstart,
+                              uint32_t* cursor, uint32_t* idx, uint32_t* status, cudaStream_t stream) {
+  if (n >= (int64_t(1) << 32)) return cudaErrorInvalidValue;
+  Entries en{n, k, labels, nullptr, nullptr, nullptr, status};
+  cudaError_t e = cudaMemsetAsync(bcount, 0, size_t(k) * 4, stream);
+  if (e != cudaSuccess) return e;
+  const unsigned grid = unsigned(std::max<int64_t>(1, std::min<int64_t>(cdiv(n, 256 * 8), int64_t(num_sms()) * 8)));
+  const size_t smem = k <= kHistSmem ? size_t(k) * 4 : 0;
+  k_bucket_count<<<grid, 256, smem, stream>>>(en, n, k, bcount);
+  k_bucket_scan<<<1, kScanThreads, 0, stream>>>(bcount, k, k, bstart, cursor, nullptr);
+  k_bucket_scatter<<<unsigned(cdiv(n, 256 * kScatterIPT)), 256, 0, stream>>>(en, n, k, cursor, idx, nullptr);
   return cudaGetLastError();
 }
 
@@ -868,7 +882,7 @@ cudaError_t launch_aggregate(const AggLaunch& L) {
   cudaError_t e = cudaMemsetAsync(L.bcount, 0, size_t(nb) * 4, L.stream);
   if (e != cudaSuccess) return e;
   {
-    const unsigned grid = unsigned(std::max<int64_t>(1, std::min<int64_t>(cdiv(E, 256 * 8), int64_t(kNumSMs) * 8)));
+    const unsigned grid = unsigned(std::max<int64_t>(1, std::min<int64_t>(cdiv(E, 256 * 8), int64_t(num_sms()) * 8)));
     const size_t smem = nb <= kHistSmem ? size_t(nb) * 4 : 0;
     k_bucket_count<<<grid, 256, smem, L.stream>>>(en, E, nb, L.bcount);
   }

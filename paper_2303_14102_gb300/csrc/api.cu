@@ -2,11 +2,28 @@
 // workspace carving and the sequence of kernel launches of each entry point.
 // No allocation, no synchronisation: every call only enqueues work on the
 // caller's stream.
+#include <atomic>
 #include <cmath>
 
 #include "sil_internal.cuh"
 
 namespace sil {
+
+int num_sms() {
+  constexpr int kMaxDev = 64;
+  static std::atomic<int> cache[kMaxDev];  // 0 = not queried yet
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) return 1;
+  if (dev < kMaxDev) {
+    const int c = cache[dev].load(std::memory_order_relaxed);
+    if (c > 0) return c;
+  }
+  int v = 0;
+  if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) return 1;
+  v = std::min(v, kMaxPartials);  // grids sized from it write one partial sum per CTA
+  if (dev < kMaxDev) cache[dev].store(v, std::memory_order_relaxed);
+  return v;
+}
 
 WsLayout ws_layout(int64_t n, int32_t d, int32_t k, int32_t dtype, int32_t dist, int32_t batch) {
   (void)dist;
@@ -35,8 +52,8 @@ WsLayout ws_layout(int64_t n, int32_t d, int32_t k, int32_t dtype, int32_t dist,
   L.bk = take((3 * 2 * K + 1) * 4);
   L.bidx = take(2 * N * 4);
   L.bw = take(2 * N * 4);
-  L.zbf = take(tc_pack_bytes(k, d));
-  L.tcp = take(tc_partial_bytes(n, d, k, dtype));
+  L.zbf = take(std::max(tc_pack_bytes(k, d), t32_pack_bytes(k, d)));
+  L.tcp = take(std::max(tc_partial_bytes(n, d, k, dtype), dtype == SIL_F32 ? t32_partial_bytes(n, d, k) : size_t(0)));
   L.batch = take(K * (size_t(d) + 2) * 8);
   L.total = o;
   return L;
@@ -153,8 +170,10 @@ int run_score(const void* X, int32_t dtype, int64_t n, int32_t d, int64_t ldx, c
               const int32_t* labels, int32_t k, int32_t dist, float* s_out, float* sa, float* sb,
               int32_t* skstar, int32_t path, void* ws, const WsLayout& L, cudaStream_t st,
               int32_t* np) {
-  const bool tc_ok = path != SIL_PATH_SIMT && tc_eligible(dtype, n, d, ldx, k, X, labels);
-  if (path == SIL_PATH_TENSOR && !tc_ok) return SIL_EUNSUPPORTED;
+  const bool tf32_ok = path == SIL_PATH_TENSOR_TF32 && t32_eligible(dtype, n, d, ldx, k, X, labels);
+  const bool tc_ok = (path == SIL_PATH_AUTO || path == SIL_PATH_TENSOR) &&
+                     tc_eligible(dtype, n, d, ldx, k, X, labels);
+  if ((path == SIL_PATH_TENSOR && !tc_ok) || (path == SIL_PATH_TENSOR_TF32 && !tf32_ok)) return SIL_EUNSUPPORTED;
   ScoreLaunch s{};
   s.X = X;
   s.dtype = dtype;
@@ -176,6 +195,9 @@ int run_score(const void* X, int32_t dtype, int64_t n, int32_t d, int64_t ldx, c
   s.n_partials = np;
   s.status = at<uint32_t>(ws, L.misc);
   s.stream = st;
+  if (tf32_ok)
+    return cu(launch_score_tf32(s, at<double>(ws, L.g), at<void>(ws, L.zbf), at<void>(ws, L.tcp),
+                                L.batch - L.tcp, s.status));
   if (tc_ok)
     return cu(launch_score_tc(s, at<double>(ws, L.g), at<void>(ws, L.zbf), at<void>(ws, L.tcp),
                               L.batch - L.tcp, s.status));
@@ -217,7 +239,7 @@ int sil_score(const void* X, int32_t dtype, int64_t n, int32_t d, int64_t ldx,
               uint32_t* dev_status, void* stream) {
   SIL_TRY(check_common(X, dtype, n, d, ldx, col_scale, labels, k, dist));
   if (!count || !s1 || !s2) return SIL_EINVAL;
-  if (path < SIL_PATH_AUTO || path > SIL_PATH_TENSOR) return SIL_EINVAL;
+  if (path < SIL_PATH_AUTO || path > SIL_PATH_TENSOR_TF32) return SIL_EINVAL;
   SIL_TRY(check_ws(ws, ws_bytes, n, d, k, dtype, dist, 1));
   const WsLayout L = ws_layout(n, d, k, dtype, dist, 1);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -365,10 +387,45 @@ int sil_score_batched(const void* X, int32_t dtype, int64_t n, int32_t d, int64_
   return SIL_OK;
 }
 
+size_t sil_euclidean_workspace_size(int64_t n, int32_t d, int32_t k) {
+  if (n < 0 || d <= 0 || k <= 0) return 0;
+  return euclid_ws_bytes(n, d, k);
+}
+
+int sil_score_euclidean(const void* X, int32_t dtype, int64_t n, int32_t d, int64_t ldx, const float* col_scale,
+                        const int32_t* labels, int32_t k, float* s_out, double* S_out, void* saved, void* ws,
+                        size_t ws_bytes, uint32_t* dev_status, void* stream) {
+  SIL_TRY(check_common(X, dtype, n, d, ldx, col_scale, labels, k, SIL_SQEUCLIDEAN));
+  if (!S_out) return SIL_EINVAL;
+  if (d > euclid_max_d()) return SIL_EUNSUPPORTED;
+  if (ws == nullptr || (reinterpret_cast<uintptr_t>(ws) & 255u) != 0 || ws_bytes < euclid_ws_bytes(n, d, k))
+    return SIL_EWORKSPACE;
+  float* sa = nullptr;
+  float* sb = nullptr;
+  int32_t* skstar = nullptr;
+  if (saved) {
+    sa = static_cast<float*>(saved);
+    sb = sa + n;
+    skstar = reinterpret_cast<int32_t*>(sb + n);
+  }
+  return cu(launch_euclid(X, dtype, n, d, ldx, col_scale, labels, k, s_out, sa, sb, skstar, ws, dev_status, S_out,
+                          static_cast<cudaStream_t>(stream)));
+}
+
 int sil_tensor_plan(int32_t dtype, int32_t d, int32_t k, int32_t* block_k, int32_t* n_blocks) {
   if (!block_k || !n_blocks || d <= 0 || k <= 0) return SIL_EINVAL;
   if (dtype < SIL_F32 || dtype > SIL_FP8_E4M3) return SIL_EINVAL;
   return tc_plan_query(dtype, d, k, block_k, n_blocks) ? SIL_OK : SIL_EUNSUPPORTED;
+}
+
+int sil_tensor_kernel(int32_t dtype, int32_t d, int32_t k) {
+  if (d <= 0 || k <= 0 || dtype < SIL_F32 || dtype > SIL_FP8_E4M3) return 0;
+  int out = t32_serves(dtype, d, k) ? SIL_TENSOR_KERNEL_TF32 : 0;
+  int32_t bk = 0, nb = 0;
+  const bool box_ok = (dtype == SIL_F32 && d >= 32) || (dtype == SIL_BF16 && d >= 64) ||
+                      (dtype == SIL_FP8_E4M3 && d == 128);
+  if (box_ok && tc_plan_query(dtype, d, k, &bk, &nb)) out |= SIL_TENSOR_KERNEL_SPLIT;
+  return out;
 }
 
 int sil_tensor_plan_candidates(int32_t dtype, int32_t d, int32_t k, int32_t* plans, int32_t max_plans,

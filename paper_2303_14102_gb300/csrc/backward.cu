@@ -230,7 +230,7 @@ bool vec_ok_b(const void* X, int32_t dtype, int64_t ldx) {
 
 cudaError_t launch_backward_weights(const BackLaunch& b, float* w1, float* w2) {
   if (b.n == 0) return cudaSuccess;
-  const unsigned grid = unsigned(std::min<int64_t>(cdiv(b.n, 256), int64_t(kNumSMs) * 8));
+  const unsigned grid = unsigned(std::min<int64_t>(cdiv(b.n, 256), int64_t(num_sms()) * 8));
   k_bw_weights<<<grid, 256, 0, b.stream>>>(b.n, b.labels, b.k, b.cl, b.sa, b.sb, b.skstar, w1, w2);
   return cudaGetLastError();
 }
@@ -268,7 +268,7 @@ cudaError_t launch_backward_grad(const BackLaunch& b, const float* Wf, const flo
   g.dX = b.dX;
   g.lddx = b.lddx;
   g.vec_out = (reinterpret_cast<uintptr_t>(b.dX) % 16 == 0) && (b.lddx % 4 == 0);
-  const unsigned grid = unsigned(std::min<int64_t>(cdiv(b.n, 8), int64_t(kNumSMs) * 16));
+  const unsigned grid = unsigned(std::min<int64_t>(cdiv(b.n, 8), int64_t(num_sms()) * 16));
   switch (b.dtype) {
     case SIL_F32: k_bw_grad<SIL_F32><<<grid, 256, 0, b.stream>>>(g); break;
     case SIL_BF16: k_bw_grad<SIL_BF16><<<grid, 256, 0, b.stream>>>(g); break;

@@ -470,7 +470,7 @@ cudaError_t launch_simt_t(ScoreK& k, cudaStream_t stream, int32_t* np) {
   if (e != cudaSuccess) return e;
   const int64_t groups = cdiv(k.n, int64_t(kScoreThreads) * PPT);
   const int per_sm = std::max(1, std::min(2, (220 * 1024) / smem));
-  const int grid = int(std::max<int64_t>(1, std::min<int64_t>(groups, int64_t(kNumSMs) * per_sm)));
+  const int grid = int(std::max<int64_t>(1, std::min<int64_t>(std::min<int64_t>(groups, int64_t(num_sms()) * per_sm), kMaxPartials)));
   fn<<<grid, kScoreThreads, smem, stream>>>(k);
   *np = grid;
   return cudaGetLastError();
@@ -490,7 +490,7 @@ cudaError_t launch_wide_t(ScoreK& k, cudaStream_t stream, int32_t* np) {
   if (e != cudaSuccess) return e;
   const int64_t groups = cdiv(k.n, 64);
   const int per_sm = std::max(1, std::min(8, (220 * 1024) / smem));
-  const int grid = int(std::max<int64_t>(1, std::min<int64_t>(groups, int64_t(kNumSMs) * per_sm)));
+  const int grid = int(std::max<int64_t>(1, std::min<int64_t>(std::min<int64_t>(groups, int64_t(num_sms()) * per_sm), kMaxPartials)));
   fn<<<grid, 64, smem, stream>>>(k);
   *np = grid;
   return cudaGetLastError();

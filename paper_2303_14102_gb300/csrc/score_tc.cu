@@ -60,6 +60,7 @@
 #include <vector>
 
 #include "sil_internal.cuh"
+#include "tcgen05.cuh"
 #include "tma.cuh"
 
 namespace sil {
@@ -102,76 +103,6 @@ constexpr int kSideSlots = 4;  // row-term ring of the modes whose converters wr
 constexpr int kOwnElsewhere = -1;
 constexpr int kRowInvalid = -0x7fffffff - 1;
 
-// ------------------------------------------------------------ tcgen05 PTX
-__device__ __forceinline__ uint64_t umma_desc_sw128(uint32_t saddr) {
-  // K-major, 128-byte swizzle: 8-row groups 1024 bytes apart (SBO), version 1.
-  return uint64_t((saddr >> 4) & 0x3FFF) | (uint64_t(1) << 16) | (uint64_t(1024 >> 4) << 32) |
-         (uint64_t(1) << 46) | (uint64_t(2) << 61);
-}
-
-// K-major, 64-byte swizzle (rows of 32 BF16): 8-row groups 512 bytes apart.
-__device__ __forceinline__ uint64_t umma_desc_sw64(uint32_t saddr) {
-  return uint64_t((saddr >> 4) & 0x3FFF) | (uint64_t(1) << 16) | (uint64_t(512 >> 4) << 32) |
-         (uint64_t(1) << 46) | (uint64_t(4) << 61);
-}
-
-__host__ __device__ constexpr uint32_t umma_idesc_bf16(int M, int N) {
-  return (1u << 4)                     // D: FP32
-         | (1u << 7)                   // A: BF16
-         | (1u << 10)                  // B: BF16
-         | ((uint32_t(N) >> 3) << 17)  // N / 8
-         | ((uint32_t(M) >> 4) << 24); // M / 16
-}
-
-__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
-                                          uint32_t accumulate) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "setp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-      "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
-      : "memory");
-}
-
-__device__ __forceinline__ void umma_commit(uint64_t* bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                   smem_u32(bar))
-               : "memory");
-}
-
-__device__ __forceinline__ void tc_fence_before() {
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-}
-__device__ __forceinline__ void tc_fence_after() {
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-}
-
-// Start loading 16 consecutive accumulator columns of this warp's 32 lanes;
-// the registers are valid only after tmem_wait_ld() and reg_fence16().
-__device__ __forceinline__ void tmem_ld16_async(uint32_t taddr, uint32_t (&r)[16]) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
-      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-        "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
-}
-
-__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
-
-// Ties the registers to the preceding wait so no use is scheduled before it.
-__device__ __forceinline__ void reg_fence16(uint32_t (&r)[16]) {
-  asm volatile(""
-               : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]),
-                 "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]),
-                 "+r"(r[14]), "+r"(r[15]));
-}
-
-// Byte offset of 16-byte chunk q of row r inside a 128-byte-swizzled block.
-__device__ __forceinline__ int sw128(int r, int q) { return r * 128 + ((q ^ (r & 7)) << 4); }
-// ... and inside a 64-byte-swizzled block (rows of 64 bytes, 512-byte atoms).
-__device__ __forceinline__ int sw64(int r, int q) { return r * 64 + ((q ^ ((r >> 1) & 3)) << 4); }
 
 __device__ __forceinline__ uint32_t pack_bf16x2(float lo_elem, float hi_elem) {
   // element with the lower column index goes to the low half
@@ -493,22 +424,6 @@ __device__ inline TcBars tc_bars(unsigned char* base, const TcSmem& L, int nxs, 
   return b;
 }
 
-// Bounded wait that also notices another role's abort.
-__device__ __forceinline__ bool tc_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
-                                        uint32_t* status) {
-  const uint32_t a = smem_u32(bar);
-  if (mbar_try_wait(a, parity)) return true;
-  const uint64_t t0 = globaltimer_ns();
-  while (!mbar_try_wait(a, parity)) {
-    if (*abort_flag) return false;
-    if (globaltimer_ns() - t0 > kWaitTimeoutNs) {
-      *abort_flag = 1;
-      set_status(status, SIL_ETIMEOUT);
-      return false;
-    }
-  }
-  return true;
-}
 
 // Self-test of failure detection without a fault: one CTA waits on mbarriers
 // that nothing completes, through the production waits.  Warp 0 runs tc_wait
@@ -1820,7 +1735,7 @@ cudaError_t launch_score_tc(const ScoreLaunch& s, const double* g, void* pack, v
     k.pown = reinterpret_cast<float*>(p + 2 * align256(G * N * 4));
   }
   const int64_t ntiles = cdiv(s.n, kTM);
-  const int per_block = std::max(1, kNumSMs / plan.nblk);
+  const int per_block = std::max(1, num_sms() / plan.nblk);
   const dim3 grid(unsigned(std::min<int64_t>(ntiles, per_block)), unsigned(plan.nblk));
   const int cg = dp == 256 ? 1 : tc_conv_groups(mode, dp, kp);
   const int threads = dp == 256 ? kTcThreads : tc_threads(dp, cg);
@@ -1854,11 +1769,18 @@ cudaError_t launch_score_tc(const ScoreLaunch& s, const double* g, void* pack, v
     *s.n_partials = int(grid.x);
     return cudaSuccess;
   }
-  const int cgrid = int(std::max<int64_t>(1, std::min<int64_t>(cdiv(s.n, 256), kMaxPartials)));
-  k_tc_combine<<<cgrid, 256, 0, s.stream>>>(s.n, s.k, plan.nblk, s.labels, s.cl, k.scale, k.rms, k.pmin,
-                                            save ? k.parg : nullptr, k.pown, s.s_out, s.sa, s.sb, s.skstar,
-                                            s.partials);
-  *s.n_partials = cgrid;
+  return launch_tc_combine(s.n, s.k, plan.nblk, s.labels, s.cl, k.scale, k.rms, k.pmin, save ? k.parg : nullptr,
+                           k.pown, s.s_out, s.sa, s.sb, s.skstar, s.partials, s.stream, s.n_partials);
+}
+
+cudaError_t launch_tc_combine(int64_t n, int32_t k, int32_t nblk, const int32_t* labels, const float4* cl,
+                              float scale, int32_t rms, const float* pmin, const int32_t* parg, const float* pown,
+                              float* s_out, float* sa, float* sb, int32_t* skstar, double* partials,
+                              cudaStream_t stream, int32_t* n_partials) {
+  const int cgrid = int(std::max<int64_t>(1, std::min<int64_t>(cdiv(n, 256), kMaxPartials)));
+  k_tc_combine<<<cgrid, 256, 0, stream>>>(n, k, nblk, labels, cl, scale, rms, pmin, parg, pown, s_out, sa, sb,
+                                          skstar, partials);
+  *n_partials = cgrid;
   return cudaGetLastError();
 }
 

@@ -20,12 +20,15 @@ namespace sil {
 
 constexpr int kScoreThreads = 256;   // threads per SIMT pass-2 CTA
 constexpr int kMaxPartials = 8192;   // per-CTA partial sums of s_i
-constexpr int kNumSMs = 152;         // GB300
 constexpr int kSmemBudget = 100 * 1024;  // dynamic shared memory per CTA we aim for
 
 __host__ __device__ inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 __host__ __device__ inline int64_t round_up(int64_t a, int64_t b) { return cdiv(a, b) * b; }
 inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// Streaming multiprocessors of the current device (queried once per device
+// and cached; 152 on a GB300).  Persistent grids are sized from it.
+int num_sms();
 
 // Eq. 2 from a point's mean distances a (own cluster) and b (nearest other
 // cluster), both >= 0: 0 when max(a, b) = 0.  With rms set, a and b are means
@@ -174,6 +177,19 @@ cudaError_t launch_invnorm(const void* X, int32_t dtype, int64_t n, int32_t d, i
 // Whether pass 1 splits the rows into column slices, so that the cosine norm
 // must come from launch_invnorm.
 bool agg_needs_invnorm(int32_t dtype, int32_t d);
+// Counting sort of the rows by label (the first steps of pass 1): bcount[k],
+// bstart[k + 1] (bstart[k] = rows with a valid label), cursor[k] scratch, idx
+// = row indices in label order; a label outside [0, k) sets SIL_ELABEL and its
+// row is left out.
+cudaError_t launch_label_sort(const int32_t* labels, int64_t n, int32_t k, uint32_t* bcount, uint32_t* bstart,
+                              uint32_t* cursor, uint32_t* idx, uint32_t* status, cudaStream_t stream);
+// The exact Euclidean Silhouette by the quadratic method: workspace bytes,
+// the largest d served, and the launch (s_out, sa/sb/skstar nullable).
+size_t euclid_ws_bytes(int64_t n, int32_t d, int32_t k);
+int euclid_max_d();
+cudaError_t launch_euclid(const void* X, int32_t dtype, int64_t n, int32_t d, int64_t ldx, const float* cs,
+                          const int32_t* labels, int32_t k, float* s_out, float* sa, float* sb, int32_t* skstar,
+                          void* ws, uint32_t* user_status, double* S_out, cudaStream_t st);
 // Enqueue pass 1 (outputs must be zeroed or hold sums to add to).
 cudaError_t launch_aggregate(const AggLaunch& a);
 
@@ -234,6 +250,23 @@ size_t tc_partial_bytes(int64_t n, int32_t d, int32_t k, int32_t dtype);
 cudaError_t launch_selftest_wait(uint32_t* out, cudaStream_t stream);
 cudaError_t launch_score_tc(const ScoreLaunch& s, const double* g, void* pack, void* partial_ws,
                             size_t partial_bytes, uint32_t* status);
+// Minimum over the cluster blocks of per-block nearest distances (pmin, parg:
+// [nblk][n]; pown: a_i from the own cluster's block), then Eq. 2 and one
+// partial sum per CTA (their number into *n_partials).
+cudaError_t launch_tc_combine(int64_t n, int32_t k, int32_t nblk, const int32_t* labels, const float4* cl,
+                              float scale, int32_t rms, const float* pmin, const int32_t* parg, const float* pown,
+                              float* s_out, float* sa, float* sb, int32_t* skstar, double* partials,
+                              cudaStream_t stream, int32_t* n_partials);
+// TF32-ranked tensor-core pass 2 for FP32 rows of 32..64 columns (b_i and a_i
+// exact in FP32): eligibility, bytes of its packed centroids and of its
+// per-block results inside the workspace, and the launch.
+bool t32_serves(int32_t dtype, int32_t d, int32_t k);  // host-only: the shape has a plan
+bool t32_eligible(int32_t dtype, int64_t n, int32_t d, int64_t ldx, int32_t k, const void* X,
+                  const int32_t* labels);
+size_t t32_pack_bytes(int32_t k, int32_t d);
+size_t t32_partial_bytes(int64_t n, int32_t d, int32_t k);
+cudaError_t launch_score_tf32(const ScoreLaunch& s, const double* g, void* pack, void* partial_ws,
+                              size_t partial_bytes, uint32_t* status);
 // S = sum(partials)/n, NaN when the workspace status word is non-zero; the
 // word is OR-ed into user_status.
 cudaError_t launch_reduce_S(const double* partials, int32_t np, int64_t n, const uint32_t* ws_status,

@@ -10,6 +10,7 @@ Entry points mirror the C names:
   score(X, labels, K, agg, ...)         -> Score(S, s, saved)  sil_score
   score_backward(X, labels, K, agg, ...)-> dX                  sil_score_backward
   score_batched(X, labels, ks, ...)     -> S[B]                sil_score_batched
+  score_euclidean(X, labels, K, ...)    -> Score(S, s, saved)  sil_score_euclidean (exact, O(N^2))
   silhouette(X, labels, K, ...)         -> S (aggregate + score)
   silhouette_chunked(X_host, labels_host, K, ...)
                                         -> S of host-resident data streamed in row chunks
@@ -38,10 +39,11 @@ SIL_AGG_ACCUMULATE = 1
 # "euclidean_rms": the square root of each point-to-cluster mean squared
 # Euclidean distance in Eq. 2 (the approximation of the Limitations section)
 METRICS = {"sqeuclidean": 0, "cosine": 1, "euclidean_rms": 2}
-PATHS = {"auto": 0, "simt": 1, "tensor": 2}
+PATHS = {"auto": 0, "simt": 1, "tensor": 2, "tensor_tf32": 3}
 EXPORTED = ("sil_workspace_size", "sil_saved_size", "sil_aggregate", "sil_score",
             "sil_score_backward", "sil_score_batched", "sil_tensor_plan", "sil_tensor_plan_candidates",
-            "sil_tensor_plan_set", "sil_score_noalloc", "sil_selftest_bounded_wait", "sil_status_string",
+            "sil_tensor_plan_set", "sil_tensor_kernel", "sil_score_noalloc", "sil_score_euclidean",
+            "sil_euclidean_workspace_size", "sil_selftest_bounded_wait", "sil_status_string",
             "sil_version")
 
 _lock = threading.Lock()
@@ -93,6 +95,12 @@ def load(build_if_stale: bool = True) -> ctypes.CDLL:
             lib.sil_tensor_plan_candidates.restype = ctypes.c_int
             lib.sil_tensor_plan_set.argtypes = [i32, i32, i32, i32, i32, i32, i32, i32]
             lib.sil_tensor_plan_set.restype = ctypes.c_int
+            lib.sil_score_euclidean.argtypes = [vp, i32, i64, i32, i64, vp, vp, i32, vp, vp, vp, vp, sz, vp, vp]
+            lib.sil_score_euclidean.restype = ctypes.c_int
+            lib.sil_euclidean_workspace_size.argtypes = [i64, i32, i32]
+            lib.sil_euclidean_workspace_size.restype = sz
+            lib.sil_tensor_kernel.argtypes = [i32, i32, i32]
+            lib.sil_tensor_kernel.restype = ctypes.c_int
             lib.sil_selftest_bounded_wait.argtypes = [vp, vp]
             lib.sil_selftest_bounded_wait.restype = ctypes.c_int
             lib.sil_status_string.argtypes = [i32]
@@ -350,6 +358,11 @@ def tensor_plan(dtype: torch.dtype, D: int, K: int):
 
 
 _DTYPES = {torch.float32: 0, torch.bfloat16: 1, torch.float8_e4m3fn: 2}
+def tensor_kernels(dtype: torch.dtype, D: int, K: int) -> set:
+    """Tensor-core kernels serving this shape: {"split"} (paths "auto" and
+    "tensor"), {"tf32"} (path "tensor_tf32"), both or neither."""
+    bits = int(load().sil_tensor_kernel(_DTYPES[dtype], D, K))
+    return {name for bit, name in ((1, "split"), (2, "tf32")) if bits & bit}
 
 
 def tensor_plan_candidates(dtype: torch.dtype, D: int, K: int, max_plans: int = 8):
@@ -372,12 +385,13 @@ def tensor_plan_set(dtype: torch.dtype, D: int, K: int, plan=None) -> None:
 
 def autotune(X: torch.Tensor, labels: torch.Tensor, K: int, metric: str = "sqeuclidean",
              col_scale: torch.Tensor | None = None, max_plans: int = 6, reps: int = 3):
-    """Time pass 2 under each of the best-modelled tensor-path plans for this
-    shape on these inputs and keep the fastest for the rest of the process.
+    """Time pass 2 under each of the best-modelled plans of the split-precision
+    tensor kernel for this shape on these inputs and keep the fastest for the
+    rest of the process.
 
-    Returns [(seconds per call, plan), ...] in the order tried (empty when the
-    tensor path does not serve the shape).  The timing runs the real kernels
-    on the caller's data; nothing is cached across processes.
+    Returns [(seconds per call, plan), ...] in the order tried (empty when that
+    kernel does not serve the shape).  The timing runs the real kernels on the
+    caller's data; nothing is cached across processes.
     """
     N, D = X.shape
     plans = tensor_plan_candidates(X.dtype, D, K, max_plans)
@@ -403,15 +417,38 @@ def autotune(X: torch.Tensor, labels: torch.Tensor, K: int, metric: str = "sqeuc
 
 def autotune_batched(X: torch.Tensor, labels: torch.Tensor, ks, metric: str = "sqeuclidean",
                      col_scale: torch.Tensor | None = None, max_plans: int = 4, reps: int = 2):
-    """:func:`autotune` for each distinct k of a batch of labelings (B x N),
-    on the first labeling with that k.  Returns {k: fastest plan}."""
+    """:func:`autotune` for each distinct k of a batch of labelings (B x N)
+    that the split-precision kernel serves, on the first labeling with that k.
+    Returns {k: fastest plan} (None where another kernel scores the shape)."""
     best = {}
     for b, k in enumerate(int(k) for k in ks):
         if k in best:
             continue
+        if "split" not in tensor_kernels(X.dtype, X.shape[1], k):
+            best[k] = None
+            continue
         res = autotune(X, labels[b], k, metric, col_scale=col_scale, max_plans=max_plans, reps=reps)
         best[k] = min(res)[1] if res else None
     return best
+
+
+def score_euclidean(X: torch.Tensor, labels: torch.Tensor, K: int, col_scale: torch.Tensor | None = None,
+                    want_s: bool = False, save: bool = False, status: torch.Tensor | None = None) -> Score:
+    """sil_score_euclidean: the exact (non-squared) Euclidean Silhouette by the
+    quadratic method (O(N^2 D); no aggregates needed)."""
+    _check_X(X, labels)
+    lib = load()
+    N, D = X.shape
+    S = torch.empty((), dtype=torch.float64, device=X.device)
+    s = torch.empty(N, dtype=torch.float32, device=X.device) if want_s else None
+    saved = torch.empty(int(lib.sil_saved_size(N)), dtype=torch.uint8, device=X.device) if save else None
+    need = int(lib.sil_euclidean_workspace_size(N, D, K))
+    ws = _WS.get(X.device, need)
+    rc = lib.sil_score_euclidean(_ptr(X), _dtype_code(X), N, D, X.stride(0), _ptr(col_scale), _ptr(labels), K,
+                                 _ptr(s), _ptr(S), _ptr(saved), _ptr(ws), need, _ptr(status),
+                                 _stream_handle(X.device))
+    _rc(rc, "sil_score_euclidean")
+    return Score(S=S, s=s, saved=saved)
 
 
 def silhouette(X: torch.Tensor, labels: torch.Tensor, K: int, metric: str = "sqeuclidean",

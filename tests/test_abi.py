@@ -209,3 +209,31 @@ def test_every_candidate_plan_is_one_the_library_accepts(dtype_name):
 
 def test_selftest_refuses_a_null_status_array(lib):
     assert lib.sil_selftest_bounded_wait(None, None) == sil.SIL_EINVAL
+
+
+def test_tensor_kernel_query(lib):
+    import torch
+    assert sil.tensor_kernels(torch.float32, 64, 100) == {"split", "tf32"}  # the at-scale shape
+    assert sil.tensor_kernels(torch.float32, 32, 512) == {"split", "tf32"}  # two cluster blocks
+    assert sil.tensor_kernels(torch.float32, 40, 7) == {"split", "tf32"}    # padded columns
+    assert sil.tensor_kernels(torch.float32, 128, 100) == {"split"}
+    assert sil.tensor_kernels(torch.float32, 256, 1000) == {"split"}        # 64-column chunks
+    assert sil.tensor_kernels(torch.bfloat16, 64, 100) == {"split"}
+    assert sil.tensor_kernels(torch.float8_e4m3fn, 128, 1000) == {"split"}
+    assert sil.tensor_kernels(torch.float8_e4m3fn, 64, 10) == set()
+    assert sil.tensor_kernels(torch.float32, 16, 100) == set()
+    assert sil.tensor_kernels(torch.float32, 257, 100) == set()
+    assert lib.sil_tensor_kernel(7, 64, 100) == 0 and lib.sil_tensor_kernel(0, 64, 0) == 0
+
+
+def test_exact_euclidean_argument_checks(lib):
+    vp = ctypes.c_void_p
+    fake = vp(256)  # never dereferenced: each call below is refused on the host
+    assert lib.sil_euclidean_workspace_size(1000, 64, 10) > lib.sil_euclidean_workspace_size(100, 64, 10) > 0
+    assert lib.sil_euclidean_workspace_size(1000, 0, 10) == 0
+    assert lib.sil_score_euclidean(fake, 0, 100, 129, 129, None, fake, 3, None, fake, None, fake, 1 << 30,
+                                   None, None) == sil.SIL_EUNSUPPORTED
+    assert lib.sil_score_euclidean(fake, 0, 100, 8, 8, None, fake, 3, None, None, None, fake, 1 << 30,
+                                   None, None) == sil.SIL_EINVAL
+    assert lib.sil_score_euclidean(fake, 0, 100, 8, 8, None, fake, 3, None, fake, None, None, 0,
+                                   None, None) == sil.SIL_EWORKSPACE

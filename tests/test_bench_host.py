@@ -84,3 +84,26 @@ def test_cpu_baseline_reports_all_cores_and_one_thread():
     assert oracle.num_threads() == cores  # the thread count is put back
     ref = oracle.linear(w.X.numpy().astype(np.float64), w.labels.numpy(), w.K)
     assert abs(cb["S_sample"] - ref["S"]) < 1e-12
+
+
+def test_traffic_record_is_used_only_for_unchanged_sources(tmp_path, monkeypatch):
+    import torch
+    rec = json.load(open(bench.TRAFFIC_RECORD))
+    entry = rec["k_score_tc"]
+    assert set(entry) >= {"D", "K", "rows", "dram_bytes", "sources", "sha256", "profile"}
+    assert os.path.exists(os.path.join(ROOT, entry["profile"]))
+    t, why = bench.measured_traffic("k_score_tc (pass 2, tcgen05)", 10_000_000, 64, 100, torch.float32)
+    if bench.source_digest(entry["sources"]) == entry["sha256"]:
+        assert t == entry["dram_bytes"] / entry["rows"] * 10_000_000 and "ncu" in why
+    else:
+        assert t is None and "changed" in why
+    # a record whose sources no longer hash the same is not used
+    bad = dict(rec, k_score_tc=dict(entry, sha256="0" * 64))
+    p = tmp_path / "rec.json"
+    p.write_text(json.dumps(bad))
+    monkeypatch.setattr(bench, "TRAFFIC_RECORD", str(p))
+    t, why = bench.measured_traffic("k_score_tc (pass 2, tcgen05)", 10_000_000, 64, 100, torch.float32)
+    assert t is None and "changed" in why
+    # nor one of another shape
+    t, why = bench.measured_traffic("k_score_tc (pass 2, tcgen05)", 10_000_000, 32, 100, torch.float32)
+    assert t is None

@@ -29,6 +29,8 @@ def score(Xt, lt, K, path="auto"):
     ("simt", torch.float32, 2000, 300, 7),      # rows wider than the register tile
     ("tensor", torch.float32, 5000, 64, 20),    # tcgen05, FP32 split into BF16 hi + lo
     ("tensor", torch.float32, 4000, 64, 300),   # two cluster blocks and the combine kernel
+    ("tensor_tf32", torch.float32, 5000, 64, 20),   # tcgen05, TF32 ranking, exact FP32 candidates
+    ("tensor_tf32", torch.float32, 4000, 64, 300),
     ("tensor", torch.float32, 3000, 160, 9),    # FP32 rows in 64-column chunks
     ("tensor", torch.bfloat16, 5000, 64, 20),   # BF16 storage
 ])

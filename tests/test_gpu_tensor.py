@@ -1,11 +1,16 @@
 """Parity of the tcgen05 tensor-core pass 2 with the FP64 oracle.
 
-FP32 storage runs the in-kernel BF16 hi/lo split (three MMAs per k-step),
-BF16 storage runs two, FP8 storage (d = 128, per-column scales folded into
-the centroids) runs two on the widened codes; all must meet the FP32
-tolerances of the SIMT path.  Sizes cover one and two 64-wide K atoms, padded
-D, K from 2 to 1000 (one cluster block of up to 256, and several blocks whose
-per-block minima are combined), ragged last tiles and multi-tile CTAs.
+Two kernels.  The split-precision kernel (paths "auto" and "tensor"): FP32
+storage runs the in-kernel BF16 hi/lo split (three MMAs per k-step), BF16
+storage runs two, FP8 storage (d = 128, per-column scales folded into the
+centroids) runs two on the widened codes.  The TF32 kernel (path
+"tensor_tf32", FP32 rows of 32..64 columns) ranks the clusters with one TF32
+product on the tile as TMA delivers it and recomputes a_i and every cluster
+inside the provable error band exactly in FP32.  All must meet the
+FP32 tolerances of the SIMT path.  Sizes cover one and two 32/64-wide K
+atoms, padded D, K from 2 to 1000 (one cluster block of up to 256, and
+several blocks whose per-block minima are combined), ragged last tiles and
+multi-tile CTAs.
 """
 import numpy as np
 import pytest
@@ -28,17 +33,21 @@ def run(Xt, lt, K, metric, path, save=True, cs=None):
 
 
 @pytest.mark.parametrize("metric", METRICS)
-@pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16])
+@pytest.mark.parametrize("dtype,path", [(torch.float32, "tensor"), (torch.float32, "tensor_tf32"),
+                                        (torch.bfloat16, "tensor")])
 @pytest.mark.parametrize("N,D,K", [(1000, 64, 2), (4097, 64, 7), (20000, 64, 100), (3001, 128, 17),
                                    (5000, 100, 33), (2000, 40, 5), (300, 64, 256), (129, 64, 3),
                                    (700, 128, 128), (700, 128, 256), (3000, 64, 300),
-                                   (2500, 128, 700), (1500, 64, 1000), (3000, 32, 7), (2000, 32, 300)])
-def test_tensor_path_against_bruteforce(metric, dtype, N, D, K):
+                                   (2500, 128, 700), (1500, 64, 1000), (3000, 32, 7), (2000, 32, 300),
+                                   (2000, 48, 129), (1000, 32, 16), (5000, 64, 512)])
+def test_tensor_path_against_bruteforce(metric, dtype, path, N, D, K):
     if dtype == torch.bfloat16 and (D < 64 or (2 * D) % 16):
         pytest.skip("BF16 tensor path needs d >= 64 and 16-byte rows (TMA)")
+    if path == "tensor_tf32" and "tf32" not in sil.tensor_kernels(dtype, D, K):
+        pytest.skip("the TF32 kernel serves FP32 rows of 32..64 columns")
     X, lab = case(700 + N + D + K, N, D, K, metric)
     Xt, lt = to_dev(X, lab, dtype)
-    r, st = run(Xt, lt, K, metric, "tensor")
+    r, st = run(Xt, lt, K, metric, path)
     ref = oracle.bruteforce(dequant(Xt), lab, K, metric)
     if ref["status"] == oracle.EDEGENERATE:
         assert st & sil.SIL_EDEGENERATE
@@ -53,9 +62,10 @@ def test_tensor_path_against_bruteforce(metric, dtype, N, D, K):
 
 
 @pytest.mark.parametrize("metric", METRICS)
-def test_tensor_and_simt_agree_at_scale_recipe(metric):
+@pytest.mark.parametrize("path", ["tensor", "tensor_tf32"])
+def test_tensor_and_simt_agree_at_scale_recipe(metric, path):
     w = synth.workload_at_scale(device="cuda", N=300_000)
-    ra, sa_ = run(w.X, w.labels, w.K, metric, "tensor", save=False)
+    ra, sa_ = run(w.X, w.labels, w.K, metric, path, save=False)
     rb, sb_ = run(w.X, w.labels, w.K, metric, "simt", save=False)
     assert sa_ == 0 and sb_ == 0
     assert float((ra.s - rb.s).abs().max()) <= TOL_SI
@@ -70,6 +80,22 @@ def test_tensor_path_far_from_origin():
     assert st == 0
     ref = oracle.linear(w.X.double().numpy(), w.labels.numpy(), 40)
     assert_scores(r.s, r.S, ref)
+
+
+@pytest.mark.parametrize("metric", METRICS)
+@pytest.mark.parametrize("D,K", [(64, 40), (32, 300)])
+def test_tf32_far_from_origin(metric, D, K):
+    # centres at radius 1e3: ||x|| ||mu'|| ~ 1e6, so the TF32 band spans
+    # thousands and many clusters are recomputed exactly per point
+    assert "tf32" in sil.tensor_kernels(torch.float32, D, K)
+    w = synth.blobs(20000, D, K, seed=10 + D, sphere_radius=1e3)
+    Xt, lt = w.X.cuda(), w.labels.cuda()
+    r, st = run(Xt, lt, K, metric, "tensor_tf32")
+    assert st == 0
+    ref = oracle.linear(w.X.double().numpy(), w.labels.numpy(), K, metric)
+    assert_scores(r.s, r.S, ref)
+    _, b, ks = sil.unpack_saved(r.saved, 20000)
+    np.testing.assert_allclose(b.cpu().double().numpy(), ref["b"], rtol=1e-5)
 
 
 def test_auto_picks_tensor_when_eligible():
@@ -217,21 +243,23 @@ def test_tensor_refuses_ineligible_shapes():
         sil.score(Xt, lt, 3, agg, path="tensor")
 
 
-@pytest.mark.parametrize("recipe", ["at_scale", "batched_labeling_0", "precision_bf16"])
+@pytest.mark.parametrize("recipe", ["at_scale", "at_scale_tf32", "batched_labeling_0", "batched_labeling_0_tf32",
+                                    "precision_bf16"])
 def test_tensor_and_simt_agree_on_every_row_at_full_size(recipe):
     # every row, not a sample: a pipeline hazard that corrupts one row in a
     # million shows up here
-    if recipe == "at_scale":
+    path = "tensor_tf32" if recipe.endswith("_tf32") else "tensor"
+    if recipe.startswith("at_scale"):
         w = synth.workload_at_scale(device="cuda")
         X, lab, K = w.X, w.labels, w.K
-    elif recipe == "batched_labeling_0":
+    elif recipe.startswith("batched_labeling_0"):
         X, labs, ks = synth.workload_batched(device="cuda", B=1)
         lab, K = labs[0].contiguous(), ks[0]
     else:
         w = synth.workload_precision(device="cuda", N=20_000_000)
         X, lab, K = synth.to_bf16(w.X), w.labels, w.K
     agg = sil.aggregate(X, lab, K)
-    rt = sil.score(X, lab, K, agg, want_s=True, save=True, path="tensor")
+    rt = sil.score(X, lab, K, agg, want_s=True, save=True, path=path)
     rs = sil.score(X, lab, K, agg, want_s=True, save=True, path="simt")
     torch.cuda.synchronize()
     d = (rt.s - rs.s).abs()
@@ -249,9 +277,10 @@ def _close_clusters(N, D, kmin, kmax, B=2):
 
 
 @pytest.mark.parametrize("metric", METRICS)
-@pytest.mark.parametrize("dtype,D", [(torch.float32, 64), (torch.bfloat16, 64), (torch.float32, 32),
-                                     (torch.float32, 160)])
-def test_close_clusters_match_the_oracle_without_bias(dtype, D, metric):
+@pytest.mark.parametrize("dtype,D,path", [(torch.float32, 64, "tensor"), (torch.float32, 64, "tensor_tf32"),
+                                          (torch.bfloat16, 64, "tensor"), (torch.float32, 32, "tensor"),
+                                          (torch.float32, 32, "tensor_tf32"), (torch.float32, 160, "tensor")])
+def test_close_clusters_match_the_oracle_without_bias(dtype, D, path, metric):
     # b_i of such rows comes from the difference form, so the error of S is
     # not the tensor cores' round-towards-zero bias times the cancellation.
     # D = 160 runs the chunked kernel, which reads such rows back from
@@ -261,7 +290,7 @@ def test_close_clusters_match_the_oracle_without_bias(dtype, D, metric):
     for b, k in enumerate(ks):
         lab = labs[b].contiguous()
         agg = sil.aggregate(Xs, lab, k, metric)
-        r = sil.score(Xs, lab, k, agg, metric, want_s=True, save=True, path="tensor")
+        r = sil.score(Xs, lab, k, agg, metric, want_s=True, save=True, path=path)
         torch.cuda.synchronize()
         ref = oracle.linear(dequant(Xs), lab.cpu().numpy(), k, metric)
         assert abs(float(r.S) - ref["S"]) <= TOL_S, (k, float(r.S) - ref["S"])
