@@ -89,7 +89,9 @@ typedef enum {
 
 /* Pass-2 implementation choice for sil_score. */
 typedef enum {
-  SIL_PATH_AUTO = 0,   /* library picks from (k, d, dtype) */
+  SIL_PATH_AUTO = 0,   /* library picks from (k, d, dtype): the split-precision
+                          tensor kernel, or for float32 rows of 32..64 columns
+                          and k <= 48 the TF32 kernel (faster there) */
   SIL_PATH_SIMT = 1,   /* FP32 FFMA with the centroids staged in shared memory */
   SIL_PATH_TENSOR = 2, /* tcgen05 tensor-core GEMM with a fused epilogue: the
                           split-precision kernel (BF16 hi/lo operands, a
@@ -162,6 +164,17 @@ int sil_score(const void* X, int32_t dtype, int64_t n, int32_t d, int64_t ldx,
               uint32_t* dev_status, void* stream);
 
 /*
+ * Both passes of one labeling in one call: sil_aggregate into (count, s1, s2)
+ * (device outputs, overwritten, as sil_aggregate documents them), then
+ * sil_score from them on the same workspace, with the same s_out, S_out,
+ * saved, path and results as those two calls.
+ */
+int sil_silhouette(const void* X, int32_t dtype, int64_t n, int32_t d, int64_t ldx, const float* col_scale,
+                   const int32_t* labels, int32_t k, int32_t dist, int64_t* count, double* s1, double* s2,
+                   float* s_out, double* S_out, void* saved, int32_t path, void* ws, size_t ws_bytes,
+                   uint32_t* dev_status, void* stream);
+
+/*
  * dS/dX with the labels fixed and b_i's argmin held at its value (the min
  * and max of Eq. 1 taken as subgradients).  grad_S (device, one double,
  * nullable = 1.0) scales the result, dX (device float32, row-major n x d,
@@ -179,7 +192,14 @@ int sil_score_backward(const void* X, int32_t dtype, int64_t n, int32_t d, int64
  * S for `batch` labelings of the same X.  labels is device int32 of
  * batch x n (labeling b at labels + b*ldl), k_host (host int32[batch]) the
  * number of label ids of each labeling, S_out (device double[batch]).
- * Equivalent to sil_aggregate + sil_score per labeling.
+ * Equivalent to sil_aggregate + sil_score per labeling.  For float32 rows of
+ * 32..64 columns, k <= 512 and 16-byte aligned rows (ldl a multiple of 4),
+ * pass 1 and the finalisation run per labeling and the pass 2 of EVERY
+ * labeling runs as one tensor-core launch (a CTA row per labeling block of
+ * at most 256 clusters, the CTAs of all labelings streaming the same rows
+ * of X); wider labelings' two blocks are combined by one more launch.  Other
+ * shapes run the per-labeling launch sequence.  The workspace grows with
+ * batch x n (two planes of per-block distances and one of a_i per labeling).
  */
 int sil_score_batched(const void* X, int32_t dtype, int64_t n, int32_t d, int64_t ldx,
                       const float* col_scale, const int32_t* labels, int64_t ldl,
@@ -208,6 +228,23 @@ size_t sil_euclidean_workspace_size(int64_t n, int32_t d, int32_t k);
 int sil_score_euclidean(const void* X, int32_t dtype, int64_t n, int32_t d, int64_t ldx, const float* col_scale,
                         const int32_t* labels, int32_t k, float* s_out, double* S_out, void* saved, void* ws,
                         size_t ws_bytes, uint32_t* dev_status, void* stream);
+
+/*
+ * S of rows scored in m disjoint chunks (Sec. II: S is the mean of s_i over
+ * every point), from each chunk's S_out of sil_score: S_chunks (device
+ * double[m]) and n_chunks (device int64[m], the chunks' row counts) give
+ * *S_out (device double) = sum_c n_c S_c / sum_c n_c in FP64; NaN if a chunk
+ * mean is NaN.  Returns SIL_EINVAL for m <= 0 or a NULL pointer.
+ */
+int sil_chunk_mean(const double* S_chunks, const int64_t* n_chunks, int32_t m, double* S_out, void* stream);
+
+/*
+ * Launch plan of the one-launch batched pass 2 (see sil_score_batched), for an
+ * autotuner: ranges = CTAs per labeling block (1..64, each streaming an equal
+ * share of the rows), a_buffers = A-operand buffers (2 or 4; 0 = the deepest
+ * that fits).  Process-wide; returns SIL_EINVAL out of range.  Host-only.
+ */
+int sil_batched_plan_set(int32_t ranges, int32_t a_buffers);
 
 /* Largest sizes sil_score_noalloc serves. */
 #define SIL_NOALLOC_MAX_K 1024

@@ -3,6 +3,7 @@
 // No allocation, no synchronisation: every call only enqueues work on the
 // caller's stream.
 #include <atomic>
+#include <cstdlib>
 #include <cmath>
 
 #include "sil_internal.cuh"
@@ -55,6 +56,24 @@ WsLayout ws_layout(int64_t n, int32_t d, int32_t k, int32_t dtype, int32_t dist,
   L.zbf = take(std::max(tc_pack_bytes(k, d), t32_pack_bytes(k, d)));
   L.tcp = take(std::max(tc_partial_bytes(n, d, k, dtype), dtype == SIL_F32 ? t32_partial_bytes(n, d, k) : size_t(0)));
   L.batch = take(K * (size_t(d) + 2) * 8);
+  // one launch for every labeling's pass 2 (shapes the batched kernel serves)
+  const size_t pack = batch > 1 && dtype == SIL_F32 && k <= 512 ? tc_batched_pack_bytes(batch, k, d) : 0;
+  if (pack) {
+    const size_t B = size_t(batch), KP = size_t(round_up(std::max(k, 16), 16));
+    L.bst = take(B * 4);
+    L.bitems = take(2 * B * sizeof(TcItem));  // at most two blocks per labeling
+    L.bmulti = take(B * sizeof(TcItem));
+    L.bzf = take(B * KP * dz * 4);
+    L.bcl = take(B * KP * 16);
+    L.bg = take(B * dz * 8);
+    L.bgf = take(B * dz * 4);
+    L.bpack = take(pack);
+    L.bpart = take(B * size_t(kBatchedMaxRanges) * 8);
+    // nearest distance per (block, point) and a_i per point of the labelings
+    // with two blocks
+    L.bplanes = take(2 * B * N * 4);
+    L.bown = take(B * N * 4);
+  }
   L.total = o;
   return L;
 }
@@ -109,11 +128,12 @@ void set_sort_scratch(AggLaunch* a, void* ws, const WsLayout& L, int32_t k, int6
   a->widx = at<float>(ws, L.bw);
 }
 
-// Pass 1 into (count, s1, s2), status into the workspace word.
+// Pass 1 into (count, s1, s2), status into the workspace word (or wst).
 int run_aggregate(const void* X, int32_t dtype, int64_t n, int32_t d, int64_t ldx, const float* cs,
                   const int32_t* labels, int32_t k, int32_t dist, int64_t* count, double* s1,
-                  double* s2, bool accumulate, void* ws, const WsLayout& L, cudaStream_t st) {
-  uint32_t* wst = at<uint32_t>(ws, L.misc);
+                  double* s2, bool accumulate, void* ws, const WsLayout& L, cudaStream_t st,
+                  uint32_t* wst = nullptr) {
+  if (!wst) wst = at<uint32_t>(ws, L.misc);
   if (!accumulate) {
     SIL_TRY(cu(cudaMemsetAsync(count, 0, size_t(k) * 8, st)));
     SIL_TRY(cu(cudaMemsetAsync(s1, 0, size_t(k) * size_t(d) * 8, st)));
@@ -165,12 +185,25 @@ int run_finalize(const int64_t* count, const double* s1, const double* s2, int32
   return cu(launch_finalize(f));
 }
 
+// The automatic path takes the TF32-ranked kernel for few clusters: it has
+// no converter warps (the lower cost per point), but sweeps the ranked
+// values twice (the higher cost per cluster).  Measured on 1e7 rows of 64
+// columns, pass 2 in ms (split-precision / TF32): K = 2 0.71 / 0.50,
+// 16 0.72 / 0.62, 32 0.75 / 0.72, 64 0.79 / 0.85, 100 0.93 / 1.08.
+constexpr int32_t kTf32AutoMaxK = 48;
+
+bool takes_tf32(int32_t path, const void* X, int32_t dtype, int64_t n, int32_t d, int64_t ldx,
+                const int32_t* labels, int32_t k) {
+  return (path == SIL_PATH_TENSOR_TF32 || (path == SIL_PATH_AUTO && k <= kTf32AutoMaxK)) &&
+         t32_eligible(dtype, n, d, ldx, k, X, labels);
+}
+
 // Pass 2 over finalized constants; writes partial sums, returns their count.
 int run_score(const void* X, int32_t dtype, int64_t n, int32_t d, int64_t ldx, const float* cs,
               const int32_t* labels, int32_t k, int32_t dist, float* s_out, float* sa, float* sb,
               int32_t* skstar, int32_t path, void* ws, const WsLayout& L, cudaStream_t st,
               int32_t* np) {
-  const bool tf32_ok = path == SIL_PATH_TENSOR_TF32 && t32_eligible(dtype, n, d, ldx, k, X, labels);
+  const bool tf32_ok = takes_tf32(path, X, dtype, n, d, ldx, labels, k);
   const bool tc_ok = (path == SIL_PATH_AUTO || path == SIL_PATH_TENSOR) &&
                      tc_eligible(dtype, n, d, ldx, k, X, labels);
   if ((path == SIL_PATH_TENSOR && !tc_ok) || (path == SIL_PATH_TENSOR_TF32 && !tf32_ok)) return SIL_EUNSUPPORTED;
@@ -257,6 +290,33 @@ int sil_score(const void* X, int32_t dtype, int64_t n, int32_t d, int64_t ldx,
   int32_t np = 0;
   SIL_TRY(run_score(X, dtype, n, d, ldx, col_scale, labels, k, dist, s_out, sa, sb, skstar, path, ws,
                     L, st, &np));
+  return cu(launch_reduce_S(at<double>(ws, L.partials), np, n, wst, dev_status, S_out, st));
+}
+
+int sil_silhouette(const void* X, int32_t dtype, int64_t n, int32_t d, int64_t ldx, const float* col_scale,
+                   const int32_t* labels, int32_t k, int32_t dist, int64_t* count, double* s1, double* s2,
+                   float* s_out, double* S_out, void* saved, int32_t path, void* ws, size_t ws_bytes,
+                   uint32_t* dev_status, void* stream) {
+  SIL_TRY(check_common(X, dtype, n, d, ldx, col_scale, labels, k, dist));
+  if (!count || !s1 || !s2) return SIL_EINVAL;
+  if (path < SIL_PATH_AUTO || path > SIL_PATH_TENSOR_TF32) return SIL_EINVAL;
+  SIL_TRY(check_ws(ws, ws_bytes, n, d, k, dtype, dist, 1));
+  const WsLayout L = ws_layout(n, d, k, dtype, dist, 1);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  uint32_t* wst = at<uint32_t>(ws, L.misc);
+  SIL_TRY(cu(cudaMemsetAsync(wst, 0, 4, st)));
+  SIL_TRY(run_aggregate(X, dtype, n, d, ldx, col_scale, labels, k, dist, count, s1, s2, false, ws, L, st));
+  SIL_TRY(run_finalize(count, s1, s2, k, d, dist, ws, L, st));
+  float* sa = nullptr;
+  float* sb = nullptr;
+  int32_t* skstar = nullptr;
+  if (saved) {
+    sa = static_cast<float*>(saved);
+    sb = sa + n;
+    skstar = reinterpret_cast<int32_t*>(sb + n);
+  }
+  int32_t np = 0;
+  SIL_TRY(run_score(X, dtype, n, d, ldx, col_scale, labels, k, dist, s_out, sa, sb, skstar, path, ws, L, st, &np));
   return cu(launch_reduce_S(at<double>(ws, L.partials), np, n, wst, dev_status, S_out, st));
 }
 
@@ -354,6 +414,105 @@ int sil_score_backward(const void* X, int32_t dtype, int64_t n, int32_t d, int64
   return cu(launch_publish_status(wst, dev_status, st));
 }
 
+}  // extern "C"
+
+namespace {
+
+// Items of the batched launch, handed to the device by value (kernel
+// parameters), so that a captured graph holds them too.
+constexpr int kItemChunk = 64;
+struct ItemChunk {
+  TcItem v[kItemChunk];
+};
+__global__ void k_set_items(ItemChunk c, int32_t count, TcItem* dst) {
+  if (int(threadIdx.x) < count) dst[threadIdx.x] = c.v[threadIdx.x];
+}
+
+// Every labeling's pass 1 and finalisation, then one tensor-core launch for
+// all their pass 2 and one reduction to the B means.
+int run_batched_single_launch(const void* X, int64_t n, int32_t d, int64_t ldx, const int32_t* labels, int64_t ldl,
+                              const int32_t* k_host, int32_t batch, int32_t kmax, int32_t dist, double* S_out,
+                              void* ws, const WsLayout& L, uint32_t* dev_status, cudaStream_t st) {
+  const int64_t dz = round_up(d, 4), kmaxp = round_up(std::max(kmax, 16), 16);
+  uint32_t* bst = at<uint32_t>(ws, L.bst);
+  TcItem* items = at<TcItem>(ws, L.bitems);
+  TcItem* multi = at<TcItem>(ws, L.bmulti);
+  float* bzf = at<float>(ws, L.bzf);
+  float4* bcl = at<float4>(ws, L.bcl);
+  double* bg = at<double>(ws, L.bg);
+  float* bgf = at<float>(ws, L.bgf);
+  SIL_TRY(cu(cudaMemsetAsync(bst, 0, size_t(batch) * 4, st)));
+  int64_t* count = at<int64_t>(ws, L.batch);
+  double* s1 = reinterpret_cast<double*>(count + kmax);
+  double* s2 = s1 + size_t(kmax) * d;
+  int32_t zrows = 0, n_items = 0, n_multi = 0, n_planes = 0;
+  ItemChunk chunk{}, mchunk{};
+  int32_t in_chunk = 0, in_mchunk = 0;
+  auto flush = [&](ItemChunk& c, int32_t& cnt, TcItem* dst, int32_t done) -> int {
+    if (cnt == 0) return SIL_OK;
+    k_set_items<<<1, kItemChunk, 0, st>>>(c, cnt, dst + (done - cnt));
+    cnt = 0;
+    return cu(cudaGetLastError());
+  };
+  for (int32_t b = 0; b < batch; ++b) {
+    const int32_t kb = k_host[b];
+    const int32_t* lab = labels + b * ldl;
+    SIL_TRY(run_aggregate(X, SIL_F32, n, d, ldx, nullptr, lab, kb, dist, count, s1, s2, false, ws, L, st, bst + b));
+    FinLaunch f{};
+    f.count = reinterpret_cast<const unsigned long long*>(count);
+    f.s1 = s1;
+    f.s2 = s2;
+    f.k = kb;
+    f.d = d;
+    f.dist = dist;
+    f.g = bg + b * dz;
+    f.gf = bgf + b * dz;
+    f.zf = bzf + b * kmaxp * dz;
+    f.cl = bcl + b * kmaxp;
+    f.status = bst + b;
+    f.stream = st;
+    SIL_TRY(cu(launch_finalize(f)));
+    // blocks of at most 256 clusters (the MMA N), balanced
+    const int32_t nblk = int32_t(cdiv(kb, 256));
+    const int32_t kp = int32_t(round_up(std::max<int64_t>(cdiv(kb, nblk), 16), 16));
+    const int32_t plane0 = nblk > 1 ? n_planes : -1, own_plane = nblk > 1 ? n_multi : -1;
+    for (int32_t j = 0; j < nblk; ++j) {
+      TcItem& it = chunk.v[in_chunk++];
+      it.b = b;
+      it.k = kb;
+      it.nblk = nblk;
+      it.kb0 = j * kp;
+      it.kp = kp;
+      it.zrow = zrows;
+      it.cl_off = int32_t(b * kmaxp);
+      it.zf_off = int32_t(b * kmaxp * dz);
+      it.g_off = int32_t(b * dz);
+      it.plane = nblk > 1 ? plane0 + j : -1;
+      it.own_plane = own_plane;
+      zrows += kp;
+      ++n_items;
+      if (j == 0 && nblk > 1) mchunk.v[in_mchunk++] = it;
+      if (in_chunk == kItemChunk) SIL_TRY(flush(chunk, in_chunk, items, n_items));
+    }
+    if (nblk > 1) {
+      n_planes += nblk;
+      ++n_multi;
+      if (in_mchunk == kItemChunk) SIL_TRY(flush(mchunk, in_mchunk, multi, n_multi));
+    }
+  }
+  SIL_TRY(flush(chunk, in_chunk, items, n_items));
+  SIL_TRY(flush(mchunk, in_mchunk, multi, n_multi));
+  SIL_TRY(cu(launch_score_tc_batched(X, n, d, ldx, labels, ldl, batch, kmax, dist, items, n_items, zrows, multi,
+                                     n_multi, bzf, bcl, bg, bgf, at<void>(ws, L.bpack), at<float>(ws, L.bplanes),
+                                     at<float>(ws, L.bown), at<double>(ws, L.bpart), bst, st)));
+  return cu(launch_reduce_S_batched(at<double>(ws, L.bpart), tc_batched_ranges(), n, batch, bst, dev_status, S_out,
+                                    st));
+}
+
+}  // namespace
+
+extern "C" {
+
 int sil_score_batched(const void* X, int32_t dtype, int64_t n, int32_t d, int64_t ldx,
                       const float* col_scale, const int32_t* labels, int64_t ldl,
                       const int32_t* k_host, int32_t batch, int32_t dist, double* S_out,
@@ -369,6 +528,10 @@ int sil_score_batched(const void* X, int32_t dtype, int64_t n, int32_t d, int64_
   const WsLayout L = ws_layout(n, d, kmax, dtype, dist, batch);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   uint32_t* wst = at<uint32_t>(ws, L.misc);
+  if (L.bpack && batch > 1 && n > 0 && !(getenv("SIL_BATCH_PER_LABELING") && getenv("SIL_BATCH_PER_LABELING")[0] == '1') &&
+      tc_batched_eligible(dtype, n, d, ldx, kmax, X, labels, ldl))
+    return run_batched_single_launch(X, n, d, ldx, labels, ldl, k_host, batch, kmax, dist, S_out, ws, L, dev_status,
+                                     st);
   int64_t* count = at<int64_t>(ws, L.batch);
   double* s1 = reinterpret_cast<double*>(count + kmax);
   double* s2 = s1 + size_t(kmax) * d;
@@ -426,6 +589,13 @@ int sil_tensor_kernel(int32_t dtype, int32_t d, int32_t k) {
                       (dtype == SIL_FP8_E4M3 && d == 128);
   if (box_ok && tc_plan_query(dtype, d, k, &bk, &nb)) out |= SIL_TENSOR_KERNEL_SPLIT;
   return out;
+}
+
+int sil_batched_plan_set(int32_t ranges, int32_t a_buffers) { return tc_batched_plan_set(ranges, a_buffers); }
+
+int sil_chunk_mean(const double* S_chunks, const int64_t* n_chunks, int32_t m, double* S_out, void* stream) {
+  if (m <= 0 || !S_chunks || !n_chunks || !S_out) return SIL_EINVAL;
+  return cu(launch_chunk_mean(S_chunks, n_chunks, m, S_out, static_cast<cudaStream_t>(stream)));
 }
 
 int sil_tensor_plan_candidates(int32_t dtype, int32_t d, int32_t k, int32_t* plans, int32_t max_plans,

@@ -449,6 +449,49 @@ __global__ void k_reduce_S(const double* partials, int32_t np, int64_t n, const 
   }
 }
 
+// S over row chunks from the chunk means: sum_c n_c S_c / sum_c n_c in FP64
+// (one CTA, fixed order); NaN if any chunk mean is NaN.
+__global__ void k_chunk_mean(const double* S_chunks, const int64_t* n_chunks, int32_t m, double* S_out) {
+  __shared__ double rs[256];
+  __shared__ double rn[256];
+  double s = 0.0, c = 0.0;
+  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    s += S_chunks[i] * double(n_chunks[i]);
+    c += double(n_chunks[i]);
+  }
+  rs[threadIdx.x] = s;
+  rn[threadIdx.x] = c;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (int(threadIdx.x) < o) {
+      rs[threadIdx.x] += rs[threadIdx.x + o];
+      rn[threadIdx.x] += rn[threadIdx.x + o];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *S_out = rn[0] > 0.0 ? rs[0] / rn[0] : NAN;
+}
+
+// One CTA per labeling: S_b from its np partial sums (fixed order).
+__global__ void k_reduce_S_batched(const double* partials, int32_t np, int64_t n, const uint32_t* status,
+                                   uint32_t* user_status, double* S_out) {
+  __shared__ double red[256];
+  const int b = blockIdx.x;
+  double t = 0.0;
+  for (int i = threadIdx.x; i < np; i += blockDim.x) t += partials[int64_t(b) * np + i];
+  red[threadIdx.x] = t;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (int(threadIdx.x) < s) red[threadIdx.x] += red[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const uint32_t st = status[b];
+    if (user_status && st) atomicOr(user_status, st);
+    S_out[b] = (st == 0 && n > 0) ? red[0] / double(n) : NAN;
+  }
+}
+
 __global__ void k_publish_status(const uint32_t* ws_status, uint32_t* user_status) {
   if (threadIdx.x == 0 && user_status) {
     const uint32_t st = *ws_status;
@@ -557,6 +600,19 @@ cudaError_t launch_score_simt(ScoreLaunch& s) {
 cudaError_t launch_reduce_S(const double* partials, int32_t np, int64_t n, const uint32_t* ws_status,
                             uint32_t* user_status, double* S_out, cudaStream_t stream) {
   k_reduce_S<<<1, 1024, 0, stream>>>(partials, np, n, ws_status, user_status, S_out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reduce_S_batched(const double* partials, int32_t np, int64_t n, int32_t batch,
+                                    const uint32_t* status, uint32_t* user_status, double* S_out,
+                                    cudaStream_t stream) {
+  k_reduce_S_batched<<<batch, 256, 0, stream>>>(partials, np, n, status, user_status, S_out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_chunk_mean(const double* S_chunks, const int64_t* n_chunks, int32_t m, double* S_out,
+                              cudaStream_t stream) {
+  k_chunk_mean<<<1, 256, 0, stream>>>(S_chunks, n_chunks, m, S_out);
   return cudaGetLastError();
 }
 

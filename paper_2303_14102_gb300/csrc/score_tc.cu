@@ -55,6 +55,7 @@
 #include <cuda_fp8.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstdlib>
 #include <mutex>
 #include <vector>
@@ -311,6 +312,12 @@ __device__ __forceinline__ int tc_lane_find(uint32_t tbase, int kp, const float*
 }
 
 // ------------------------------------------------------------ parameters
+__host__ __device__ inline int tc_pow2(int v) {
+  int p = 32;
+  while (p < v) p <<= 1;
+  return p;
+}
+
 struct TcK {
   int64_t n;
   int32_t d;
@@ -341,6 +348,8 @@ struct TcK {
   int32_t* parg;  // [nblk][n] its index (backward record)
   float* pown;    // [n]       a_i before scaling, from the own cluster's block
   uint32_t* status;
+  int32_t zbox_rows;   // rows of Z per TMA box (the block width, or 16 when widths vary)
+  const TcItem* items; // several labelings in one launch: item blockIdx.y (else nullptr)
 };
 
 struct TcMaps {
@@ -461,7 +470,7 @@ __global__ void k_selftest_wait(uint32_t* out) {
   __syncthreads();
 }
 
-template <int MODE, int DP, bool TRACK, int CG>
+template <int MODE, int DP, bool TRACK, int CG, bool BATCH = false>
 __global__ void __launch_bounds__(tc_threads(DP, CG), 1) k_score_tc(TcK a, const __grid_constant__ TcMaps maps) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   // 1024-byte alignment for the swizzled tiles, by offsetting the shared array
@@ -476,7 +485,7 @@ __global__ void __launch_bounds__(tc_threads(DP, CG), 1) k_score_tc(TcK a, const
   // the plans never pass odd rings to two converter groups (see
   // tc_rings_ok); refuse them here too rather than alias mbarrier phases
   if (CG == 2 && ((a.nab & 1) || (STAGED && (a.nxs & 1)))) {
-    if (threadIdx.x == 0) set_status(a.status, SIL_EUNSUPPORTED);
+    if (threadIdx.x == 0) set_status(a.status + (BATCH ? a.items[blockIdx.y].b : 0), SIL_EUNSUPPORTED);
     return;
   }
   // where the epilogue reads an ill-conditioned row back: FP32 plans without
@@ -490,9 +499,43 @@ __global__ void __launch_bounds__(tc_threads(DP, CG), 1) k_score_tc(TcK a, const
   const int64_t ntiles = cdiv(a.n, kTM);
   // tiles of this CTA: blockIdx.x, blockIdx.x + gridDim.x, ...; cluster block blockIdx.y
   const int my_tiles = blockIdx.x < ntiles ? int(cdiv(ntiles - blockIdx.x, gridDim.x)) : 0;
-  const int kb0 = int(blockIdx.y) * a.kp;  // first cluster of this block
-  const int kblk = min(a.kp, a.k - kb0);   // clusters of this block (>= 1)
-  const bool fused = a.nblk == 1;
+  // This CTA's clusters: block blockIdx.y (of a.kp clusters) of one
+  // labeling, or -- several labelings scored in one launch -- all the
+  // clusters (at most 512) of labeling a.items[blockIdx.y], with its own
+  // constants, labels row, status word and partial-sum slot.
+  int kall = a.k, kb0 = int(blockIdx.y) * a.kp, kpc = a.kp, zrow = kb0, lab_b = -1;
+  const float* cbp = a.cb;
+  const float4* clp = a.cl;
+  const float* zfp = a.zf;
+  const float* gfp = a.gf;
+  bool fused = a.nblk == 1;
+  int64_t pidx = blockIdx.x;
+  uint32_t* sts = a.status;
+  int64_t plane = blockIdx.y, own_plane = 0;
+  if constexpr (BATCH) {
+    const TcItem it = a.items[blockIdx.y];
+    kall = it.k;
+    kb0 = it.kb0;
+    kpc = it.kp;
+    zrow = it.zrow;
+    lab_b = it.b;
+    cbp = a.cb + it.zrow - it.kb0;  // cbp[kb0 + i] is the block's row i
+    clp = a.cl + it.cl_off;
+    zfp = a.zf + it.zf_off;
+    gfp = a.gf + it.g_off;
+    fused = it.nblk == 1;
+    pidx = int64_t(it.b) * gridDim.x + blockIdx.x;
+    sts = a.status + it.b;
+    plane = it.plane;
+    own_plane = it.own_plane;
+  }
+  const int kblk = min(kpc, kall - kb0);  // clusters of this block (>= 1)
+  // TMEM: two accumulators (double-buffered tiles) when a block fits in 256
+  // columns, one of up to 512 otherwise
+  const int acc_cols = BATCH ? tc_pow2(kpc) : a.acc_cols;
+  const int nslot = !BATCH || acc_cols <= 256 ? 2 : 1;
+  const int sl_shift = nslot == 2 ? 1 : 0;  // tile t uses accumulator t & sl_mask, phase (t >> sl_shift) & 1
+  const int sl_mask = nslot - 1;
   float* cbs = reinterpret_cast<float*>(base + L.cb);
 
   if (threadIdx.x == 0) {
@@ -518,24 +561,24 @@ __global__ void __launch_bounds__(tc_threads(DP, CG), 1) k_score_tc(TcK a, const
     *B.abort_flag = 0;
     fence_mbar_init();
   }
-  for (int i = threadIdx.x; i < a.kp; i += blockDim.x) cbs[i] = a.cb[kb0 + i];
+  for (int i = threadIdx.x; i < kpc; i += blockDim.x) cbs[i] = cbp[kb0 + i];
   float* gsm = reinterpret_cast<float*>(base + L.gsm);
   float* csm = reinterpret_cast<float*>(base + L.csm);
   float4* clsm = reinterpret_cast<float4*>(base + L.clsm);
   float* zsm = reinterpret_cast<float*>(base + L.zsm);
-  for (int i = threadIdx.x; i < DP; i += blockDim.x) gsm[i] = i < a.dz ? a.gf[i] : 0.f;
+  for (int i = threadIdx.x; i < DP; i += blockDim.x) gsm[i] = i < a.dz ? gfp[i] : 0.f;
   if (MODE == kModeFP8)
     for (int i = threadIdx.x; i < DP; i += blockDim.x) csm[i] = i < a.d ? a.cs[i] : 0.f;
-  for (int i = threadIdx.x; i < kblk; i += blockDim.x) clsm[i] = a.cl[kb0 + i];
+  for (int i = threadIdx.x; i < kblk; i += blockDim.x) clsm[i] = clp[kb0 + i];
   if (a.zst)
     for (int i = threadIdx.x; i < kblk * a.zst; i += blockDim.x) {
       const int kk = i / a.zst, c = i - kk * a.zst;
-      zsm[i] = c < a.dz ? a.zf[int64_t(kb0 + kk) * a.dz + c] : 0.f;
+      zsm[i] = c < a.dz ? zfp[int64_t(kb0 + kk) * a.dz + c] : 0.f;
     }
-  if (warp == 1) {  // TMEM: two accumulators of acc_cols columns
+  if (warp == 1) {  // TMEM: nslot accumulators of acc_cols columns
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32(B.tmem_base)),
-                 "r"(2 * a.acc_cols)
+                 "r"(nslot * acc_cols)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     tc_fence_before();
@@ -547,17 +590,21 @@ __global__ void __launch_bounds__(tc_threads(DP, CG), 1) k_score_tc(TcK a, const
   if (warp == 0) {
     // ------------------------------------------------------- TMA producer
     if (lane == 0) {
-      mbar_arrive_expect_tx(B.zfull, uint32_t(2 * natom * a.kp * ROWB));
+      // the block's split centroids: kpc rows of Z in boxes of a.zbox_rows
+      // rows (atoms laid out for a.kp rows)
+      mbar_arrive_expect_tx(B.zfull, uint32_t(2 * natom * kpc * ROWB));
       for (int at = 0; at < natom; ++at) {
-        tma_load_2d(base + L.zh + at * a.kp * ROWB, &maps.zh, at * 64, kb0, B.zfull);
-        tma_load_2d(base + L.zl + at * a.kp * ROWB, &maps.zl, at * 64, kb0, B.zfull);
+        for (int r0 = 0; r0 < kpc; r0 += a.zbox_rows) {
+          tma_load_2d(base + L.zh + at * a.kp * ROWB + r0 * ROWB, &maps.zh, at * 64, zrow + r0, B.zfull);
+          tma_load_2d(base + L.zl + at * a.kp * ROWB + r0 * ROWB, &maps.zl, at * 64, zrow + r0, B.zfull);
+        }
       }
       int t = 0;
       for (; t < my_tiles; ++t) {
         const int32_t row0 = int32_t((blockIdx.x + int64_t(t) * gridDim.x) * kTM);
         if (STAGED) {
           const int j = t % a.nxs;
-          if (!tc_wait(&B.xempty[j], ((t / a.nxs) & 1) ^ 1, abort_flag, a.status)) break;
+          if (!tc_wait(&B.xempty[j], ((t / a.nxs) & 1) ^ 1, abort_flag, sts)) break;
           unsigned char* xs = base + L.xs + j * L.xs_stride;
           constexpr int raw = raw_tile_bytes(MODE, DP);
           mbar_arrive_expect_tx(&B.xfull[j], uint32_t(raw + kTM * 4));
@@ -568,15 +615,17 @@ __global__ void __launch_bounds__(tc_threads(DP, CG), 1) k_score_tc(TcK a, const
             for (int s128 = 0; s128 < DP / 128; ++s128)
               tma_load_2d(xs + s128 * kAtomBytes, &maps.x, s128 * 128, row0, &B.xfull[j]);
           }
-          tma_load_1d(xs + raw, &maps.lab, row0, &B.xfull[j]);
+          if constexpr (!BATCH) tma_load_1d(xs + raw, &maps.lab, row0, &B.xfull[j]);
+          else tma_load_2d(xs + raw, &maps.lab, row0, lab_b, &B.xfull[j]);
         } else {
           const int i = t % a.nab;
-          if (!tc_wait(&B.aempty[i], ((t / a.nab) & 1) ^ 1, abort_flag, a.status)) break;
+          if (!tc_wait(&B.aempty[i], ((t / a.nab) & 1) ^ 1, abort_flag, sts)) break;
           unsigned char* ab = base + L.abuf + i * L.abuf_stride;
           mbar_arrive_expect_tx(&B.afull[i], uint32_t(natom * kAtomBytes + kTM * 4));
           for (int at = 0; at < natom; ++at)
             tma_load_2d(ab + at * kAtomBytes, &maps.x, at * 64, row0, &B.afull[i]);
-          tma_load_1d(base + L.side + i * L.side_stride + kTM * 16, &maps.lab, row0, &B.afull[i]);
+          if constexpr (!BATCH) tma_load_1d(base + L.side + i * L.side_stride + kTM * 16, &maps.lab, row0, &B.afull[i]);
+          else tma_load_2d(base + L.side + i * L.side_stride + kTM * 16, &maps.lab, row0, lab_b, &B.afull[i]);
         }
       }
       if (*abort_flag) {
@@ -591,54 +640,60 @@ __global__ void __launch_bounds__(tc_threads(DP, CG), 1) k_score_tc(TcK a, const
   } else if (warp == 1) {
     // --------------------------------------------------------- MMA issuer
     if (lane == 0) {
-      const uint32_t idesc = umma_idesc_bf16(kTM, a.kp);
+      // blocks wider than 256 clusters (one labeling of a batched launch) run
+      // as two MMAs of N <= 256 into adjacent TMEM columns
+      const int nh = BATCH && kpc > 256 ? 2 : 1;
       int t = 0;
-      bool ok = tc_wait(B.zfull, 0, abort_flag, a.status);
+      bool ok = tc_wait(B.zfull, 0, abort_flag, sts);
       for (; ok && t < my_tiles; ++t) {
-        const int i = t % a.nab, bsel = t & 1;
-        if (!tc_wait(&B.afull[i], (t / a.nab) & 1, abort_flag, a.status)) break;
-        if (!tc_wait(&B.accempty[bsel], ((t >> 1) & 1) ^ 1, abort_flag, a.status)) break;
+        const int i = t % a.nab, bsel = t & sl_mask;
+        if (!tc_wait(&B.afull[i], (t / a.nab) & 1, abort_flag, sts)) break;
+        if (!tc_wait(&B.accempty[bsel], ((t >> sl_shift) & 1) ^ 1, abort_flag, sts)) break;
         tc_fence_after();
-        const uint32_t d_tmem = tmem + uint32_t(bsel * a.acc_cols);
         const uint32_t ahi = smem_u32(base + L.abuf + i * L.abuf_stride);
         const uint32_t alo = ahi + uint32_t(L.lo_off);
-        const uint32_t zh = smem_u32(base + L.zh), zl = smem_u32(base + L.zl);
-        // The small correction products (x.Z_lo, x_lo.Z_hi) go into the fresh
-        // accumulator first and the large x_hi.Z_hi products last: each
-        // tensor-core accumulation rounds relative to the running magnitude,
-        // so this order adds the fewest steps at the final, largest magnitude
-        // (a measured bias of ~1e-6 in b_i when the order was interleaved).
-        if constexpr (NARROW) {
+        for (int hh = 0; hh < nh; ++hh) {
+          const uint32_t idesc = umma_idesc_bf16(kTM, hh == 0 ? (kpc < 256 ? kpc : 256) : kpc - 256);
+          const uint32_t d_tmem = tmem + uint32_t(bsel * acc_cols + hh * 256);
+          const uint32_t zh = smem_u32(base + L.zh) + uint32_t(hh * 256 * ROWB);
+          const uint32_t zl = smem_u32(base + L.zl) + uint32_t(hh * 256 * ROWB);
+          // The small correction products (x.Z_lo, x_lo.Z_hi) go into the fresh
+          // accumulator first and the large x_hi.Z_hi products last: each
+          // tensor-core accumulation rounds relative to the running magnitude,
+          // so this order adds the fewest steps at the final, largest magnitude
+          // (a measured bias of ~1e-6 in b_i when the order was interleaved).
+          if constexpr (NARROW) {
 #pragma unroll
-          for (int ks = 0; ks < 2; ++ks) {
-            const uint32_t o = uint32_t(ks * 32);
-            umma_bf16(d_tmem, umma_desc_sw64(ahi + o), umma_desc_sw64(zl + o), idesc, ks != 0);
-            umma_bf16(d_tmem, umma_desc_sw64(alo + o), umma_desc_sw64(zh + o), idesc, 1);
-          }
-#pragma unroll
-          for (int ks = 0; ks < 2; ++ks) {
-            const uint32_t o = uint32_t(ks * 32);
-            umma_bf16(d_tmem, umma_desc_sw64(ahi + o), umma_desc_sw64(zh + o), idesc, 1);
-          }
-        } else {
-#pragma unroll
-          for (int at = 0; at < natom; ++at) {
-#pragma unroll
-            for (int ks = 0; ks < 4; ++ks) {
-              const uint32_t ao = uint32_t(at * kAtomBytes + ks * 32);
-              const uint32_t bo = uint32_t(at * a.kp * 128 + ks * 32);
-              umma_bf16(d_tmem, umma_desc_sw128(ahi + ao), umma_desc_sw128(zl + bo), idesc, (at | ks) != 0);
-              if (MODE == kModeF32)
-                umma_bf16(d_tmem, umma_desc_sw128(alo + ao), umma_desc_sw128(zh + bo), idesc, 1);
+            for (int ks = 0; ks < 2; ++ks) {
+              const uint32_t o = uint32_t(ks * 32);
+              umma_bf16(d_tmem, umma_desc_sw64(ahi + o), umma_desc_sw64(zl + o), idesc, ks != 0);
+              umma_bf16(d_tmem, umma_desc_sw64(alo + o), umma_desc_sw64(zh + o), idesc, 1);
             }
-          }
 #pragma unroll
-          for (int at = 0; at < natom; ++at) {
+            for (int ks = 0; ks < 2; ++ks) {
+              const uint32_t o = uint32_t(ks * 32);
+              umma_bf16(d_tmem, umma_desc_sw64(ahi + o), umma_desc_sw64(zh + o), idesc, 1);
+            }
+          } else {
 #pragma unroll
-            for (int ks = 0; ks < 4; ++ks) {
-              const uint32_t ao = uint32_t(at * kAtomBytes + ks * 32);
-              const uint32_t bo = uint32_t(at * a.kp * 128 + ks * 32);
-              umma_bf16(d_tmem, umma_desc_sw128(ahi + ao), umma_desc_sw128(zh + bo), idesc, 1);
+            for (int at = 0; at < natom; ++at) {
+#pragma unroll
+              for (int ks = 0; ks < 4; ++ks) {
+                const uint32_t ao = uint32_t(at * kAtomBytes + ks * 32);
+                const uint32_t bo = uint32_t(at * a.kp * 128 + ks * 32);
+                umma_bf16(d_tmem, umma_desc_sw128(ahi + ao), umma_desc_sw128(zl + bo), idesc, (at | ks) != 0);
+                if (MODE == kModeF32)
+                  umma_bf16(d_tmem, umma_desc_sw128(alo + ao), umma_desc_sw128(zh + bo), idesc, 1);
+              }
+            }
+#pragma unroll
+            for (int at = 0; at < natom; ++at) {
+#pragma unroll
+              for (int ks = 0; ks < 4; ++ks) {
+                const uint32_t ao = uint32_t(at * kAtomBytes + ks * 32);
+                const uint32_t bo = uint32_t(at * a.kp * 128 + ks * 32);
+                umma_bf16(d_tmem, umma_desc_sw128(ahi + ao), umma_desc_sw128(zh + bo), idesc, 1);
+              }
             }
           }
         }
@@ -648,7 +703,7 @@ __global__ void __launch_bounds__(tc_threads(DP, CG), 1) k_score_tc(TcK a, const
       if (*abort_flag && t > 0) {
         // the last committed accumulator must be complete before TMEM is freed
         const int u = t - 1;
-        mbar_wait(&B.accfull[u & 1], uint32_t((u >> 1) & 1));
+        mbar_wait(&B.accfull[u & sl_mask], uint32_t((u >> sl_shift) & 1));
       }
     }
   } else if (warp < EPI0) {
@@ -669,11 +724,11 @@ __global__ void __launch_bounds__(tc_threads(DP, CG), 1) k_score_tc(TcK a, const
       int own;
       if (STAGED) {
         const int j = t % a.nxs;
-        if (!tc_wait(&B.xfull[j], (t / a.nxs) & 1, abort_flag, a.status)) break;
+        if (!tc_wait(&B.xfull[j], (t / a.nxs) & 1, abort_flag, sts)) break;
         // FP8 writes the A operand while it reads the stage; FP32 waits for its
         // A buffer only after the row terms (the MMA of the previous tile in
         // that buffer overlaps them)
-        if (MODE == kModeFP8 && !tc_wait(&B.aempty[i], ((t / a.nab) & 1) ^ 1, abort_flag, a.status)) break;
+        if (MODE == kModeFP8 && !tc_wait(&B.aempty[i], ((t / a.nab) & 1) ^ 1, abort_flag, sts)) break;
         const unsigned char* xs = base + L.xs + j * L.xs_stride;
         if (MODE == kModeF32) {
 #pragma unroll
@@ -733,7 +788,7 @@ __global__ void __launch_bounds__(tc_threads(DP, CG), 1) k_score_tc(TcK a, const
         __syncwarp();
         if (lane == 0) mbar_arrive(&B.xempty[j]);
       } else {
-        if (!tc_wait(&B.afull[i], (t / a.nab) & 1, abort_flag, a.status)) break;
+        if (!tc_wait(&B.afull[i], (t / a.nab) & 1, abort_flag, sts)) break;
 #pragma unroll
         for (int c8 = 0; c8 < HP / 8; ++c8) {
           const int col = h * HP + 8 * c8;
@@ -749,8 +804,8 @@ __global__ void __launch_bounds__(tc_threads(DP, CG), 1) k_score_tc(TcK a, const
         own = reinterpret_cast<const int32_t*>(reinterpret_cast<unsigned char*>(side) + kTM * 16)[r];
       }
       bool valid = row < a.n;
-      if (valid && (own < 0 || own >= a.k)) {
-        if (h == 0) set_status(a.status, SIL_ELABEL);
+      if (valid && (own < 0 || own >= kall)) {
+        if (h == 0) set_status(sts, SIL_ELABEL);
         valid = false;
       }
       float inv = 1.f;
@@ -764,7 +819,7 @@ __global__ void __launch_bounds__(tc_threads(DP, CG), 1) k_score_tc(TcK a, const
         float ss = ss2.x + ss2.y;
         ss += __shfl_xor_sync(0xffffffffu, ss, 16);
         if (valid && !(ss > 0.f)) {
-          if (h == 0) set_status(a.status, SIL_EZERONORM);
+          if (h == 0) set_status(sts, SIL_EZERONORM);
           valid = false;
         }
         inv = ss > 0.f ? rsqrtf(ss) : 0.f;
@@ -786,7 +841,7 @@ __global__ void __launch_bounds__(tc_threads(DP, CG), 1) k_score_tc(TcK a, const
           if (a.zst)  // staged centroids (uniform branch)
             z = *reinterpret_cast<const float4*>(zsm + olc * a.zst + col);
           else
-            z = __ldg(reinterpret_cast<const float4*>(a.zf + int64_t(kb0 + olc) * a.dz + col));
+            z = __ldg(reinterpret_cast<const float4*>(zfp + int64_t(kb0 + olc) * a.dz + col));
         }
         const float2 xa = make_float2(x[4 * c4], x[4 * c4 + 1]), xb = make_float2(x[4 * c4 + 2], x[4 * c4 + 3]);
         const float2 ca = __ffma2_rn(xa, inv2, make_float2(-g.x, -g.y));
@@ -802,7 +857,7 @@ __global__ void __launch_bounds__(tc_threads(DP, CG), 1) k_score_tc(TcK a, const
       xn2s += __shfl_xor_sync(0xffffffffu, xn2s, 16);
       aes += __shfl_xor_sync(0xffffffffu, aes, 16);
       if (MODE == kModeF32) {
-        if (!tc_wait(&B.aempty[i], ((t / a.nab) & 1) ^ 1, abort_flag, a.status)) break;
+        if (!tc_wait(&B.aempty[i], ((t / a.nab) & 1) ^ 1, abort_flag, sts)) break;
         // hi/lo BF16 split of this half row into the swizzled A buffer
 #pragma unroll
         for (int c8 = 0; c8 < HP / 8; ++c8) {
@@ -828,7 +883,7 @@ __global__ void __launch_bounds__(tc_threads(DP, CG), 1) k_score_tc(TcK a, const
         // for their slot
         __syncwarp();
         if (lane == 0) mbar_arrive(&B.afull[i]);
-        if (!tc_wait(&B.sempty[sl], ((t / kSideSlots) & 1) ^ 1, abort_flag, a.status)) break;
+        if (!tc_wait(&B.sempty[sl], ((t / kSideSlots) & 1) ^ 1, abort_flag, sts)) break;
       }
       if (h == 0) {
         float aown = 0.f;
@@ -850,15 +905,19 @@ __global__ void __launch_bounds__(tc_threads(DP, CG), 1) k_score_tc(TcK a, const
     // ---------------------------------------------- epilogue warps EPI0..
     const int q = warp & 3;       // TMEM lane quarter this warp may access
     const int r = q * 32 + lane;  // tile row = TMEM lane
-    const int eg = (warp - EPI0) >> 2;  // this warp's group takes tiles eg, eg + EG, ...
-    const float rb = tc_cond_radius(a.cl, a.k, gsm, DP, lane);
+    // this warp's group takes tiles eg, eg + EG, ... and owns accumulator eg;
+    // with a single (wide) accumulator group 0 takes every tile, so that no
+    // group waits on a barrier phase the other group's tile also completes
+    const int eg = (warp - EPI0) >> 2;
+    const int egs = nslot == 2 ? EG : 1;
+    const float rb = tc_cond_radius(clp, kall, gsm, DP, lane);
     float tsum = 0.f;
-    for (int t = eg; t < my_tiles; t += EG) {
-      const int i = t % a.nab, bsel = t & 1, sl = STAGED ? t % kSideSlots : i;
-      if (!tc_wait(&B.accfull[bsel], (t >> 1) & 1, abort_flag, a.status)) break;
+    for (int t = eg; eg < egs && t < my_tiles; t += egs) {
+      const int i = t % a.nab, bsel = t & sl_mask, sl = STAGED ? t % kSideSlots : i;
+      if (!tc_wait(&B.accfull[bsel], (t >> sl_shift) & 1, abort_flag, sts)) break;
       if (STAGED) {
-        if (!tc_wait(&B.sfull[sl], (t / kSideSlots) & 1, abort_flag, a.status)) break;
-      } else if (!tc_wait(&B.pfull[i], (t / a.nab) & 1, abort_flag, a.status)) {
+        if (!tc_wait(&B.sfull[sl], (t / kSideSlots) & 1, abort_flag, sts)) break;
+      } else if (!tc_wait(&B.pfull[i], (t / a.nab) & 1, abort_flag, sts)) {
         break;
       }
       tc_fence_after();
@@ -868,17 +927,17 @@ __global__ void __launch_bounds__(tc_threads(DP, CG), 1) k_score_tc(TcK a, const
       const int own = code >= 0 ? code : (row_ok && code <= -2 ? -2 - code : -1);  // in-block index
       const float sc = -2.f * side[2 * kTM + r];
       const float xn2 = side[r];
-      const uint32_t tbase = tmem + uint32_t(bsel * a.acc_cols) + (uint32_t(q * 32) << 16);
+      const uint32_t tbase = tmem + uint32_t(bsel * acc_cols) + (uint32_t(q * 32) << 16);
       int kb = -1;
       // two warpgroups keep half the registers each: two loads in flight
-      const float best = tc_lane_min<TRACK, EG == 2 ? 2 : 4>(tbase, a.kp, cbs, sc, own, kb);
+      const float best = tc_lane_min<TRACK, EG == 2 ? 2 : 4>(tbase, kpc, cbs, sc, own, kb);
       // The GEMM ranks the clusters; for ill-conditioned rows b_i is then the
       // nearest cluster's distance in the difference form, like a_i, from the
       // point's operand row: its A buffer (held until this has been read), or,
       // for FP32 plans without the argmin pass, the row read back from global
       // memory and rounded to the same hi + lo bits.
       const bool exact = row_ok && best < INFINITY && tc_ill_conditioned(xn2, best, rb);
-      if (!TRACK && __any_sync(0xffffffffu, exact)) kb = tc_lane_find(tbase, a.kp, cbs, sc, own, best, exact);
+      if (!TRACK && __any_sync(0xffffffffu, exact)) kb = tc_lane_find(tbase, kpc, cbs, sc, own, best, exact);
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&B.accempty[bsel]);
@@ -889,11 +948,11 @@ __global__ void __launch_bounds__(tc_threads(DP, CG), 1) k_score_tc(TcK a, const
         const float wn = co.y > 0.f ? co.z / co.y : 0.f;  // W_k / n_k
         if (ROWS_GLOBAL) {
           dk = wn + tc_row_dist_global<true>(a.xg + row * a.ldx, a.d, side[2 * kTM + r], gsm,
-                                             a.zst ? zsm + kb * a.zst : a.zf + int64_t(kb0 + kb) * a.dz);
+                                             a.zst ? zsm + kb * a.zst : zfp + int64_t(kb0 + kb) * a.dz);
         } else {
-          if (!STAGED) tc_wait(&B.afull[i], (t / a.nab) & 1, abort_flag, a.status);  // TMA-written rows
+          if (!STAGED) tc_wait(&B.afull[i], (t / a.nab) & 1, abort_flag, sts);  // TMA-written rows
           dk = wn + tc_row_dist<MODE, DP>(base + L.abuf + i * L.abuf_stride, L.lo_off, r, side[2 * kTM + r], gsm,
-                                          csm, a.zst ? zsm + kb * a.zst : nullptr, a.zf + int64_t(kb0 + kb) * a.dz,
+                                          csm, a.zst ? zsm + kb * a.zst : nullptr, zfp + int64_t(kb0 + kb) * a.dz,
                                           a.dz);
         }
       }
@@ -924,10 +983,10 @@ __global__ void __launch_bounds__(tc_threads(DP, CG), 1) k_score_tc(TcK a, const
           }
           tsum += sv;
         } else {
-          const int64_t o = int64_t(blockIdx.y) * a.n + row;
+          const int64_t o = plane * a.n + row;
           a.pmin[o] = row_ok ? dk : __int_as_float(0x7fc00000);
           if (TRACK && a.parg) a.parg[o] = (row_ok && dk < INFINITY) ? kb0 + kb : -1;
-          if (own >= 0) a.pown[row] = side[kTM + r];
+          if (own >= 0) a.pown[own_plane * a.n + row] = side[kTM + r];
         }
       }
       // BF16: the A buffer (refilled by TMA) also holds the labels of the slot
@@ -944,14 +1003,14 @@ __global__ void __launch_bounds__(tc_threads(DP, CG), 1) k_score_tc(TcK a, const
       if (warp == EPI0 && lane == 0) {
         double p = 0.0;
         for (int w = 0; w < 4 * EG; ++w) p += double(red[w]);
-        a.partials[blockIdx.x] = p;
+        a.partials[pidx] = p;
       }
     }
   }
   __syncthreads();
   if (warp == 1) {
     tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * a.acc_cols)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(nslot * acc_cols)
                  : "memory");
   }
 }
@@ -1388,23 +1447,59 @@ __global__ void k_tc_combine(int64_t n, int32_t k, int32_t nblk, const int32_t* 
   }
 }
 
-// Split centroids and per-cluster constants for the tensor-core kernel:
-//   zh/zl (bf16 [kpad][dp], zero padded) with zh + zl ~ (cs *) mu'_k to ~16 bits,
-//   cb[k] = bias_k + 2 g.(zh + zl)_k (+inf for empty clusters and padding).
+// The labelings of a batched launch whose clusters span several blocks:
+// multi[blockIdx.y] names one (its first block's item); each CTA takes rows
+// blockIdx.x, + gridDim.x, ... and writes the labeling's partial sum
+// partials[b * gridDim.x + blockIdx.x] (the slot its fused form would use).
+__global__ void k_tc_combine_items(const TcItem* multi, int64_t n, const int32_t* labels, int64_t ldl,
+                                   const float4* cl_all, float scale, int32_t rms, const float* planes,
+                                   const float* own_planes, double* partials) {
+  const TcItem it = multi[blockIdx.y];
+  const int32_t* lab = labels + int64_t(it.b) * ldl;
+  const float4* cl = cl_all + it.cl_off;
+  float tsum = 0.f;
+  for (int64_t row = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; row < n;
+       row += int64_t(gridDim.x) * blockDim.x) {
+    const int own = lab[row];
+    float best = INFINITY, sv = 0.f;
+    bool bad = own < 0 || own >= it.k;
+    for (int g = 0; g < it.nblk && !bad; ++g) {
+      const float v = planes[(int64_t(it.plane) + g) * n + row];
+      if (v != v) bad = true;  // NaN marks a row the scoring kernel rejected
+      else best = fminf(best, v);
+    }
+    if (!bad && best < INFINITY && cl[own].w > 1.5f)
+      sv = sil_eq2(fmaxf(0.f, scale * own_planes[int64_t(it.own_plane) * n + row]), fmaxf(0.f, scale * best),
+                   rms != 0);
+    tsum += sv;
+  }
+  __shared__ float red[32];
+  for (int o = 16; o > 0; o >>= 1) tsum += __shfl_xor_sync(0xffffffffu, tsum, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = tsum;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < int(blockDim.x >> 5); ++w) t += double(red[w]);
+    partials[int64_t(it.b) * gridDim.x + blockIdx.x] = t;
+  }
+}
+
+// Split centroids and per-cluster constants for the tensor-core kernel, one
+// row kk (one CTA):
+//   zh/zl (bf16 [dp], zero padded) with zh + zl ~ (cs *) mu'_k to ~16 bits,
+//   cb = bias_k + 2 g.(zh + zl)_k (+inf for empty clusters and padding).
 // With FP8 storage the column scales cs are folded into the split values.
-__global__ void k_tc_pack(const float* zf, const float4* cl, const double* g, const float* cs, int32_t k,
-                          int32_t d, int32_t dz, int32_t dp, __nv_bfloat16* zh, __nv_bfloat16* zl,
-                          float* cb) {
+__device__ void tc_pack_row(int kk, const float* zf, const float4* cl, const double* g, const float* cs, int32_t k,
+                            int32_t d, int32_t dz, int32_t dp, __nv_bfloat16* zh, __nv_bfloat16* zl, float* cb) {
   __shared__ double red[32];
-  const int kk = blockIdx.x;
   double dot = 0.0;
   for (int c = threadIdx.x; c < dp; c += blockDim.x) {
     const float z = (kk < k && c < dz) ? zf[int64_t(kk) * dz + c] : 0.f;
     const float zs = cs ? (c < d ? z * cs[c] : 0.f) : z;
     const __nv_bfloat16 hh = __float2bfloat16_rn(zs);
     const __nv_bfloat16 ll = __float2bfloat16_rn(zs - __bfloat162float(hh));
-    zh[int64_t(kk) * dp + c] = hh;
-    zl[int64_t(kk) * dp + c] = ll;
+    zh[c] = hh;
+    zl[c] = ll;
     // The centring term uses the split value the GEMM actually sees, so the
     // split's residual enters d_k only through x' = x - g (zero mean), not as
     // a per-cluster offset g.(mu' - hi - lo).
@@ -1421,8 +1516,28 @@ __global__ void k_tc_pack(const float* zf, const float4* cl, const double* g, co
     for (int w = 0; w < int(blockDim.x >> 5); ++w) t += red[w];
     float v = INFINITY;
     if (kk < k && cl[kk].w > 0.5f) v = float(double(cl[kk].x) + 2.0 * t);
-    cb[kk] = v;
+    *cb = v;
   }
+}
+
+// Split centroids of one labeling: rows 0..kpad-1 (one CTA each).
+__global__ void k_tc_pack(const float* zf, const float4* cl, const double* g, const float* cs, int32_t k,
+                          int32_t d, int32_t dz, int32_t dp, __nv_bfloat16* zh, __nv_bfloat16* zl,
+                          float* cb) {
+  const int kk = blockIdx.x;
+  tc_pack_row(kk, zf, cl, g, cs, k, d, dz, dp, zh + int64_t(kk) * dp, zl + int64_t(kk) * dp, cb + kk);
+}
+
+// Split centroids of every labeling of a batched launch: labeling blockIdx.y,
+// its rows 0..kp-1 at rows zrow.. of the packed arrays.
+__global__ void k_tc_pack_items(const TcItem* items, const float* zf_all, const float4* cl_all, const double* g_all,
+                                int32_t d, int32_t dz, int32_t dp, __nv_bfloat16* zh, __nv_bfloat16* zl, float* cb) {
+  const TcItem it = items[blockIdx.y];
+  const int kk = blockIdx.x;
+  if (kk >= it.kp) return;
+  const int64_t r = int64_t(it.zrow) + kk;
+  tc_pack_row(it.kb0 + kk, zf_all + it.zf_off, cl_all + it.cl_off, g_all + it.g_off, nullptr, it.k, d, dz, dp,
+              zh + r * dp, zl + r * dp, cb + r);
 }
 
 int pow2_at_least(int v) {
@@ -1723,6 +1838,8 @@ cudaError_t launch_score_tc(const ScoreLaunch& s, const double* g, void* pack, v
   k.skstar = s.skstar;
   k.partials = s.partials;
   k.status = status;
+  k.zbox_rows = kp;
+  k.items = nullptr;
   const bool save = s.sa != nullptr;
   // the kernels built for the backward record track the argmin in the main
   // pass; without the record they serve rank = 1 plans
@@ -1781,6 +1898,134 @@ cudaError_t launch_tc_combine(int64_t n, int32_t k, int32_t nblk, const int32_t*
   k_tc_combine<<<cgrid, 256, 0, stream>>>(n, k, nblk, labels, cl, scale, rms, pmin, parg, pown, s_out, sa, sb,
                                           skstar, partials);
   *n_partials = cgrid;
+  return cudaGetLastError();
+}
+
+bool tc_batched_eligible(int32_t dtype, int64_t n, int32_t d, int64_t ldx, int32_t kmax, const void* X,
+                         const int32_t* labels, int64_t ldl) {
+  if (dtype != SIL_F32 || kmax > 512 || d < 32 || d > 64) return false;
+  if (ldl % 4 != 0) return false;  // 16-byte rows of the labels map
+  if (!tc_eligible(dtype, n, d, ldx, std::min(kmax, 256), X, labels)) return false;
+  return tc_batched_pack_bytes(1, kmax, d) > 0;
+}
+
+// Launch plan of the batched launch: row ranges (CTAs per labeling block)
+// and A-operand buffers (0: the deepest ring that fits); set by an autotuner.
+std::atomic<int> g_batched_ranges{8};
+std::atomic<int> g_batched_nab{0};
+
+int tc_batched_ranges() { return g_batched_ranges.load(); }
+
+int tc_batched_plan_set(int32_t ranges, int32_t a_buffers) {
+  if (ranges < 1 || ranges > kBatchedMaxRanges || (a_buffers != 0 && a_buffers != 2 && a_buffers != 4))
+    return SIL_EINVAL;
+  g_batched_ranges.store(ranges);
+  g_batched_nab.store(a_buffers);
+  return SIL_OK;
+}
+
+namespace {
+// ring depths of the batched launch for rows of dp columns and blocks of up to
+// 256 clusters (wider labelings are split into two blocks)
+bool tc_batched_plan(int dp, int* nab, int* nxs, int* smem) {
+  const int want = g_batched_nab.load();
+  for (int b = 4; b >= 2; b -= 2) {
+    if (want && b != want) continue;
+    const int sm = tc_smem(kModeF32, dp, 256, 2, b, 0).total;
+    if (sm <= kSmemMax) {
+      *nab = b;
+      *nxs = 2;
+      *smem = sm;
+      return true;
+    }
+  }
+  return false;
+}
+}  // namespace
+
+size_t tc_batched_pack_bytes(int32_t batch, int32_t kmax, int32_t d) {
+  const int dp = tc_dp(d), kmaxp = int(round_up(std::max(kmax, 16), 16));
+  int nab, nxs, smem;
+  if (!tc_batched_plan(dp, &nab, &nxs, &smem)) return 0;
+  // the blocks of a labeling (at most two) are at most 31 rows wider than its clusters
+  const size_t rows = size_t(batch) * size_t(kmaxp + 32);
+  return align256(rows * size_t(dp) * 2) * 2 + align256(rows * 4);
+}
+
+cudaError_t launch_score_tc_batched(const void* X, int64_t n, int32_t d, int64_t ldx, const int32_t* labels,
+                                    int64_t ldl, int32_t batch, int32_t kmax, int32_t dist, const TcItem* items,
+                                    int32_t n_items, int32_t total_zrows, const TcItem* multi, int32_t n_multi,
+                                    const float* zf_all, const float4* cl_all, const double* g_all,
+                                    const float* gf_all, void* pack, float* planes, float* own_planes,
+                                    double* partials, uint32_t* status_all, cudaStream_t stream) {
+  const int dp = tc_dp(d), dz = int(round_up(d, 4));
+  int nab = 0, nxs = 0, smem = 0;
+  if (!tc_batched_plan(dp, &nab, &nxs, &smem)) return cudaErrorInvalidValue;
+  const size_t rows = size_t(batch) * size_t(round_up(std::max(kmax, 16), 16) + 32);
+  __nv_bfloat16* zh = static_cast<__nv_bfloat16*>(pack);
+  __nv_bfloat16* zl = reinterpret_cast<__nv_bfloat16*>(static_cast<char*>(pack) + align256(rows * size_t(dp) * 2));
+  float* cb = reinterpret_cast<float*>(static_cast<char*>(pack) + 2 * align256(rows * size_t(dp) * 2));
+  k_tc_pack_items<<<dim3(256u, unsigned(n_items)), 128, 0, stream>>>(items, zf_all, cl_all, g_all, d, dz, dp, zh,
+                                                                     zl, cb);
+  cudaError_t err = cudaGetLastError();
+  if (err != cudaSuccess) return err;
+  TcMaps maps{};
+  const uint32_t zbox = dp == 32 ? 32 : 64;
+  const CUtensorMapSwizzle zsw = dp == 32 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B;
+  if (!encode_tmap_2d(&maps.x, X, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, uint64_t(d), uint64_t(n), uint64_t(ldx) * 4, 32,
+                      kTM, CU_TENSOR_MAP_SWIZZLE_128B) ||
+      !encode_tmap_2d(&maps.lab, labels, CU_TENSOR_MAP_DATA_TYPE_INT32, 4, uint64_t(n), uint64_t(batch),
+                      uint64_t(ldl) * 4, kTM, 1, CU_TENSOR_MAP_SWIZZLE_NONE) ||
+      !encode_tmap_2d(&maps.zh, zh, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, uint64_t(dp), uint64_t(total_zrows),
+                      uint64_t(dp) * 2, zbox, 16, zsw) ||
+      !encode_tmap_2d(&maps.zl, zl, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, uint64_t(dp), uint64_t(total_zrows),
+                      uint64_t(dp) * 2, zbox, 16, zsw))
+    return cudaErrorInvalidValue;
+  TcK k{};
+  k.n = n;
+  k.d = d;
+  k.k = kmax;
+  k.kp = 256;  // shared-memory layout for the widest block
+  k.nblk = 1;
+  k.acc_cols = 256;
+  k.dz = dz;
+  k.cosine = dist == SIL_COSINE;
+  k.rms = dist == SIL_EUCLIDEAN_RMS;
+  k.scale = dist == SIL_COSINE ? 0.5f : 1.f;
+  k.nxs = nxs;
+  k.nab = nab;
+  k.zst = 0;
+  k.xg = static_cast<const float*>(X);
+  k.ldx = ldx;
+  k.zf = zf_all;
+  k.cl = cl_all;
+  k.gf = gf_all;
+  k.cb = cb;
+  k.partials = partials;
+  k.pmin = planes;
+  k.pown = own_planes;
+  k.status = status_all;
+  k.zbox_rows = 16;
+  k.items = items;
+  const unsigned ranges = unsigned(tc_batched_ranges());
+  const dim3 grid(ranges, unsigned(n_items));
+  const int cg = tc_conv_groups(kModeF32, dp, 256);
+  auto launch = [&](auto fn, int threads) {
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    fn<<<grid, threads, smem, stream>>>(k, maps);
+    return cudaGetLastError();
+  };
+  cudaError_t e;
+  if (dp == 32)
+    e = cg == 2 ? launch(k_score_tc<kModeF32, 32, true, 2, true>, tc_threads(32, 2))
+                : launch(k_score_tc<kModeF32, 32, true, 1, true>, tc_threads(32, 1));
+  else
+    e = cg == 2 ? launch(k_score_tc<kModeF32, 64, true, 2, true>, tc_threads(64, 2))
+                : launch(k_score_tc<kModeF32, 64, true, 1, true>, tc_threads(64, 1));
+  if (e != cudaSuccess || n_multi == 0) return e;
+  k_tc_combine_items<<<dim3(ranges, unsigned(n_multi)), 256, 0, stream>>>(multi, n, labels, ldl, cl_all, k.scale,
+                                                                         k.rms, planes, own_planes, partials);
   return cudaGetLastError();
 }
 

@@ -72,6 +72,9 @@ struct WsLayout {
   size_t zbf;       // bf16 centroid tiles for the tensor path
   size_t tcp;       // tensor path with several cluster blocks: per-block minima
   size_t batch;     // batched aggregates
+  // batched tensor-core launch (several labelings, k_max <= 512): per labeling
+  // status words, items, finalized constants, packed centroids, CTA sums
+  size_t bst, bitems, bmulti, bzf, bcl, bg, bgf, bpack, bpart, bplanes, bown;
   size_t total;
 };
 
@@ -209,6 +212,19 @@ struct FinLaunch {
 };
 cudaError_t launch_finalize(const FinLaunch& f);
 
+// One labeling of a batched tensor-core launch (CTA row blockIdx.y): its
+// cluster count, block width (MMA N, up to 512 as two MMAs), first row in the
+// packed centroids of all labelings, and offsets of its finalized constants
+// (float4 cluster terms, FP32 centred centroids, global centre).
+struct TcItem {
+  int32_t b;       // labeling (row of labels, status word, partial-sum slots)
+  int32_t k, nblk; // clusters of the labeling and its blocks
+  int32_t kb0, kp; // first cluster of this block and its width (MMA N)
+  int32_t zrow;    // first row of this block in the packed centroids
+  int32_t cl_off, zf_off, g_off;  // the labeling's finalized constants
+  int32_t plane, own_plane;       // several blocks: result planes (else -1)
+};
+
 struct ScoreLaunch {
   const void* X;
   int32_t dtype;
@@ -267,6 +283,31 @@ size_t t32_pack_bytes(int32_t k, int32_t d);
 size_t t32_partial_bytes(int64_t n, int32_t d, int32_t k);
 cudaError_t launch_score_tf32(const ScoreLaunch& s, const double* g, void* pack, void* partial_ws,
                               size_t partial_bytes, uint32_t* status);
+// Batched tensor-core pass 2: every labeling in one launch (grid.y = labeling,
+// grid.x = row ranges).  Eligibility (k_max <= 512, FP32 rows of 32 or 64
+// columns padded, 16-byte aligned X, labels rows and strides), and the launch
+// from finalized constants of all labelings (items on the device); partials
+// get batch x (*ranges) sums.  Host-side plan: ranges per labeling.
+bool tc_batched_eligible(int32_t dtype, int64_t n, int32_t d, int64_t ldx, int32_t kmax, const void* X,
+                         const int32_t* labels, int64_t ldl);
+int tc_batched_ranges();
+constexpr int kBatchedMaxRanges = 64;
+int tc_batched_plan_set(int32_t ranges, int32_t a_buffers);
+size_t tc_batched_pack_bytes(int32_t batch, int32_t kmax, int32_t d);
+cudaError_t launch_score_tc_batched(const void* X, int64_t n, int32_t d, int64_t ldx, const int32_t* labels,
+                                    int64_t ldl, int32_t batch, int32_t kmax, int32_t dist, const TcItem* items,
+                                    int32_t n_items, int32_t total_zrows, const TcItem* multi, int32_t n_multi,
+                                    const float* zf_all, const float4* cl_all, const double* g_all,
+                                    const float* gf_all, void* pack, float* planes, float* own_planes,
+                                    double* partials, uint32_t* status_all, cudaStream_t stream);
+// S_out[b] = (sum of partials[b * np .. b * np + np)) / n, NaN when status[b]
+// is non-zero (OR-ed into user_status).
+cudaError_t launch_reduce_S_batched(const double* partials, int32_t np, int64_t n, int32_t batch,
+                                    const uint32_t* status, uint32_t* user_status, double* S_out,
+                                    cudaStream_t stream);
+// S = sum_c n_c S_c / sum_c n_c over m row chunks (device arrays).
+cudaError_t launch_chunk_mean(const double* S_chunks, const int64_t* n_chunks, int32_t m, double* S_out,
+                              cudaStream_t stream);
 // S = sum(partials)/n, NaN when the workspace status word is non-zero; the
 // word is OR-ed into user_status.
 cudaError_t launch_reduce_S(const double* partials, int32_t np, int64_t n, const uint32_t* ws_status,

@@ -11,7 +11,7 @@ Entry points mirror the C names:
   score_backward(X, labels, K, agg, ...)-> dX                  sil_score_backward
   score_batched(X, labels, ks, ...)     -> S[B]                sil_score_batched
   score_euclidean(X, labels, K, ...)    -> Score(S, s, saved)  sil_score_euclidean (exact, O(N^2))
-  silhouette(X, labels, K, ...)         -> S (aggregate + score)
+  silhouette(X, labels, K, ...)         -> Score(S, s, saved)  sil_silhouette (both passes, one call)
   silhouette_chunked(X_host, labels_host, K, ...)
                                         -> S of host-resident data streamed in row chunks
 Results stay on the device and nothing synchronises; ``check_status`` reads
@@ -42,8 +42,8 @@ METRICS = {"sqeuclidean": 0, "cosine": 1, "euclidean_rms": 2}
 PATHS = {"auto": 0, "simt": 1, "tensor": 2, "tensor_tf32": 3}
 EXPORTED = ("sil_workspace_size", "sil_saved_size", "sil_aggregate", "sil_score",
             "sil_score_backward", "sil_score_batched", "sil_tensor_plan", "sil_tensor_plan_candidates",
-            "sil_tensor_plan_set", "sil_tensor_kernel", "sil_score_noalloc", "sil_score_euclidean",
-            "sil_euclidean_workspace_size", "sil_selftest_bounded_wait", "sil_status_string",
+            "sil_tensor_plan_set", "sil_tensor_kernel", "sil_batched_plan_set", "sil_chunk_mean", "sil_score_noalloc", "sil_score_euclidean",
+            "sil_euclidean_workspace_size", "sil_silhouette", "sil_selftest_bounded_wait", "sil_status_string",
             "sil_version")
 
 _lock = threading.Lock()
@@ -80,6 +80,9 @@ def load(build_if_stale: bool = True) -> ctypes.CDLL:
             lib.sil_score.argtypes = [vp, i32, i64, i32, i64, vp, vp, i32, i32, vp, vp, vp, vp, vp,
                                       vp, i32, vp, sz, vp, vp]
             lib.sil_score.restype = ctypes.c_int
+            lib.sil_silhouette.argtypes = [vp, i32, i64, i32, i64, vp, vp, i32, i32, vp, vp, vp, vp, vp,
+                                           vp, i32, vp, sz, vp, vp]
+            lib.sil_silhouette.restype = ctypes.c_int
             lib.sil_score_backward.argtypes = [vp, i32, i64, i32, i64, vp, vp, i32, i32, vp, vp, vp,
                                                vp, vp, vp, i64, vp, sz, vp, vp]
             lib.sil_score_backward.restype = ctypes.c_int
@@ -99,6 +102,10 @@ def load(build_if_stale: bool = True) -> ctypes.CDLL:
             lib.sil_score_euclidean.restype = ctypes.c_int
             lib.sil_euclidean_workspace_size.argtypes = [i64, i32, i32]
             lib.sil_euclidean_workspace_size.restype = sz
+            lib.sil_chunk_mean.argtypes = [vp, vp, i32, vp, vp]
+            lib.sil_chunk_mean.restype = ctypes.c_int
+            lib.sil_batched_plan_set.argtypes = [i32, i32]
+            lib.sil_batched_plan_set.restype = ctypes.c_int
             lib.sil_tensor_kernel.argtypes = [i32, i32, i32]
             lib.sil_tensor_kernel.restype = ctypes.c_int
             lib.sil_selftest_bounded_wait.argtypes = [vp, vp]
@@ -415,11 +422,45 @@ def autotune(X: torch.Tensor, labels: torch.Tensor, K: int, metric: str = "sqeuc
     return results
 
 
+def batched_plan_set(ranges: int = 8, a_buffers: int = 0) -> None:
+    """Plan of the one-launch batched pass 2: CTAs per labeling block and A buffers (0: model)."""
+    _rc(load().sil_batched_plan_set(int(ranges), int(a_buffers)), "sil_batched_plan_set")
+
+
+def serves_one_launch(X: torch.Tensor, labels: torch.Tensor, ks) -> bool:
+    """Whether sil_score_batched runs every labeling's pass 2 as one launch for these inputs."""
+    N, D = X.shape
+    return (X.dtype == torch.float32 and 32 <= D <= 64 and max(int(k) for k in ks) <= 512
+            and labels.stride(0) % 4 == 0 and X.stride(0) % 4 == 0 and "split" in tensor_kernels(X.dtype, D, 256))
+
+
 def autotune_batched(X: torch.Tensor, labels: torch.Tensor, ks, metric: str = "sqeuclidean",
                      col_scale: torch.Tensor | None = None, max_plans: int = 4, reps: int = 2):
-    """:func:`autotune` for each distinct k of a batch of labelings (B x N)
-    that the split-precision kernel serves, on the first labeling with that k.
-    Returns {k: fastest plan} (None where another kernel scores the shape)."""
+    """Pick launch plans of sil_score_batched by timing them on these inputs.
+
+    Where every labeling's pass 2 runs as one launch: the plan of that launch
+    (CTAs per labeling block in 4, 8, 16, 32 and 2 or 4 A buffers), timed on
+    the whole batched call; returns {"one_launch": (ranges, a_buffers)}.
+    Otherwise :func:`autotune` for each distinct k that the split-precision
+    kernel serves, on the first labeling with that k; returns {k: fastest
+    plan} (None where another kernel scores the shape)."""
+    if serves_one_launch(X, labels, ks):
+        stream = torch.cuda.current_stream(X.device)
+        results = []
+        for ranges in (4, 8, 16, 32):
+            for nab in (2, 4):
+                batched_plan_set(ranges, nab)
+                score_batched(X, labels, ks, metric, col_scale=col_scale)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                for _ in range(reps):
+                    score_batched(X, labels, ks, metric, col_scale=col_scale)
+                e1.record(stream)
+                torch.cuda.synchronize(X.device)
+                results.append((e0.elapsed_time(e1) / reps, (ranges, nab)))
+        best_plan = min(results)[1]
+        batched_plan_set(*best_plan)
+        return {"one_launch": best_plan, "timings_ms": results}
     best = {}
     for b, k in enumerate(int(k) for k in ks):
         if k in best:
@@ -453,11 +494,28 @@ def score_euclidean(X: torch.Tensor, labels: torch.Tensor, K: int, col_scale: to
 
 def silhouette(X: torch.Tensor, labels: torch.Tensor, K: int, metric: str = "sqeuclidean",
                col_scale: torch.Tensor | None = None, want_s: bool = False,
-               path: str = "auto", status: torch.Tensor | None = None) -> Score:
-    """Both passes: the Silhouette S (and optionally every s_i) of one labeling."""
-    agg = aggregate(X, labels, K, metric, col_scale=col_scale, status=status)
-    return score(X, labels, K, agg, metric, col_scale=col_scale, want_s=want_s, path=path,
-                 status=status)
+               path: str = "auto", status: torch.Tensor | None = None, save: bool = False,
+               out=None) -> Score:
+    """Both passes: the Silhouette S (and optionally every s_i) of one labeling,
+    in one call of sil_silhouette.  ``out`` = (count, s1, s2) device tensors
+    receive the aggregates."""
+    _check_X(X, labels)
+    lib = load()
+    N, D = X.shape
+    if out is None:
+        out = (torch.empty(K, dtype=torch.int64, device=X.device),
+               torch.empty(K, D, dtype=torch.float64, device=X.device),
+               torch.empty(K, dtype=torch.float64, device=X.device))
+    count, s1, s2 = out
+    S = torch.empty((), dtype=torch.float64, device=X.device)
+    s = torch.empty(N, dtype=torch.float32, device=X.device) if want_s else None
+    saved = torch.empty(int(lib.sil_saved_size(N)), dtype=torch.uint8, device=X.device) if save else None
+    ws, need = _ws_for(X, K, metric)
+    rc = lib.sil_silhouette(_ptr(X), _dtype_code(X), N, D, X.stride(0), _ptr(col_scale), _ptr(labels), K,
+                            METRICS[metric], _ptr(count), _ptr(s1), _ptr(s2), _ptr(s), _ptr(S), _ptr(saved),
+                            PATHS[path], _ptr(ws), need, _ptr(status), _stream_handle(X.device))
+    _rc(rc, "sil_silhouette")
+    return Score(S=S, s=s, saved=saved)
 
 
 def selftest_bounded_wait(device=None) -> tuple[int, int, int]:
@@ -482,19 +540,14 @@ def row_chunks(N: int, chunk_rows: int) -> list[tuple[int, int]]:
     return [(a, min(a + chunk_rows, N)) for a in range(0, N, chunk_rows)]
 
 
-def combine_chunk_scores(S_chunks, n_chunks) -> float:
-    """S of all rows from the means of disjoint row chunks.
-
-    S is the mean of s_i over every row (Eq. 2 averaged over the N points), so
-    with S_c the mean over chunk c of n_c rows, S = sum_c n_c S_c / sum_c n_c.
-    """
-    S_chunks, n_chunks = list(S_chunks), list(n_chunks)
-    if len(S_chunks) != len(n_chunks) or not n_chunks:
-        raise ValueError("one row count per chunk score, at least one chunk")
-    total = sum(int(n) for n in n_chunks)
-    if total <= 0:
-        raise ValueError("no rows")
-    return float(sum(float(S) * int(n) for S, n in zip(S_chunks, n_chunks)) / total)
+def chunk_mean(S_chunks: torch.Tensor, n_chunks: torch.Tensor) -> torch.Tensor:
+    """sil_chunk_mean: S of all rows from per-chunk means (device float64[m])
+    and row counts (device int64[m]), as a 0-d device float64."""
+    out = torch.empty((), dtype=torch.float64, device=S_chunks.device)
+    rc = load().sil_chunk_mean(_ptr(S_chunks), _ptr(n_chunks), int(S_chunks.numel()), _ptr(out),
+                               _stream_handle(S_chunks.device))
+    _rc(rc, "sil_chunk_mean")
+    return out
 
 
 @dataclasses.dataclass
@@ -517,9 +570,10 @@ def silhouette_chunked(X_host: torch.Tensor, labels_host: torch.Tensor, K: int,
     the row-weighted mean of the chunk means.  Each chunk is copied from host
     memory on a copy stream into one of two device buffers, so the copy of
     chunk c+1 overlaps the kernels of chunk c (pinned host tensors make the
-    copies asynchronous).  Every step of both passes runs in libsil's kernels;
-    this function only moves chunks and adds up n_c * S_c on the host.  It
-    synchronises once, at the end, and raises SilError on a data error.
+    copies asynchronous).  Every step of both passes, and the row-weighted mean
+    of the chunk means (sil_chunk_mean), runs in libsil's kernels; this
+    function only moves chunks.  It synchronises once, at the end, and raises
+    SilError on a data error.
     """
     if X_host.is_cuda or labels_host.is_cuda:
         raise ValueError("silhouette_chunked streams host tensors; use silhouette() for device data")
@@ -542,7 +596,8 @@ def silhouette_chunked(X_host: torch.Tensor, labels_host: torch.Tensor, K: int,
            torch.zeros(K, D, dtype=torch.float64, device=device),
            torch.zeros(K, dtype=torch.float64, device=device))
     status = new_status(device)
-    S_host = torch.empty(len(chunks), dtype=torch.float64).pin_memory()
+    S_dev = torch.empty(len(chunks), dtype=torch.float64, device=device)
+    n_dev = torch.tensor([b - a for a, b in chunks], dtype=torch.int64).to(device)
     s_host = torch.empty(N, dtype=torch.float32).pin_memory() if want_s else None
     compute = torch.cuda.current_stream(device)
     copy_stream = torch.cuda.Stream(device)
@@ -571,14 +626,14 @@ def silhouette_chunked(X_host: torch.Tensor, labels_host: torch.Tensor, K: int,
             for i, (a, b) in enumerate(chunks):  # pass 2: every chunk against all rows' aggregates
                 x, lab, buf = stage(len(chunks) + i, a, b)
                 r = score(x, lab, K, agg, metric, col_scale=col_scale, want_s=want_s, status=status)
-                S_host[i].copy_(r.S, non_blocking=True)
+                S_dev[i].copy_(r.S)
                 if want_s:
                     s_host[a:b].copy_(r.s, non_blocking=True)
                 consumed[buf].record(compute)
+            S = chunk_mean(S_dev, n_dev)
     finally:
         # also when a call raised: no copy may still target the buffers freed on return
         copy_stream.synchronize()
         compute.synchronize()
     check_status(status, "silhouette_chunked")
-    S = combine_chunk_scores(S_host.tolist(), [b - a for a, b in chunks])
-    return ChunkedScore(S=S, s=s_host, chunks=len(chunks))
+    return ChunkedScore(S=float(S.item()), s=s_host, chunks=len(chunks))

@@ -98,6 +98,19 @@ def test_score_path_validation(lib):
     assert rc == sil.SIL_EINVAL  # a labeling with k = 0
 
 
+def test_fused_call_validation(lib):
+    vp = ctypes.c_void_p
+
+    def call(count=vp(16), path=0, ws=vp(256), d=4, k=3):
+        return lib.sil_silhouette(vp(16), 0, 10, d, 4, None, vp(16), k, 0, count, vp(16), vp(16), None, vp(16),
+                                  None, path, ws, 1 << 30, None, None)
+    assert call(count=None) == sil.SIL_EINVAL     # aggregates are outputs here
+    assert call(path=9) == sil.SIL_EINVAL
+    assert call(d=0) == sil.SIL_EINVAL
+    assert call(k=0) == sil.SIL_EINVAL
+    assert call(ws=vp(257)) == sil.SIL_EWORKSPACE  # misaligned workspace
+
+
 def test_binding_refuses_cpu_tensors():
     import torch
     X = torch.zeros(4, 2)
@@ -237,3 +250,13 @@ def test_exact_euclidean_argument_checks(lib):
                                    None, None) == sil.SIL_EINVAL
     assert lib.sil_score_euclidean(fake, 0, 100, 8, 8, None, fake, 3, None, fake, None, None, 0,
                                    None, None) == sil.SIL_EWORKSPACE
+
+
+def test_batched_plan_set_checks(lib):
+    try:
+        assert lib.sil_batched_plan_set(0, 0) == sil.SIL_EINVAL
+        assert lib.sil_batched_plan_set(65, 0) == sil.SIL_EINVAL
+        assert lib.sil_batched_plan_set(8, 3) == sil.SIL_EINVAL
+        assert lib.sil_batched_plan_set(16, 2) == sil.SIL_OK
+    finally:
+        assert lib.sil_batched_plan_set(8, 0) == sil.SIL_OK

@@ -1,5 +1,6 @@
-"""Host logic of the out-of-core streaming call (no GPU): the row partition, and the
-combination of per-chunk means into S, pinned against the oracle."""
+"""Host logic of the out-of-core streaming call (no GPU): the row partition, the
+identity the library's combination of per-chunk means relies on (pinned against
+the oracle), and argument checks that answer before any device is touched."""
 import numpy as np
 import pytest
 import torch
@@ -38,16 +39,18 @@ def test_chunk_means_combine_to_the_mean_over_all_rows(metric):
     parts = [oracle.linear(X, lab, K, metric, agg=full["agg"], idx=np.arange(a, b)) for a, b in chunks]
     for (a, b), p in zip(chunks, parts):
         np.testing.assert_allclose(p["s"], full["s"][a:b], rtol=0, atol=1e-15)
-    S = sil.combine_chunk_scores([p["S"] for p in parts], [b - a for a, b in chunks])
+    n = np.array([b - a for a, b in chunks], dtype=np.float64)
+    S = float(np.sum(n * np.array([p["S"] for p in parts])) / n.sum())  # what sil_chunk_mean computes
     assert abs(S - full["S"]) <= 1e-15
     assert abs(S - oracle.bruteforce(X, lab, K, metric)["S"]) <= 1e-12
 
 
-def test_combine_rejects_bad_input():
-    with pytest.raises(ValueError):
-        sil.combine_chunk_scores([], [])
-    with pytest.raises(ValueError):
-        sil.combine_chunk_scores([0.5], [1, 2])
+def test_chunk_mean_rejects_bad_arguments():
+    lib = sil.load()
+    fake = __import__("ctypes").c_void_p(256)  # never dereferenced: refused on the host
+    assert lib.sil_chunk_mean(fake, fake, 0, fake, None) == sil.SIL_EINVAL
+    assert lib.sil_chunk_mean(None, fake, 3, fake, None) == sil.SIL_EINVAL
+    assert lib.sil_chunk_mean(fake, fake, 3, None, None) == sil.SIL_EINVAL
 
 
 def test_streaming_call_checks_arguments_before_touching_a_device():

@@ -45,3 +45,14 @@ def test_chunked_reports_a_bad_label():
     lab[4321] = 4  # outside [0, K)
     with pytest.raises(sil.SilError):
         sil.silhouette_chunked(torch.from_numpy(X), torch.from_numpy(lab), 4, chunk_rows=1000)
+
+
+def test_chunk_mean_is_the_row_weighted_mean():
+    import numpy as np
+    S = torch.tensor([0.5, 0.25, -0.125, 1.0], dtype=torch.float64, device="cuda")
+    n = torch.tensor([3, 1, 8, 2], dtype=torch.int64, device="cuda")
+    got = float(sil.chunk_mean(S, n))
+    ref = float(np.sum(S.cpu().numpy() * n.cpu().numpy()) / n.sum().item())
+    assert got == pytest.approx(ref, rel=1e-15, abs=1e-15)
+    S[1] = float("nan")
+    assert np.isnan(float(sil.chunk_mean(S, n)))

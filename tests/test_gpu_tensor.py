@@ -25,15 +25,21 @@ METRICS = ["sqeuclidean", "cosine"]
 
 
 def run(Xt, lt, K, metric, path, save=True, cs=None):
+    """path "<p>_fused": both passes in one sil_silhouette call; otherwise
+    sil_aggregate + sil_score."""
     st = sil.new_status(Xt.device)
-    agg = sil.aggregate(Xt, lt, K, metric, col_scale=cs, status=st)
-    r = sil.score(Xt, lt, K, agg, metric, col_scale=cs, want_s=True, save=save, path=path, status=st)
+    if path.endswith("_fused"):
+        r = sil.silhouette(Xt, lt, K, metric, col_scale=cs, want_s=True, save=save, path=path[:-6], status=st)
+    else:
+        agg = sil.aggregate(Xt, lt, K, metric, col_scale=cs, status=st)
+        r = sil.score(Xt, lt, K, agg, metric, col_scale=cs, want_s=True, save=save, path=path, status=st)
     torch.cuda.synchronize()
     return r, int(st.item())
 
 
 @pytest.mark.parametrize("metric", METRICS)
 @pytest.mark.parametrize("dtype,path", [(torch.float32, "tensor"), (torch.float32, "tensor_tf32"),
+                                        (torch.float32, "tensor_fused"), (torch.float32, "tensor_tf32_fused"),
                                         (torch.bfloat16, "tensor")])
 @pytest.mark.parametrize("N,D,K", [(1000, 64, 2), (4097, 64, 7), (20000, 64, 100), (3001, 128, 17),
                                    (5000, 100, 33), (2000, 40, 5), (300, 64, 256), (129, 64, 3),
@@ -43,7 +49,7 @@ def run(Xt, lt, K, metric, path, save=True, cs=None):
 def test_tensor_path_against_bruteforce(metric, dtype, path, N, D, K):
     if dtype == torch.bfloat16 and (D < 64 or (2 * D) % 16):
         pytest.skip("BF16 tensor path needs d >= 64 and 16-byte rows (TMA)")
-    if path == "tensor_tf32" and "tf32" not in sil.tensor_kernels(dtype, D, K):
+    if path.startswith("tensor_tf32") and "tf32" not in sil.tensor_kernels(dtype, D, K):
         pytest.skip("the TF32 kernel serves FP32 rows of 32..64 columns")
     X, lab = case(700 + N + D + K, N, D, K, metric)
     Xt, lt = to_dev(X, lab, dtype)
@@ -62,7 +68,7 @@ def test_tensor_path_against_bruteforce(metric, dtype, path, N, D, K):
 
 
 @pytest.mark.parametrize("metric", METRICS)
-@pytest.mark.parametrize("path", ["tensor", "tensor_tf32"])
+@pytest.mark.parametrize("path", ["tensor", "tensor_tf32", "tensor_fused"])
 def test_tensor_and_simt_agree_at_scale_recipe(metric, path):
     w = synth.workload_at_scale(device="cuda", N=300_000)
     ra, sa_ = run(w.X, w.labels, w.K, metric, path, save=False)
@@ -98,12 +104,47 @@ def test_tf32_far_from_origin(metric, D, K):
     np.testing.assert_allclose(b.cpu().double().numpy(), ref["b"], rtol=1e-5)
 
 
-def test_auto_picks_tensor_when_eligible():
-    X, lab = case(5, 3000, 64, 10)
+@pytest.mark.parametrize("path", ["tensor", "tensor_tf32", "simt"])
+def test_fused_call_matches_the_two_calls(path):
+    # sil_silhouette = sil_aggregate + sil_score: from the aggregates it
+    # returned, sil_score gives bit-identical s_i and saved record
+    N, D, K = 50_000, 64, 30
+    X, lab = case(79, N, D, K)
     Xt, lt = to_dev(X, lab)
-    agg = sil.aggregate(Xt, lt, 10)
-    ra = sil.score(Xt, lt, 10, agg, want_s=True, path="auto")
-    rt = sil.score(Xt, lt, 10, agg, want_s=True, path="tensor")
+    agg = (torch.empty(K, dtype=torch.int64, device="cuda"), torch.empty(K, D, dtype=torch.float64, device="cuda"),
+           torch.empty(K, dtype=torch.float64, device="cuda"))
+    st = sil.new_status(Xt.device)
+    rb = sil.silhouette(Xt, lt, K, want_s=True, save=True, path=path, status=st, out=agg)
+    ra = sil.score(Xt, lt, K, agg, want_s=True, save=True, path=path, status=st)
+    torch.cuda.synchronize()
+    assert int(st.item()) == 0
+    assert torch.equal(ra.s, rb.s) and torch.equal(ra.saved, rb.saved)
+    assert float(ra.S) == float(rb.S)
+
+
+def test_fused_call_returns_the_aggregates():
+    # the same tolerances as sil_aggregate's own parity test (the order of the
+    # rows inside a cluster's bucket, and so the FP32 run sums, may vary)
+    X, lab = case(78, 20000, 64, 30, spread=50.0)
+    Xt, lt = to_dev(X, lab)
+    out = (torch.empty(30, dtype=torch.int64, device="cuda"), torch.empty(30, 64, dtype=torch.float64, device="cuda"),
+           torch.empty(30, dtype=torch.float64, device="cuda"))
+    sil.silhouette(Xt, lt, 30, out=out)
+    rc, r1, r2 = oracle.aggregate(X.astype(np.float64), lab, 30)
+    np.testing.assert_array_equal(out[0].cpu().numpy(), rc)
+    np.testing.assert_allclose(out[1].cpu().numpy(), r1, rtol=1e-6, atol=1e-6 * np.abs(r1).max())
+    np.testing.assert_allclose(out[2].cpu().numpy(), r2, rtol=1e-6, atol=1e-6 * np.abs(r2).max())
+
+
+@pytest.mark.parametrize("K,kernel", [(10, "tensor_tf32"), (48, "tensor_tf32"), (49, "tensor"), (100, "tensor")])
+def test_auto_picks_the_tensor_kernel_by_cluster_count(K, kernel):
+    # few clusters: the TF32-ranked kernel (no converter warps); more: the
+    # split-precision kernel (one sweep over the ranked values)
+    X, lab = case(5 + K, 3000, 64, K)
+    Xt, lt = to_dev(X, lab)
+    agg = sil.aggregate(Xt, lt, K)
+    ra = sil.score(Xt, lt, K, agg, want_s=True, path="auto")
+    rt = sil.score(Xt, lt, K, agg, want_s=True, path=kernel)
     assert torch.equal(ra.s, rt.s)  # same aggregates, same kernel: bit-identical
 
 
