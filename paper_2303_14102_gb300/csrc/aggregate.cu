@@ -133,6 +133,14 @@ struct Entries {
     if (report && l != -1) set_status(status, SIL_ELABEL);
     return -1;
   }
+  // The raw label of entry e, and its bucket (-1: none); `bad` records an
+  // out-of-range label (the caller reports it once, after its loads).
+  __device__ __forceinline__ int label(int64_t e) const { return e < n ? __ldg(lab1 + e) : __ldg(lab2 + (e - n)); }
+  __device__ __forceinline__ int bucket_of(int64_t e, int l, bool& bad) const {
+    if (l >= 0 && l < k) return e < n ? l : k + l;
+    if (e < n || l != -1) bad = true;
+    return -1;
+  }
   __device__ __forceinline__ uint32_t row(int64_t e) const { return uint32_t(e < n ? e : e - n); }
   __device__ __forceinline__ float weight(int64_t e) const { return e < n ? w1[e] : w2[e - n]; }
 };
@@ -158,14 +166,24 @@ __global__ void __launch_bounds__(256) k_bucket_count(Entries en, int64_t E, int
   __syncthreads();
   const int lane = threadIdx.x & 31;
   constexpr int UNR = 8;  // labels in flight per thread
-  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  // entries are below 2^32 (the callers check): 32-bit positions
+  const uint32_t stride = gridDim.x * blockDim.x, E32 = uint32_t(E);
   // the loop bound is uniform per warp, so every lane reaches the warp collectives
-  for (int64_t base = int64_t(blockIdx.x) * blockDim.x + threadIdx.x - lane; base < E; base += stride * UNR) {
-    int b[UNR];
+  bool bad = false;
+  for (uint64_t base = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x - lane; base < E;
+       base += uint64_t(stride) * UNR) {
+    // every label load is issued before any is used (a status write between
+    // them would keep the compiler from overlapping the loads)
+    int l[UNR], b[UNR];
 #pragma unroll
     for (int i = 0; i < UNR; ++i) {
-      const int64_t e = base + i * stride + lane;
-      b[i] = e < E ? en.bucket(e, true) : -1;
+      const uint64_t e = base + uint64_t(i) * stride + lane;
+      l[i] = e < E32 ? en.label(int64_t(e)) : -1;
+    }
+#pragma unroll
+    for (int i = 0; i < UNR; ++i) {
+      const uint64_t e = base + uint64_t(i) * stride + lane;
+      b[i] = e < E32 ? en.bucket_of(int64_t(e), l[i], bad) : -1;
     }
     // shared-memory counters take one fire-and-forget increment per label;
     // global ones are aggregated per warp first
@@ -178,6 +196,7 @@ __global__ void __launch_bounds__(256) k_bucket_count(Entries en, int64_t E, int
       }
     }
   }
+  if (bad) set_status(en.status, SIL_ELABEL);
   if (priv) {
     __syncthreads();
     for (int b = threadIdx.x; b < nb; b += blockDim.x)
@@ -222,14 +241,26 @@ __global__ void __launch_bounds__(kScanThreads) k_bucket_scan(const uint32_t* bc
 // Each CTA places kScatterIPT * 256 consecutive entries.  With few buckets it
 // counts them in shared memory first and reserves one range per bucket with
 // a single global atomic (the hot buckets of skewed size distributions would
-// otherwise serialise on their cursor).
+// otherwise serialise on their cursor), then lays its entries out in bucket
+// order in shared memory, so that the index (and weight) writes are runs of
+// consecutive addresses -- one per bucket the CTA touches -- instead of
+// 4-byte scatters.
+constexpr int kScatterTile = 256 * kScatterIPT;
+
+// Dynamic shared memory of the scatter kernel: counts/starts and range bases
+// per bucket, then the staged entries (rows, bucket ids, weights).
+size_t scatter_smem(int32_t nb, bool weighted) {
+  if (nb > kScatterSmem) return 0;
+  return size_t(4) * (2 * size_t(nb) + kScatterTile) + size_t(2) * kScatterTile +
+         (weighted ? size_t(4) * kScatterTile : 0);
+}
+
 __global__ void __launch_bounds__(256) k_bucket_scatter(Entries en, int64_t E, int32_t nb, uint32_t* cursor,
                                                          uint32_t* idx, float* widx) {
-  __shared__ uint32_t lh[kScatterSmem];
-  __shared__ uint32_t lbase[kScatterSmem];
+  extern __shared__ __align__(16) uint32_t ssm[];
   const bool priv = nb <= kScatterSmem;
-  const int tid = threadIdx.x;
-  const int64_t c0 = int64_t(blockIdx.x) * (256 * kScatterIPT);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t c0 = int64_t(blockIdx.x) * kScatterTile;
   if (!priv) {
     for (int i = 0; i < kScatterIPT; ++i) {
       const int64_t e = c0 + int64_t(i) * 256 + tid;
@@ -242,6 +273,12 @@ __global__ void __launch_bounds__(256) k_bucket_scatter(Entries en, int64_t E, i
     }
     return;
   }
+  uint32_t* lh = ssm;                // [nb] counts, then local starts
+  uint32_t* lbase = ssm + nb;        // [nb] first global position of each range
+  uint32_t* srow = lbase + nb;       // [tile] rows in local bucket order
+  uint16_t* sbk = reinterpret_cast<uint16_t*>(srow + kScatterTile);  // their buckets
+  float* swt = reinterpret_cast<float*>(sbk + kScatterTile);           // their weights
+  __shared__ uint32_t wtot[8], total;
   for (int b = tid; b < nb; b += 256) lh[b] = 0;
   __syncthreads();
   int bk[kScatterIPT];
@@ -258,16 +295,46 @@ __global__ void __launch_bounds__(256) k_bucket_scatter(Entries en, int64_t E, i
   __syncthreads();
   for (int b = tid; b < nb; b += 256) {
     const uint32_t c = lh[b];
-    if (c) lbase[b] = atomicAdd(&cursor[b], c);
+    lbase[b] = c ? atomicAdd(&cursor[b], c) : 0u;
+  }
+  __syncthreads();
+  // local starts: exclusive scan of the counts (each thread a run of buckets)
+  const int per = (nb + 255) / 256;
+  const int b0 = min(nb, tid * per), b1 = min(nb, b0 + per);
+  uint32_t run = 0;
+  for (int b = b0; b < b1; ++b) run += lh[b];
+  uint32_t incl = run;
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += t;
+  }
+  if (lane == 31) wtot[warp] = incl;
+  __syncthreads();
+  uint32_t off = incl - run;
+  for (int w = 0; w < warp; ++w) off += wtot[w];
+  if (tid == 255) total = off + run;
+  for (int b = b0; b < b1; ++b) {
+    const uint32_t c = lh[b];
+    lh[b] = off;
+    off += c;
   }
   __syncthreads();
 #pragma unroll
   for (int i = 0; i < kScatterIPT; ++i) {
     if (bk[i] < 0) continue;
     const int64_t e = c0 + int64_t(i) * 256 + tid;
-    const uint32_t pos = lbase[bk[i]] + rk[i];
-    idx[pos] = en.row(e);
-    if (widx) widx[pos] = en.weight(e);
+    const uint32_t p = lh[bk[i]] + rk[i];
+    srow[p] = en.row(e);
+    sbk[p] = uint16_t(bk[i]);
+    if (widx) swt[p] = en.weight(e);
+  }
+  __syncthreads();
+  const uint32_t tot = total;
+  for (uint32_t p = tid; p < tot; p += 256) {
+    const int b = sbk[p];
+    const uint32_t pos = lbase[b] + (p - lh[b]);
+    idx[pos] = srow[p];
+    if (widx) widx[pos] = swt[p];
   }
 }
 
@@ -866,7 +933,11 @@ cudaError_t launch_label_sort(const int32_t* labels, int64_t n, int32_t k, uint3
   const size_t smem = k <= kHistSmem ? size_t(k) * 4 : 0;
   k_bucket_count<<<grid, 256, smem, stream>>>(en, n, k, bcount);
   k_bucket_scan<<<1, kScanThreads, 0, stream>>>(bcount, k, k, bstart, cursor, nullptr);
-  k_bucket_scatter<<<unsigned(cdiv(n, 256 * kScatterIPT)), 256, 0, stream>>>(en, n, k, cursor, idx, nullptr);
+  const size_t ssmem = scatter_smem(k, false);
+  if ((e = cudaFuncSetAttribute(k_bucket_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                int(scatter_smem(kScatterSmem, true)))) != cudaSuccess)
+    return e;
+  k_bucket_scatter<<<unsigned(cdiv(n, kScatterTile)), 256, ssmem, stream>>>(en, n, k, cursor, idx, nullptr);
   return cudaGetLastError();
 }
 
@@ -887,8 +958,11 @@ cudaError_t launch_aggregate(const AggLaunch& L) {
     k_bucket_count<<<grid, 256, smem, L.stream>>>(en, E, nb, L.bcount);
   }
   k_bucket_scan<<<1, kScanThreads, 0, L.stream>>>(L.bcount, nb, L.k, L.bstart, L.cursor, dual ? nullptr : L.count);
-  k_bucket_scatter<<<unsigned(cdiv(E, 256 * kScatterIPT)), 256, 0, L.stream>>>(en, E, nb, L.cursor, L.idx,
-                                                                              L.w1 ? L.widx : nullptr);
+  if ((e = cudaFuncSetAttribute(k_bucket_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                int(scatter_smem(kScatterSmem, true)))) != cudaSuccess)
+    return e;
+  k_bucket_scatter<<<unsigned(cdiv(E, kScatterTile)), 256, scatter_smem(nb, L.w1 != nullptr), L.stream>>>(
+      en, E, nb, L.cursor, L.idx, L.w1 ? L.widx : nullptr);
   // reference points: the first row of each cluster's bucket (buckets k + c
   // of the dual form share cluster c's)
   {
