@@ -379,14 +379,16 @@ def variant_lines(dev, steps, budget_s, pk_sustained, pk_sm_mhz):
             step()
             n = max(1, min(steps, 3))
             s = timed(step, n, torch.cuda.current_stream())
-            # the backward alone (dS/dX from the saved a_i, b_i, k*_i): two
-            # reads of X and one write of dX are its algorithmic bytes
-            bw = []
-            for _ in range(n):
-                Xg = X.detach().requires_grad_(True)
-                S = silhouette_loss(Xg, lab, w.K, metric)
-                bw.append(timed(S.backward, 1, torch.cuda.current_stream()))
-            tb = statistics.median(bw)
+            # the backward alone (dS/dX from the saved a_i, b_i, k*_i, the call
+            # autograd's backward makes), 10 calls back to back: two reads of X
+            # and one write of dX are its algorithmic bytes
+            agg = sil.aggregate(X, lab, w.K, metric)
+            rs = sil.score(X, lab, w.K, agg, metric, save=True)
+            dX = torch.empty_like(X)
+            sil.score_backward(X, lab, w.K, agg, metric, saved=rs.saved, out=dX)
+            tb = timed(lambda: sil.score_backward(X, lab, w.K, agg, metric, saved=rs.saved, out=dX), 10,
+                       torch.cuda.current_stream()) / 10
+            del agg, rs, dX
             nbytes = 3.0 * X.shape[0] * X.shape[1] * 4
             rf = sil.silhouette(X, lab, w.K, metric, want_s=True)  # the forward's kernels, with s_i kept
             check = oracle_sampled(X, lab, w.K, metric, rf.s, float(rf.S.item()))

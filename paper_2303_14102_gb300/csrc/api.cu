@@ -410,6 +410,10 @@ int sil_score_backward(const void* X, int32_t dtype, int64_t n, int32_t d, int64
   float* Wf = at<float>(ws, L.bw_f);
   float* Cf = Wf + size_t(k) * size_t(round_up(d, 4));
   SIL_TRY(cu(launch_backward_prep(bw_w, bw_p, k, d, Wf, Cf, st)));
+  b.idx = a.idx;
+  b.widx = a.widx;
+  b.bstart = a.bstart;
+  b.w2 = w2;
   SIL_TRY(cu(launch_backward_grad(b, Wf, Cf)));
   return cu(launch_publish_status(wst, dev_status, st));
 }

@@ -336,6 +336,12 @@ struct BackLaunch {
   float* dX;
   int64_t lddx;
   cudaStream_t stream;
+  // nullable: the dual pass 1's sort (rows and alpha in bucket order, bucket
+  // starts) and beta per row, for the gradient kernel that walks that order
+  const uint32_t* idx = nullptr;
+  const float* widx = nullptr;
+  const uint32_t* bstart = nullptr;
+  const float* w2 = nullptr;
 };
 // alpha_i / beta_i per point written into w1/w2 (float[n] each).
 cudaError_t launch_backward_weights(const BackLaunch& b, float* w1, float* w2);

@@ -45,6 +45,32 @@ def test_grad_against_oracle(metric, N, D, K):
 
 
 @pytest.mark.parametrize("metric", METRICS)
+@pytest.mark.parametrize("dtype", [torch.bfloat16, torch.float8_e4m3fn])
+@pytest.mark.parametrize("N,D,K", [(3000, 64, 12), (1500, 256, 40)])
+def test_grad_low_precision_rows_against_oracle(metric, dtype, N, D, K):
+    # BF16 / FP8 (with column scales) storage: the oracle differentiates the
+    # dequantised rows the kernels read
+    X, lab = case(300 + N + D, N, D, K, metric, empty=False, singleton=True)
+    Xt = torch.as_tensor(X).cuda()
+    cs = None
+    if dtype == torch.bfloat16:
+        Xq = Xt.to(torch.bfloat16)
+        Xd = Xq.float().cpu().double().numpy()
+    else:
+        cs = (Xt.abs().amax(0) / 448.0).clamp_min(1e-12).contiguous()
+        Xq = (Xt / cs).to(torch.float8_e4m3fn)
+        Xd = (Xq.float() * cs).cpu().double().numpy()
+    lt = torch.as_tensor(lab).cuda()
+    agg = sil.aggregate(Xq, lt, K, metric, col_scale=cs)
+    r = sil.score(Xq, lt, K, agg, metric, col_scale=cs, save=True)
+    g = sil.score_backward(Xq, lt, K, agg, metric, col_scale=cs, saved=r.saved)
+    torch.cuda.synchronize()
+    ref = oracle.linear_grad(Xd, lab, K, metric)
+    err = rel_err(g.cpu().double().numpy(), ref)
+    assert err <= 2e-4, err
+
+
+@pytest.mark.parametrize("metric", METRICS)
 def test_recompute_equals_saved(metric):
     X, lab = case(31, 2000, 10, 5, metric)
     a = gpu_grad(X, lab, 5, metric, saved=True)
