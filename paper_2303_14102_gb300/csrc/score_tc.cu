@@ -1448,30 +1448,43 @@ __global__ void k_tc_combine(int64_t n, int32_t k, int32_t nblk, const int32_t* 
 }
 
 // The labelings of a batched launch whose clusters span several blocks:
-// multi[blockIdx.y] names one (its first block's item); each CTA takes rows
-// blockIdx.x, + gridDim.x, ... and writes the labeling's partial sum
-// partials[b * gridDim.x + blockIdx.x] (the slot its fused form would use).
-__global__ void k_tc_combine_items(const TcItem* multi, int64_t n, const int32_t* labels, int64_t ldl,
-                                   const float4* cl_all, float scale, int32_t rms, const float* planes,
-                                   const float* own_planes, double* partials) {
+// multi[blockIdx.y] names one (its first block's item); each CTA takes the
+// rows of slice blockIdx.x of gridDim.x (four per thread in flight) and writes
+// the labeling's partial sum partials[b * gridDim.x + blockIdx.x] (the slot
+// its fused form would use).
+__global__ void __launch_bounds__(1024) k_tc_combine_items(const TcItem* multi, int64_t n, const int32_t* labels,
+                                                           int64_t ldl, const float4* cl_all, float scale, int32_t rms,
+                                                           const float* planes, const float* own_planes,
+                                                           double* partials) {
   const TcItem it = multi[blockIdx.y];
   const int32_t* lab = labels + int64_t(it.b) * ldl;
   const float4* cl = cl_all + it.cl_off;
+  const float* p0 = planes + int64_t(it.plane) * n;
+  const float* p1 = it.nblk > 1 ? p0 + n : p0;  // a labeling has at most two blocks
+  const float* po = own_planes + int64_t(it.own_plane) * n;
+  constexpr int U = 4;  // rows per thread in flight: every load of them issued first
   float tsum = 0.f;
-  for (int64_t row = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; row < n;
-       row += int64_t(gridDim.x) * blockDim.x) {
-    const int own = lab[row];
-    float best = INFINITY, sv = 0.f;
-    bool bad = own < 0 || own >= it.k;
-    for (int g = 0; g < it.nblk && !bad; ++g) {
-      const float v = planes[(int64_t(it.plane) + g) * n + row];
-      if (v != v) bad = true;  // NaN marks a row the scoring kernel rejected
-      else best = fminf(best, v);
+  for (int64_t base = int64_t(blockIdx.x) * blockDim.x * U + threadIdx.x; base < n;
+       base += int64_t(gridDim.x) * blockDim.x * U) {
+    int own[U];
+    float v0[U], v1[U], ao[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t row = base + int64_t(u) * blockDim.x;
+      const bool in = row < n;
+      own[u] = in ? lab[row] : -1;
+      v0[u] = in ? p0[row] : 0.f;
+      v1[u] = in ? p1[row] : 0.f;
+      ao[u] = in ? po[row] : 0.f;
     }
-    if (!bad && best < INFINITY && cl[own].w > 1.5f)
-      sv = sil_eq2(fmaxf(0.f, scale * own_planes[int64_t(it.own_plane) * n + row]), fmaxf(0.f, scale * best),
-                   rms != 0);
-    tsum += sv;
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      // NaN marks a row the scoring kernel rejected
+      const bool bad = own[u] < 0 || own[u] >= it.k || v0[u] != v0[u] || v1[u] != v1[u];
+      const float best = fminf(v0[u], v1[u]);
+      if (!bad && best < INFINITY && cl[own[u]].w > 1.5f)
+        tsum += sil_eq2(fmaxf(0.f, scale * ao[u]), fmaxf(0.f, scale * best), rms != 0);
+    }
   }
   __shared__ float red[32];
   for (int o = 16; o > 0; o >>= 1) tsum += __shfl_xor_sync(0xffffffffu, tsum, o);
@@ -2024,7 +2037,7 @@ cudaError_t launch_score_tc_batched(const void* X, int64_t n, int32_t d, int64_t
     e = cg == 2 ? launch(k_score_tc<kModeF32, 64, true, 2, true>, tc_threads(64, 2))
                 : launch(k_score_tc<kModeF32, 64, true, 1, true>, tc_threads(64, 1));
   if (e != cudaSuccess || n_multi == 0) return e;
-  k_tc_combine_items<<<dim3(ranges, unsigned(n_multi)), 256, 0, stream>>>(multi, n, labels, ldl, cl_all, k.scale,
+  k_tc_combine_items<<<dim3(ranges, unsigned(n_multi)), 1024, 0, stream>>>(multi, n, labels, ldl, cl_all, k.scale,
                                                                          k.rms, planes, own_planes, partials);
   return cudaGetLastError();
 }
