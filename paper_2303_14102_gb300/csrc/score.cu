@@ -424,11 +424,12 @@ __global__ void __launch_bounds__(64) k_score_simt_wide(ScoreK a) {
 }
 
 // S = sum of the partials / n in a fixed order; NaN when a flag was raised.
-__global__ void k_reduce_S(const double* partials, int32_t np, int64_t n, const uint32_t* ws_status,
-                           uint32_t* user_status, double* S_out) {
-  __shared__ double red[1024];
+__global__ void __launch_bounds__(256) k_reduce_S(const double* partials, int32_t np, int64_t n,
+                                                  const uint32_t* ws_status, uint32_t* user_status, double* S_out) {
+  __shared__ double wred[8];
   // four independent sums per thread keep the loads of up to kMaxPartials
-  // partials in flight (a fixed order for a given np: deterministic)
+  // partials in flight; shuffles, then the eight warp sums in order (a fixed
+  // order for a given np: deterministic)
   double t4[4] = {0.0, 0.0, 0.0, 0.0};
   const int stride = int(blockDim.x);
   int i = threadIdx.x;
@@ -436,16 +437,16 @@ __global__ void k_reduce_S(const double* partials, int32_t np, int64_t n, const 
 #pragma unroll
     for (int u = 0; u < 4; ++u) t4[u] += partials[i + u * stride];
   for (; i < np; i += stride) t4[0] += partials[i];
-  red[threadIdx.x] = (t4[0] + t4[1]) + (t4[2] + t4[3]);
+  double t = (t4[0] + t4[1]) + (t4[2] + t4[3]);
+  for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  if ((threadIdx.x & 31) == 0) wred[threadIdx.x >> 5] = t;
   __syncthreads();
-  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-    if (int(threadIdx.x) < s) red[threadIdx.x] += red[threadIdx.x + s];
-    __syncthreads();
-  }
   if (threadIdx.x == 0) {
+    double tot = 0.0;
+    for (int w = 0; w < int(blockDim.x >> 5); ++w) tot += wred[w];
     const uint32_t st = *ws_status;
     if (user_status && st) atomicOr(user_status, st);
-    if (S_out) *S_out = (st == 0 && n > 0) ? red[0] / double(n) : NAN;
+    if (S_out) *S_out = (st == 0 && n > 0) ? tot / double(n) : NAN;
   }
 }
 
@@ -599,7 +600,7 @@ cudaError_t launch_score_simt(ScoreLaunch& s) {
 
 cudaError_t launch_reduce_S(const double* partials, int32_t np, int64_t n, const uint32_t* ws_status,
                             uint32_t* user_status, double* S_out, cudaStream_t stream) {
-  k_reduce_S<<<1, 1024, 0, stream>>>(partials, np, n, ws_status, user_status, S_out);
+  k_reduce_S<<<1, 256, 0, stream>>>(partials, np, n, ws_status, user_status, S_out);
   return cudaGetLastError();
 }
 
