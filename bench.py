@@ -169,7 +169,8 @@ class ClockSampler:
                 out, _ = self.proc.communicate()
             self.lines = [l for l in out.splitlines() if l.strip()]
 
-    def summary(self):
+    def summary(self, window=None):
+        """Samples inside the timed region, or inside window = (t0, t1)."""
         import datetime
         rows = []
         for l in getattr(self, "lines", []):
@@ -182,15 +183,17 @@ class ClockSampler:
             except ValueError:
                 continue
         inside = rows
-        if self.t0 is not None and self.t1 is not None:
-            inside = [r for r in rows if self.t0 - 0.05 <= r[0] <= self.t1 + 0.05]
+        t0, t1 = window if window is not None else (self.t0, self.t1)
+        if t0 is not None and t1 is not None:
+            inside = [r for r in rows if t0 - 0.05 <= r[0] <= t1 + 0.05]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = {n for r in inside for n, v in zip(names, r[3]) if v.lower() == "active"}
         if not inside:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0,
                     "note": "no nvidia-smi sample fell inside the timed region"}
         return {"sm_mhz": statistics.median(r[1] for r in inside), "sm_max_mhz": max(r[2] for r in inside),
-                "reasons": sorted(reasons), "samples": len(inside), "window": "timed region only"}
+                "reasons": sorted(reasons), "samples": len(inside),
+                "window": "timed region only" if window is None else "given window"}
 
 
 def dist_setup(n_gpus):
@@ -585,9 +588,15 @@ def main():
         # per-pass split (same launches, events between the two calls), over
         # at least half a second of steps so that the split is steady
         split = []
+        ts0 = time.time()
         for _ in range(max(args.steps, int(0.5 / max(t / args.steps, 1e-6)) + 1)):
             step(record=split)
+        ts1 = time.time()
     clocks = clk.summary()
+    # the same steps run for the per-pass split right after the timed region,
+    # for at least half a second: many more samples of the clocks under this load
+    clocks["split_window"] = dict(clk.summary((ts0, ts1)), seconds=round(ts1 - ts0, 3),
+                                  window="the per-pass timing right after the timed region")
     t = max_over_ranks(t, world)
     S_val = float(r.S.item())
     sil.check_status(status, "bench")
