@@ -680,6 +680,37 @@ def main():
             chk = oracle_full(X64, lab_h, K, metric, Sv)
             variants[name] = {"points_per_s": N * args.steps / s, "ms": s / args.steps * 1e3, "S": Sv,
                               "dS_vs_oracle": chk["dS_vs_oracle"], "oracle_check": chk}
+        # the small workload (N 1e4, D 8, K 5, both passes of one call): launch
+        # latency, not bytes, bounds it -- microseconds per API call, and per
+        # replay of the same call captured in a CUDA graph
+        wsm = synth.workload_small(device=dev)
+        fn = lambda: sil.silhouette(wsm.X, wsm.labels, wsm.K, status=status)  # noqa: E731
+        rsm = fn()
+        t_call = timed(fn, 200, stream) / 200
+        graph_info = {}
+        try:
+            side = torch.cuda.Stream(dev)
+            side.wait_stream(stream)
+            with torch.cuda.stream(side):
+                for _ in range(3):
+                    fn()
+            stream.wait_stream(side)
+            graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(graph):
+                rg = fn()
+            graph.replay()
+            torch.cuda.synchronize()
+            graph_info = {"us_per_graph_replay": timed(graph.replay, 200, stream) / 200 * 1e6,
+                          "S_graph": float(rg.S.item())}
+            del graph, rg
+        except Exception as exc:  # the direct calls above stand on their own
+            graph_info = {"graph": f"not captured: {type(exc).__name__}: {exc}"[:200]}
+        S_sm = float(rsm.S.item())
+        chk = oracle_full(wsm.X.cpu().double().numpy(), wsm.labels.cpu().numpy(), wsm.K, "sqeuclidean", S_sm)
+        variants["small_sqeuclidean"] = dict({"us_per_call": t_call * 1e6, "points_per_s": wsm.X.shape[0] / t_call,
+                                              "S": S_sm, "dS_vs_oracle": chk["dS_vs_oracle"], "oracle_check": chk,
+                                              "N": wsm.X.shape[0], "D": wsm.X.shape[1], "K": wsm.K}, **graph_info)
+        del wsm
         # pass 2 on the CUDA cores (FP32 FFMA against Z in shared memory), the
         # path the tensor-core kernel replaces at this K, for comparison
         agg_s = sil.aggregate(X, lab, K, status=status)

@@ -18,12 +18,20 @@ pytestmark = pytest.mark.gpu
 METRICS = ["sqeuclidean", "cosine"]
 
 
-def run(X, lab, K, metric, dtype=torch.float32, col_scale=None, path="auto"):
+def run(X, lab, K, metric, dtype=torch.float32, col_scale=None, path="auto", fused=False):
+    """sil_aggregate + sil_score, or (fused) both in one sil_silhouette call."""
     Xt, lt = to_dev(X, lab, dtype) if not isinstance(X, torch.Tensor) else (X, lab)
     st = sil.new_status(Xt.device)
-    agg = sil.aggregate(Xt, lt, K, metric, col_scale=col_scale, status=st)
-    r = sil.score(Xt, lt, K, agg, metric, col_scale=col_scale, want_s=True, save=True, path=path,
-                  status=st)
+    if fused:
+        agg = (torch.empty(K, dtype=torch.int64, device=Xt.device),
+               torch.empty(K, Xt.shape[1], dtype=torch.float64, device=Xt.device),
+               torch.empty(K, dtype=torch.float64, device=Xt.device))
+        r = sil.silhouette(Xt, lt, K, metric, col_scale=col_scale, want_s=True, save=True, path=path,
+                           status=st, out=agg)
+    else:
+        agg = sil.aggregate(Xt, lt, K, metric, col_scale=col_scale, status=st)
+        r = sil.score(Xt, lt, K, agg, metric, col_scale=col_scale, want_s=True, save=True, path=path,
+                      status=st)
     torch.cuda.synchronize()
     return Xt, lt, agg, r, int(st.item())
 
@@ -142,39 +150,43 @@ def test_simt_path_forced_equals_auto():
 
 
 # ------------------------------------------------------------ edge cases
-def test_degenerate_single_cluster():
+@pytest.mark.parametrize("fused", [False, True])
+def test_degenerate_single_cluster(fused):
     X, _ = case(14, 500, 4, 3)
     lab = np.zeros(500, np.int32)
-    _, _, _, r, st = run(X, lab, 3, "sqeuclidean")
+    _, _, _, r, st = run(X, lab, 3, "sqeuclidean", fused=fused)
     assert st & sil.SIL_EDEGENERATE
     assert np.isnan(float(r.S))
     assert torch.all(r.s == 0)
 
 
-def test_bad_label_flagged():
+@pytest.mark.parametrize("fused", [False, True])
+def test_bad_label_flagged(fused):
     X, lab = case(15, 500, 4, 3)
     lab[17] = 3
-    _, _, _, r, st = run(X, lab, 3, "sqeuclidean")
+    _, _, _, r, st = run(X, lab, 3, "sqeuclidean", fused=fused)
     assert st & sil.SIL_ELABEL
     assert np.isnan(float(r.S))
 
 
-def test_zero_row_cosine_flagged():
+@pytest.mark.parametrize("fused", [False, True])
+def test_zero_row_cosine_flagged(fused):
     X, lab = case(16, 500, 4, 3, "cosine")
     X[3] = 0.0
-    _, _, _, r, st = run(X, lab, 3, "cosine")
+    _, _, _, r, st = run(X, lab, 3, "cosine", fused=fused)
     assert st & sil.SIL_EZERONORM
     assert np.isnan(float(r.S))
 
 
-def test_all_singletons_and_duplicates():
+@pytest.mark.parametrize("fused", [False, True])
+def test_all_singletons_and_duplicates(fused):
     X, _ = case(17, 40, 3, 3)
     lab = np.arange(40, dtype=np.int32)
-    _, _, _, r, st = run(X, lab, 40, "sqeuclidean")
+    _, _, _, r, st = run(X, lab, 40, "sqeuclidean", fused=fused)
     assert st == 0 and float(r.S) == 0.0
     Xd = np.repeat(np.array([[0, 0], [3, 4], [-5, 1]], np.float32), [300, 500, 200], axis=0)
     ld = np.repeat(np.array([0, 1, 2], np.int32), [300, 500, 200])
-    _, _, _, r, st = run(Xd, ld, 3, "sqeuclidean")
+    _, _, _, r, st = run(Xd, ld, 3, "sqeuclidean", fused=fused)
     assert st == 0 and abs(float(r.S) - 1.0) < 1e-6
 
 
@@ -185,6 +197,10 @@ def test_empty_input():
     assert int(count.sum()) == 0
     r = sil.score(Xt, lt, 3, (count, s1, s2))
     assert np.isnan(float(r.S))
+    out = (torch.full((3,), 7, dtype=torch.int64, device="cuda"), torch.ones(3, 4, dtype=torch.float64, device="cuda"),
+           torch.ones(3, dtype=torch.float64, device="cuda"))
+    r = sil.silhouette(Xt, lt, 3, out=out)
+    assert np.isnan(float(r.S)) and int(out[0].abs().sum()) == 0 and float(out[1].abs().sum()) == 0.0
 
 
 # ------------------------------------------------------------- batched
