@@ -1940,16 +1940,23 @@ int tc_batched_plan_set(int32_t ranges, int32_t a_buffers) {
 namespace {
 // ring depths of the batched launch for rows of dp columns and blocks of up to
 // 256 clusters (wider labelings are split into two blocks)
-bool tc_batched_plan(int dp, int* nab, int* nxs, int* smem) {
+// The deepest A ring that fits (or the one asked for), with the block's
+// centroids staged in shared memory for the converters' own-cluster term and
+// the difference form of ill-conditioned rows when they fit beside it.
+bool tc_batched_plan(int dp, int dz, int* nab, int* nxs, int* smem, int* zst) {
   const int want = g_batched_nab.load();
-  for (int b = 4; b >= 2; b -= 2) {
-    if (want && b != want) continue;
-    const int sm = tc_smem(kModeF32, dp, 256, 2, b, 0).total;
-    if (sm <= kSmemMax) {
-      *nab = b;
-      *nxs = 2;
-      *smem = sm;
-      return true;
+  for (int staged = 1; staged >= 0; --staged) {
+    const int zs = staged ? dz + 4 : 0;
+    for (int b = 4; b >= 2; b -= 2) {
+      if (want && b != want) continue;
+      const int sm = tc_smem(kModeF32, dp, 256, 2, b, zs).total;
+      if (sm <= kSmemMax) {
+        *nab = b;
+        *nxs = 2;
+        *smem = sm;
+        *zst = zs;
+        return true;
+      }
     }
   }
   return false;
@@ -1958,8 +1965,8 @@ bool tc_batched_plan(int dp, int* nab, int* nxs, int* smem) {
 
 size_t tc_batched_pack_bytes(int32_t batch, int32_t kmax, int32_t d) {
   const int dp = tc_dp(d), kmaxp = int(round_up(std::max(kmax, 16), 16));
-  int nab, nxs, smem;
-  if (!tc_batched_plan(dp, &nab, &nxs, &smem)) return 0;
+  int nab, nxs, smem, zst;
+  if (!tc_batched_plan(dp, int(round_up(d, 4)), &nab, &nxs, &smem, &zst)) return 0;
   // the blocks of a labeling (at most two) are at most 31 rows wider than its clusters
   const size_t rows = size_t(batch) * size_t(kmaxp + 32);
   return align256(rows * size_t(dp) * 2) * 2 + align256(rows * 4);
@@ -1972,8 +1979,8 @@ cudaError_t launch_score_tc_batched(const void* X, int64_t n, int32_t d, int64_t
                                     const float* gf_all, void* pack, float* planes, float* own_planes,
                                     double* partials, uint32_t* status_all, cudaStream_t stream) {
   const int dp = tc_dp(d), dz = int(round_up(d, 4));
-  int nab = 0, nxs = 0, smem = 0;
-  if (!tc_batched_plan(dp, &nab, &nxs, &smem)) return cudaErrorInvalidValue;
+  int nab = 0, nxs = 0, smem = 0, zst = 0;
+  if (!tc_batched_plan(dp, dz, &nab, &nxs, &smem, &zst)) return cudaErrorInvalidValue;
   const size_t rows = size_t(batch) * size_t(round_up(std::max(kmax, 16), 16) + 32);
   __nv_bfloat16* zh = static_cast<__nv_bfloat16*>(pack);
   __nv_bfloat16* zl = reinterpret_cast<__nv_bfloat16*>(static_cast<char*>(pack) + align256(rows * size_t(dp) * 2));
@@ -2007,7 +2014,7 @@ cudaError_t launch_score_tc_batched(const void* X, int64_t n, int32_t d, int64_t
   k.scale = dist == SIL_COSINE ? 0.5f : 1.f;
   k.nxs = nxs;
   k.nab = nab;
-  k.zst = 0;
+  k.zst = zst;
   k.xg = static_cast<const float*>(X);
   k.ldx = ldx;
   k.zf = zf_all;
