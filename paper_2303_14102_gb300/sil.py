@@ -439,7 +439,7 @@ def autotune_batched(X: torch.Tensor, labels: torch.Tensor, ks, metric: str = "s
     """Pick launch plans of sil_score_batched by timing them on these inputs.
 
     Where every labeling's pass 2 runs as one launch: the plan of that launch
-    (CTAs per labeling block in 4, 8, 16, 32 and 2 or 4 A buffers), timed on
+    (CTAs per labeling block in 4, 8, 16, 32, 64 and 2 or 4 A buffers), timed on
     the whole batched call; returns {"one_launch": (ranges, a_buffers)}.
     Otherwise :func:`autotune` for each distinct k that the split-precision
     kernel serves, on the first labeling with that k; returns {k: fastest
@@ -447,7 +447,7 @@ def autotune_batched(X: torch.Tensor, labels: torch.Tensor, ks, metric: str = "s
     if serves_one_launch(X, labels, ks):
         stream = torch.cuda.current_stream(X.device)
         results = []
-        for ranges in (4, 8, 16, 32):
+        for ranges in (4, 8, 16, 32, 64):
             for nab in (2, 4):
                 batched_plan_set(ranges, nab)
                 score_batched(X, labels, ks, metric, col_scale=col_scale)
