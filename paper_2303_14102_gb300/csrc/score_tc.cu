@@ -208,6 +208,78 @@ __device__ __forceinline__ float tc_row_dist_global(const float* xr, int d, floa
   return t;
 }
 
+// The same distance with a BF16 or FP8 row (d columns) read from global
+// memory: the values its A-buffer row holds (FP8: the code times its column
+// scale), in tc_row_dist's order of operations, so that both sources give the
+// same bits.  Rows start on 16-byte boundaries (a TMA requirement of X).
+template <int MODE, int DP>
+__device__ __forceinline__ float tc_row_dist_lp_global(const unsigned char* xr, int d, float inv, const float* gsm,
+                                                       const float* csm, const float* zg, int dz) {
+  float2 acc = make_float2(0.f, 0.f);
+  const float2 inv2 = make_float2(inv, inv);
+#pragma unroll 1
+  for (int c8 = 0; c8 < DP / 8; ++c8) {  // a rare path: few live registers
+    const int col = 8 * c8;
+    float x[8];
+    if (col + 8 <= d) {
+      if (MODE == kModeBF16) {
+        const uint4 hv = __ldg(reinterpret_cast<const uint4*>(xr + 2 * col));
+        const uint32_t hw[4] = {hv.x, hv.y, hv.z, hv.w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&hw[e]));
+          x[2 * e] = f.x;
+          x[2 * e + 1] = f.y;
+        }
+      } else {
+        const uint2 cv = __ldg(reinterpret_cast<const uint2*>(xr + col));
+        const uint32_t cw[2] = {cv.x, cv.y};
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+          const float2 f0 = fp8x2_to_float2(cw[e]), f1 = fp8x2_to_float2(cw[e] >> 16);
+          x[4 * e] = f0.x;
+          x[4 * e + 1] = f0.y;
+          x[4 * e + 2] = f1.x;
+          x[4 * e + 3] = f1.y;
+        }
+      }
+    } else {
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        float v = 0.f;
+        if (col + e < d) {
+          if (MODE == kModeBF16) {
+            v = __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(xr)[col + e]);
+          } else {
+            v = fp8x2_to_float2(uint32_t(xr[col + e])).x;
+          }
+        }
+        x[e] = v;
+      }
+    }
+#pragma unroll
+    for (int h4 = 0; h4 < 2; ++h4) {
+      const int c4 = col + 4 * h4;
+      float2 xa = make_float2(x[4 * h4], x[4 * h4 + 1]), xb = make_float2(x[4 * h4 + 2], x[4 * h4 + 3]);
+      if (MODE == kModeFP8) {
+        const float4 s4 = *reinterpret_cast<const float4*>(csm + c4);
+        xa = __fmul2_rn(xa, make_float2(s4.x, s4.y));
+        xb = __fmul2_rn(xb, make_float2(s4.z, s4.w));
+      }
+      float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (c4 < dz) z = *reinterpret_cast<const float4*>(zg + c4);
+      const float4 g = *reinterpret_cast<const float4*>(gsm + c4);
+      const float2 ca = __ffma2_rn(xa, inv2, make_float2(-g.x, -g.y));
+      const float2 cb = __ffma2_rn(xb, inv2, make_float2(-g.z, -g.w));
+      const float2 da = __fadd2_rn(ca, make_float2(-z.x, -z.y));
+      const float2 db = __fadd2_rn(cb, make_float2(-z.z, -z.w));
+      acc = __ffma2_rn(da, da, acc);
+      acc = __ffma2_rn(db, db, acc);
+    }
+  }
+  return acc.x + acc.y;
+}
+
 // The expanded form d_k = ||x'||^2 + v_k, v_k = cb_k - 2 inv x.mu'_k, loses
 // about log2(kappa) bits to cancellation, kappa = (||x inv|| + ||mu'_k||)^2 / d_k,
 // and the tensor-core sums round towards zero, so that loss is a bias that
@@ -332,7 +404,8 @@ struct TcK {
   int32_t nxs;  // raw X stages (MODE 0, 2)
   int32_t nab;  // A buffers
   int32_t zst;  // stride of the staged centroids (0: not staged)
-  const float* xg;  // the rows (FP32), for the difference form of ill-conditioned rows
+  int32_t own_rows;  // 1: the converters take the own-cluster term a warp per row (tc_own_term_by_warp; one group)
+  const void* xg;  // the rows, for the difference form of ill-conditioned rows
   int64_t ldx;
   const float* zf;
   const float4* cl;
@@ -470,6 +543,97 @@ __global__ void k_selftest_wait(uint32_t* out) {
   __syncthreads();
 }
 
+// The exact own-cluster term ||x' - mu'_c||^2 (x' = x inv - g) of the rows of
+// one converter warp whose cluster c is in this block, a row at a time with
+// every lane on DP/32 consecutive columns, so that the centroid row and the
+// point row are read coalesced: for plans of several cluster blocks whose
+// centroids stay in global memory, where a thread per half row would gather a
+// centroid row 16 bytes at a time.  The point row comes from the tile's A
+// buffer (BF16: as stored; FP8: the code times its column scale), or, FP32,
+// from global memory (the A buffer holds its hi/lo split); the arithmetic per
+// element is the converters'.  want: this lane is the first half of a row
+// that needs the term (lanes 0-15 hold rows wr0 + lane); returns the term for
+// those lanes and keep for the others.  Warp-collective.
+template <int MODE, int DP>
+__device__ __forceinline__ float tc_own_term_by_warp(const TcK& a, const unsigned char* ab, const unsigned char* gsm_b,
+                                                     const unsigned char* csm_b, const float* zfp, int kb0,
+                                                     int64_t row0, int wr0, int lane, bool want, int ol, float inv,
+                                                     float keep) {
+  constexpr int CPL = DP / 32;  // columns per lane
+  constexpr int NB = 4;         // rows with their loads in flight
+  const float* gsm = reinterpret_cast<const float*>(gsm_b);
+  const float* csm = reinterpret_cast<const float*>(csm_b);
+  const int c0 = CPL * lane;
+  float gl[CPL], sc[CPL];
+#pragma unroll
+  for (int e = 0; e < CPL; ++e) {
+    gl[e] = gsm[c0 + e];
+    sc[e] = MODE == kModeFP8 ? csm[c0 + e] : 1.f;
+  }
+  __syncwarp();  // FP8: the warp's own A rows, written by its lanes
+  unsigned m = __ballot_sync(0xffffffffu, want);
+  float out = keep;
+  while (m) {
+    int rr[NB];
+    float xv[NB][CPL], zv[NB][CPL];
+#pragma unroll
+    for (int j = 0; j < NB; ++j) {
+      rr[j] = m ? __ffs(m) - 1 : -1;  // warp-uniform
+      m &= m - 1;
+    }
+#pragma unroll
+    for (int j = 0; j < NB; ++j) {
+#pragma unroll
+      for (int e = 0; e < CPL; ++e) xv[j][e] = zv[j][e] = 0.f;
+      if (rr[j] < 0) continue;
+      const int olj = __shfl_sync(0xffffffffu, ol, rr[j]);
+      const float* zr = zfp + int64_t(kb0 + olj) * a.dz;
+#pragma unroll
+      for (int e = 0; e < CPL; ++e) zv[j][e] = c0 + e < a.dz ? __ldg(zr + c0 + e) : 0.f;
+      const int R = wr0 + rr[j];  // tile row
+      if (MODE == kModeF32) {
+        const float* xr = static_cast<const float*>(a.xg) + (row0 + R) * a.ldx;
+#pragma unroll
+        for (int e = 0; e < CPL; ++e) xv[j][e] = c0 + e < a.d ? __ldg(xr + c0 + e) : 0.f;
+      } else {
+        // BF16 operand row R (128-byte swizzle in atoms of 64 columns): the
+        // lane's CPL columns lie in one 16-byte chunk
+        const unsigned char* p = ab + (c0 / 64) * kAtomBytes + sw128(R, (c0 % 64) / 8) + (c0 % 8) * 2;
+        uint32_t w[(CPL + 1) / 2];
+        if constexpr (CPL == 4) {
+          const uint2 u = *reinterpret_cast<const uint2*>(p);
+          w[0] = u.x;
+          w[1] = u.y;
+        } else if constexpr (CPL == 2) {
+          w[0] = *reinterpret_cast<const uint32_t*>(p);
+        } else {
+          w[0] = *reinterpret_cast<const unsigned short*>(p);
+        }
+#pragma unroll
+        for (int e = 0; e < CPL; ++e) {
+          const float v = __uint_as_float((e & 1 ? w[e / 2] >> 16 : w[e / 2]) << 16);
+          xv[j][e] = MODE == kModeFP8 ? v * sc[e] : v;
+        }
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < NB; ++j) {
+      if (rr[j] < 0) continue;
+      const float invj = __shfl_sync(0xffffffffu, inv, rr[j]);
+      float p = 0.f;
+#pragma unroll
+      for (int e = 0; e < CPL; ++e) {
+        const float dd = fmaf(xv[j][e], invj, -gl[e]) - zv[j][e];
+        p = fmaf(dd, dd, p);
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) p += __shfl_xor_sync(0xffffffffu, p, o);
+      if (lane == rr[j]) out = p;
+    }
+  }
+  return out;
+}
+
 template <int MODE, int DP, bool TRACK, int CG, bool BATCH = false>
 __global__ void __launch_bounds__(tc_threads(DP, CG), 1) k_score_tc(TcK a, const __grid_constant__ TcMaps maps) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -488,10 +652,12 @@ __global__ void __launch_bounds__(tc_threads(DP, CG), 1) k_score_tc(TcK a, const
     if (threadIdx.x == 0) set_status(a.status + (BATCH ? a.items[blockIdx.y].b : 0), SIL_EUNSUPPORTED);
     return;
   }
-  // where the epilogue reads an ill-conditioned row back: FP32 plans without
-  // the argmin pass (few such rows) from global memory, so that an A buffer is
-  // free once its MMAs are; the others from the A buffer, held until then
-  constexpr bool ROWS_GLOBAL = MODE == kModeF32 && !TRACK;
+  // where the epilogue reads an ill-conditioned row back: FP32 and FP8 plans
+  // without the argmin pass (few such rows) from global memory, so that an A
+  // buffer is free once its MMAs are; the others from the A buffer, held until
+  // then (a BF16 tile's buffer also carries the labels and row-term slot that
+  // the epilogue reads, which hold it anyway)
+  constexpr bool ROWS_GLOBAL = STAGED && !TRACK;
   const TcSmem L = tc_smem(MODE, DP, a.kp, a.nxs, a.nab, a.zst);
   const TcBars B = tc_bars(base, L, a.nxs, a.nab);
   volatile int* abort_flag = B.abort_flag;
@@ -832,26 +998,38 @@ __global__ void __launch_bounds__(tc_threads(DP, CG), 1) k_score_tc(TcK a, const
       // each, two columns per packed FP32x2 instruction
       float2 xn2 = make_float2(0.f, 0.f), ae = xn2;
       const float2 inv2 = make_float2(inv, inv);
+      if (!(CG == 1 && a.own_rows)) {  // uniform branch
 #pragma unroll
-      for (int c4 = 0; c4 < HP / 4; ++c4) {
-        const int col = h * HP + 4 * c4;
-        const float4 g = *reinterpret_cast<const float4*>(gsm + col);
-        float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (col < a.dz) {
-          if (a.zst)  // staged centroids (uniform branch)
-            z = *reinterpret_cast<const float4*>(zsm + olc * a.zst + col);
-          else
-            z = __ldg(reinterpret_cast<const float4*>(zfp + int64_t(kb0 + olc) * a.dz + col));
+        for (int c4 = 0; c4 < HP / 4; ++c4) {
+          const int col = h * HP + 4 * c4;
+          const float4 g = *reinterpret_cast<const float4*>(gsm + col);
+          float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (col < a.dz) {
+            if (a.zst)  // staged centroids (uniform branch)
+              z = *reinterpret_cast<const float4*>(zsm + olc * a.zst + col);
+            else
+              z = __ldg(reinterpret_cast<const float4*>(zfp + int64_t(kb0 + olc) * a.dz + col));
+          }
+          const float2 xa = make_float2(x[4 * c4], x[4 * c4 + 1]), xb = make_float2(x[4 * c4 + 2], x[4 * c4 + 3]);
+          const float2 ca = __ffma2_rn(xa, inv2, make_float2(-g.x, -g.y));
+          const float2 cb = __ffma2_rn(xb, inv2, make_float2(-g.z, -g.w));
+          xn2 = __ffma2_rn(ca, ca, xn2);
+          xn2 = __ffma2_rn(cb, cb, xn2);
+          const float2 da = __fadd2_rn(ca, make_float2(-z.x, -z.y));
+          const float2 db = __fadd2_rn(cb, make_float2(-z.z, -z.w));
+          ae = __ffma2_rn(da, da, ae);
+          ae = __ffma2_rn(db, db, ae);
         }
-        const float2 xa = make_float2(x[4 * c4], x[4 * c4 + 1]), xb = make_float2(x[4 * c4 + 2], x[4 * c4 + 3]);
-        const float2 ca = __ffma2_rn(xa, inv2, make_float2(-g.x, -g.y));
-        const float2 cb = __ffma2_rn(xb, inv2, make_float2(-g.z, -g.w));
-        xn2 = __ffma2_rn(ca, ca, xn2);
-        xn2 = __ffma2_rn(cb, cb, xn2);
-        const float2 da = __fadd2_rn(ca, make_float2(-z.x, -z.y));
-        const float2 db = __fadd2_rn(cb, make_float2(-z.z, -z.w));
-        ae = __ffma2_rn(da, da, ae);
-        ae = __ffma2_rn(db, db, ae);
+      } else {  // the own-cluster term comes from tc_own_term_by_warp
+#pragma unroll
+        for (int c4 = 0; c4 < HP / 4; ++c4) {
+          const float4 g = *reinterpret_cast<const float4*>(gsm + h * HP + 4 * c4);
+          const float2 xa = make_float2(x[4 * c4], x[4 * c4 + 1]), xb = make_float2(x[4 * c4 + 2], x[4 * c4 + 3]);
+          const float2 ca = __ffma2_rn(xa, inv2, make_float2(-g.x, -g.y));
+          const float2 cb = __ffma2_rn(xb, inv2, make_float2(-g.z, -g.w));
+          xn2 = __ffma2_rn(ca, ca, xn2);
+          xn2 = __ffma2_rn(cb, cb, xn2);
+        }
       }
       float xn2s = xn2.x + xn2.y, aes = ae.x + ae.y;
       xn2s += __shfl_xor_sync(0xffffffffu, xn2s, 16);
@@ -885,6 +1063,9 @@ __global__ void __launch_bounds__(tc_threads(DP, CG), 1) k_score_tc(TcK a, const
         if (lane == 0) mbar_arrive(&B.afull[i]);
         if (!tc_wait(&B.sempty[sl], ((t / kSideSlots) & 1) ^ 1, abort_flag, sts)) break;
       }
+      if (CG == 1 && a.own_rows) aes = tc_own_term_by_warp<MODE, DP>(a, ab, base + L.gsm, base + L.csm, zfp, kb0,
+                                                          (blockIdx.x + int64_t(t) * gridDim.x) * kTM,
+                                                          r - (lane & 15), lane, in_blk && h == 0, ol, inv, aes);
       if (h == 0) {
         float aown = 0.f;
         int code = valid ? kOwnElsewhere : kRowInvalid;
@@ -947,8 +1128,13 @@ __global__ void __launch_bounds__(tc_threads(DP, CG), 1) k_score_tc(TcK a, const
         const float4 co = clsm[kb];
         const float wn = co.y > 0.f ? co.z / co.y : 0.f;  // W_k / n_k
         if (ROWS_GLOBAL) {
-          dk = wn + tc_row_dist_global<true>(a.xg + row * a.ldx, a.d, side[2 * kTM + r], gsm,
-                                             a.zst ? zsm + kb * a.zst : zfp + int64_t(kb0 + kb) * a.dz);
+          const float* zk = a.zst ? zsm + kb * a.zst : zfp + int64_t(kb0 + kb) * a.dz;
+          if (MODE == kModeF32)
+            dk = wn + tc_row_dist_global<true>(static_cast<const float*>(a.xg) + row * a.ldx, a.d, side[2 * kTM + r],
+                                               gsm, zk);
+          else
+            dk = wn + tc_row_dist_lp_global<MODE, DP>(static_cast<const unsigned char*>(a.xg) + row * a.ldx, a.d,
+                                                      side[2 * kTM + r], gsm, csm, zk, a.dz);
         } else {
           if (!STAGED) tc_wait(&B.afull[i], (t / a.nab) & 1, abort_flag, sts);  // TMA-written rows
           dk = wn + tc_row_dist<MODE, DP>(base + L.abuf + i * L.abuf_stride, L.lo_off, r, side[2 * kTM + r], gsm,
@@ -1346,7 +1532,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_score_tc_wide(TcK a, const __
         // from global memory (the chunked A buffers hold only part of it)
         const float4 co = clsm[kb];
         const float wn = co.y > 0.f ? co.z / co.y : 0.f;  // W_k / n_k
-        dk = wn + tc_row_dist_global<false>(a.xg + row * a.ldx, a.d, inv, gsm, a.zf + int64_t(kb0 + kb) * a.dz);
+        dk = wn + tc_row_dist_global<false>(static_cast<const float*>(a.xg) + row * a.ldx, a.d, inv, gsm,
+                                            a.zf + int64_t(kb0 + kb) * a.dz);
       }
       if (row < a.n) {
         if (fused) {
@@ -1838,7 +2025,7 @@ cudaError_t launch_score_tc(const ScoreLaunch& s, const double* g, void* pack, v
   k.nxs = plan.nxs;
   k.nab = plan.nab;
   k.zst = plan.zst;
-  k.xg = mode == kModeF32 ? static_cast<const float*>(s.X) : nullptr;
+  k.xg = s.X;
   k.ldx = s.ldx;
   k.zf = s.zf;
   k.cl = s.cl;
@@ -1869,6 +2056,9 @@ cudaError_t launch_score_tc(const ScoreLaunch& s, const double* g, void* pack, v
   const dim3 grid(unsigned(std::min<int64_t>(ntiles, per_block)), unsigned(plan.nblk));
   const int cg = dp == 256 ? 1 : tc_conv_groups(mode, dp, kp);
   const int threads = dp == 256 ? kTcThreads : tc_threads(dp, cg);
+  // the kernels of one converter group take the own-cluster term a warp per
+  // row where the centroids stay in global memory
+  k.own_rows = plan.nblk > 1 && plan.zst == 0 && dp != 256 && cg == 1 ? 1 : 0;
   auto launch = [&](auto fn) {
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, plan.smem);
     if (e != cudaSuccess) return e;
@@ -2015,7 +2205,7 @@ cudaError_t launch_score_tc_batched(const void* X, int64_t n, int32_t d, int64_t
   k.nxs = nxs;
   k.nab = nab;
   k.zst = zst;
-  k.xg = static_cast<const float*>(X);
+  k.xg = X;
   k.ldx = ldx;
   k.zf = zf_all;
   k.cl = cl_all;

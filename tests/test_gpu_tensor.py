@@ -192,6 +192,32 @@ def test_fp8_tensor_path_against_bruteforce(metric, N, K):
     assert np.mean(ks.cpu().numpy()[ok] == ref["kstar"][ok]) > 0.995
 
 
+@pytest.mark.parametrize("metric", METRICS)
+@pytest.mark.parametrize("dtype,D,K", [(torch.float32, 100, 513), (torch.bfloat16, 128, 300),
+                                       (torch.float8_e4m3fn, 128, 300), (torch.float32, 64, 1000)])
+def test_own_cluster_term_of_unstaged_block_plans(metric, dtype, D, K):
+    # plans of several cluster blocks whose centroids stay in global memory
+    # take a_i from a separate kernel (lanes of a warp share a row) instead of
+    # the converter warps: a_i and s_i element by element against brute force
+    p = sil.tensor_plan_candidates(dtype, D, K, 1)[0]
+    assert p[3] == 0 and -(-K // p[0]) > 1, p
+    N = 3001
+    X, lab = case(1300 + D + K, N, D, K, metric)
+    cs = None
+    if dtype == torch.float8_e4m3fn:
+        q, scale = synth.to_fp8_e4m3(torch.as_tensor(X))
+        Xt, lt, cs = q.cuda(), torch.as_tensor(lab).cuda(), scale.cuda()
+    else:
+        Xt, lt = to_dev(X, lab, dtype)
+    r, st = run(Xt, lt, K, metric, "tensor", cs=cs)
+    ref = oracle.bruteforce(dequant(Xt, cs), lab, K, metric)
+    assert st == 0
+    assert_scores(r.s, r.S, ref, what=f"own term {metric} {dtype} D={D} K={K}")
+    a, b, ks = sil.unpack_saved(r.saved, N)
+    ok = ref["s"] != 0
+    np.testing.assert_allclose(a.cpu().double().numpy()[ok], ref["a"][ok], rtol=1e-4, atol=1e-4)
+
+
 @pytest.mark.parametrize("storage", ["bf16", "fp8"])
 def test_precision_recipe_subsample(storage):
     # the precision workload's recipe (centres at radius 1e3, d = 128,
