@@ -431,7 +431,7 @@ struct TcMaps {
 
 // Shared-memory plan (byte offsets from a 1024-aligned base).
 struct TcSmem {
-  int zh, zl, abuf, abuf_stride, lo_off, xs, xs_stride, side, side_stride, cb, gsm, csm, clsm, zsm,
+  int zh, zl, abuf, abuf_stride, lo_off, alab, xs, xs_stride, side, side_stride, cb, gsm, csm, clsm, zsm,
       zst, bars, total;
 };
 
@@ -461,14 +461,17 @@ __host__ __device__ inline TcSmem tc_smem(int mode, int dp, int kp, int nxs, int
   s.lo_off = natom_a * kTM * rowb;
   s.abuf_stride = natom_a * kTM * rowb * (mode == kModeF32 ? 2 : 1);
   o += nab * s.abuf_stride;
+  s.alab = o;  // BF16: the labels of the tile in A buffer i (TMA, with the tile)
+  o += staged ? 0 : nab * kTM * 4;
+  o = (o + 1023) & ~1023;
   s.xs = o;
   s.xs_stride = staged ? raw_tile_bytes(mode, wide ? 64 : dp) + 1024 : 0;  // + labels (512 B), keeps 1024 alignment
   o += staged ? nxs * s.xs_stride : 0;
   s.side = o;
-  s.side_stride = kTM * 16 + 512;  // xn2, aown, inv, code + labels (BF16 mode)
-  // BF16: one slot per A buffer (TMA writes the labels beside the tile);
-  // otherwise a ring of its own, so that an A buffer is free once its MMAs are
-  o += (staged ? kSideSlots : nab) * s.side_stride;
+  s.side_stride = kTM * 16 + 512;  // xn2, aown, inv, code (+ scratch of the wide kernel)
+  // a ring of its own, so that an A buffer is free once its MMAs (and, BF16,
+  // the converters' reads) are done
+  o += kSideSlots * s.side_stride;
   s.cb = o; o += kp * 4 + 32;  // + 8 floats of block-reduction scratch
   o = (o + 15) & ~15;
   s.gsm = o; o += dp * 4;
@@ -483,7 +486,7 @@ __host__ __device__ inline TcSmem tc_smem(int mode, int dp, int kp, int nxs, int
 }
 
 struct TcBars {
-  uint64_t *xfull, *xempty, *afull, *aempty, *pfull, *accfull, *accempty, *zfull, *sfull, *sempty;
+  uint64_t *xfull, *xempty, *afull, *aempty, *accfull, *accempty, *zfull, *sfull, *sempty;
   uint32_t* tmem_base;
   int* abort_flag;
 };
@@ -495,7 +498,6 @@ __device__ inline TcBars tc_bars(unsigned char* base, const TcSmem& L, int nxs, 
   b.xempty = p; p += nxs;
   b.afull = p; p += nab;
   b.aempty = p; p += nab;
-  b.pfull = p; p += nab;
   b.accfull = p; p += 2;
   b.accempty = p; p += 2;
   b.zfull = p; p += 1;
@@ -652,12 +654,11 @@ __global__ void __launch_bounds__(tc_threads(DP, CG), 1) k_score_tc(TcK a, const
     if (threadIdx.x == 0) set_status(a.status + (BATCH ? a.items[blockIdx.y].b : 0), SIL_EUNSUPPORTED);
     return;
   }
-  // where the epilogue reads an ill-conditioned row back: FP32 and FP8 plans
-  // without the argmin pass (few such rows) from global memory, so that an A
-  // buffer is free once its MMAs are; the others from the A buffer, held until
-  // then (a BF16 tile's buffer also carries the labels and row-term slot that
-  // the epilogue reads, which hold it anyway)
-  constexpr bool ROWS_GLOBAL = STAGED && !TRACK;
+  // where the epilogue reads an ill-conditioned row back: plans without the
+  // argmin pass (few such rows) from global memory, so that an A buffer is
+  // free once its MMAs (and, BF16, the converters' reads) are done; the others
+  // from the A buffer, held until then
+  constexpr bool ROWS_GLOBAL = !TRACK;
   const TcSmem L = tc_smem(MODE, DP, a.kp, a.nxs, a.nab, a.zst);
   const TcBars B = tc_bars(base, L, a.nxs, a.nab);
   volatile int* abort_flag = B.abort_flag;
@@ -711,9 +712,9 @@ __global__ void __launch_bounds__(tc_threads(DP, CG), 1) k_score_tc(TcK a, const
     }
     for (int i = 0; i < a.nab; ++i) {
       mbar_init(&B.afull[i], STAGED ? kConvWarps : 1);  // converters, or the TMA transaction
-      // MMA commit (+ the 4 epilogue warps where they read the operand rows back)
-      mbar_init(&B.aempty[i], ROWS_GLOBAL ? 1 : 1 + 4);
-      mbar_init(&B.pfull[i], kConvWarps);  // BF16 mode: the row terms are written
+      // MMA commit (+ BF16: the converter warps; + the 4 epilogue warps where
+      // they read the operand rows back)
+      mbar_init(&B.aempty[i], 1 + (STAGED ? 0 : kConvWarps) + (ROWS_GLOBAL ? 0 : 4));
     }
     for (int i = 0; i < 2; ++i) {
       mbar_init(&B.accfull[i], 1);
@@ -790,8 +791,8 @@ __global__ void __launch_bounds__(tc_threads(DP, CG), 1) k_score_tc(TcK a, const
           mbar_arrive_expect_tx(&B.afull[i], uint32_t(natom * kAtomBytes + kTM * 4));
           for (int at = 0; at < natom; ++at)
             tma_load_2d(ab + at * kAtomBytes, &maps.x, at * 64, row0, &B.afull[i]);
-          if constexpr (!BATCH) tma_load_1d(base + L.side + i * L.side_stride + kTM * 16, &maps.lab, row0, &B.afull[i]);
-          else tma_load_2d(base + L.side + i * L.side_stride + kTM * 16, &maps.lab, row0, lab_b, &B.afull[i]);
+          if constexpr (!BATCH) tma_load_1d(base + L.alab + i * kTM * 4, &maps.lab, row0, &B.afull[i]);
+          else tma_load_2d(base + L.alab + i * kTM * 4, &maps.lab, row0, lab_b, &B.afull[i]);
         }
       }
       if (*abort_flag) {
@@ -884,7 +885,7 @@ __global__ void __launch_bounds__(tc_threads(DP, CG), 1) k_score_tc(TcK a, const
       const int i = t % a.nab;
       const int64_t row = (blockIdx.x + int64_t(t) * gridDim.x) * kTM + r;
       unsigned char* ab = base + L.abuf + i * L.abuf_stride;
-      const int sl = STAGED ? t % kSideSlots : i;  // row-term slot
+      const int sl = t % kSideSlots;  // row-term slot
       float* side = reinterpret_cast<float*>(base + L.side + sl * L.side_stride);
       float x[HP];
       int own;
@@ -967,7 +968,7 @@ __global__ void __launch_bounds__(tc_threads(DP, CG), 1) k_score_tc(TcK a, const
             x[8 * c8 + 2 * e + 1] = f.y;
           }
         }
-        own = reinterpret_cast<const int32_t*>(reinterpret_cast<unsigned char*>(side) + kTM * 16)[r];
+        own = reinterpret_cast<const int32_t*>(base + L.alab + i * kTM * 4)[r];
       }
       bool valid = row < a.n;
       if (valid && (own < 0 || own >= kall)) {
@@ -1061,11 +1062,18 @@ __global__ void __launch_bounds__(tc_threads(DP, CG), 1) k_score_tc(TcK a, const
         // for their slot
         __syncwarp();
         if (lane == 0) mbar_arrive(&B.afull[i]);
-        if (!tc_wait(&B.sempty[sl], ((t / kSideSlots) & 1) ^ 1, abort_flag, sts)) break;
       }
       if (CG == 1 && a.own_rows) aes = tc_own_term_by_warp<MODE, DP>(a, ab, base + L.gsm, base + L.csm, zfp, kb0,
                                                           (blockIdx.x + int64_t(t) * gridDim.x) * kTM,
                                                           r - (lane & 15), lane, in_blk && h == 0, ol, inv, aes);
+      if (!STAGED) {
+        // the operand rows and labels are read: TMA (async proxy) may refill
+        // the buffer once the MMAs are done too
+        fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&B.aempty[i]);
+      }
+      if (!tc_wait(&B.sempty[sl], ((t / kSideSlots) & 1) ^ 1, abort_flag, sts)) break;
       if (h == 0) {
         float aown = 0.f;
         int code = valid ? kOwnElsewhere : kRowInvalid;
@@ -1080,7 +1088,7 @@ __global__ void __launch_bounds__(tc_threads(DP, CG), 1) k_score_tc(TcK a, const
         reinterpret_cast<int*>(side)[3 * kTM + r] = code;
       }
       __syncwarp();
-      if (lane == 0) mbar_arrive(STAGED ? &B.sfull[sl] : &B.pfull[i]);
+      if (lane == 0) mbar_arrive(&B.sfull[sl]);
     }
   } else {
     // ---------------------------------------------- epilogue warps EPI0..
@@ -1094,13 +1102,9 @@ __global__ void __launch_bounds__(tc_threads(DP, CG), 1) k_score_tc(TcK a, const
     const float rb = tc_cond_radius(clp, kall, gsm, DP, lane);
     float tsum = 0.f;
     for (int t = eg; eg < egs && t < my_tiles; t += egs) {
-      const int i = t % a.nab, bsel = t & sl_mask, sl = STAGED ? t % kSideSlots : i;
+      const int i = t % a.nab, bsel = t & sl_mask, sl = t % kSideSlots;
       if (!tc_wait(&B.accfull[bsel], (t >> sl_shift) & 1, abort_flag, sts)) break;
-      if (STAGED) {
-        if (!tc_wait(&B.sfull[sl], (t / kSideSlots) & 1, abort_flag, sts)) break;
-      } else if (!tc_wait(&B.pfull[i], (t / a.nab) & 1, abort_flag, sts)) {
-        break;
-      }
+      if (!tc_wait(&B.sfull[sl], (t / kSideSlots) & 1, abort_flag, sts)) break;
       tc_fence_after();
       const float* side = reinterpret_cast<const float*>(base + L.side + sl * L.side_stride);
       const int code = reinterpret_cast<const int*>(side)[3 * kTM + r];
@@ -1142,8 +1146,10 @@ __global__ void __launch_bounds__(tc_threads(DP, CG), 1) k_score_tc(TcK a, const
                                           a.dz);
         }
       }
-      if (STAGED && !ROWS_GLOBAL) {
-        // the operand rows are read: the converters may rebuild the buffer
+      if (!ROWS_GLOBAL) {
+        // the operand rows are read: the converters (or, BF16, TMA) may
+        // rebuild the buffer
+        if (!STAGED) fence_proxy_async_smem();
         __syncwarp();
         if (lane == 0) mbar_arrive(&B.aempty[i]);
       }
@@ -1175,10 +1181,8 @@ __global__ void __launch_bounds__(tc_threads(DP, CG), 1) k_score_tc(TcK a, const
           if (own >= 0) a.pown[own_plane * a.n + row] = side[kTM + r];
         }
       }
-      // BF16: the A buffer (refilled by TMA) also holds the labels of the slot
-      if (!STAGED) fence_proxy_async_smem();
       __syncwarp();
-      if (lane == 0) mbar_arrive(STAGED ? &B.sempty[sl] : &B.aempty[i]);
+      if (lane == 0) mbar_arrive(&B.sempty[sl]);
     }
     if (fused) {
       // block partial over the epilogue threads
