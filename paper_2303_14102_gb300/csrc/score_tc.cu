@@ -1137,8 +1137,9 @@ __global__ void __launch_bounds__(tc_threads(DP, CG), 1) k_score_tc(TcK a, const
             dk = wn + tc_row_dist_global<true>(static_cast<const float*>(a.xg) + row * a.ldx, a.d, side[2 * kTM + r],
                                                gsm, zk);
           else
-            dk = wn + tc_row_dist_lp_global<MODE, DP>(static_cast<const unsigned char*>(a.xg) + row * a.ldx, a.d,
-                                                      side[2 * kTM + r], gsm, csm, zk, a.dz);
+            dk = wn + tc_row_dist_lp_global<MODE, DP>(
+                          static_cast<const unsigned char*>(a.xg) + row * a.ldx * (MODE == kModeBF16 ? 2 : 1), a.d,
+                          side[2 * kTM + r], gsm, csm, zk, a.dz);
         } else {
           if (!STAGED) tc_wait(&B.afull[i], (t / a.nab) & 1, abort_flag, sts);  // TMA-written rows
           dk = wn + tc_row_dist<MODE, DP>(base + L.abuf + i * L.abuf_stride, L.lo_off, r, side[2 * kTM + r], gsm,

@@ -369,21 +369,29 @@ def test_close_clusters_match_the_oracle_without_bias(dtype, D, path, metric):
 
 @pytest.mark.parametrize("metric", METRICS)
 @pytest.mark.parametrize("save", [False, True])
-@pytest.mark.parametrize("D,k", [(64, 120), (32, 200), (64, 400)])
-def test_ill_conditioned_rows_are_finished_in_the_difference_form(metric, save, D, k):
+@pytest.mark.parametrize("dtype,D,k", [(torch.float32, 64, 120), (torch.float32, 32, 200), (torch.float32, 64, 400),
+                                       (torch.bfloat16, 64, 120), (torch.bfloat16, 128, 400),
+                                       (torch.float8_e4m3fn, 128, 120), (torch.float8_e4m3fn, 128, 400)])
+def test_ill_conditioned_rows_are_finished_in_the_difference_form(metric, save, dtype, D, k):
     # Voronoi cells: most rows' expanded form is ill-conditioned, so b_i of
     # those rows is the GEMM's nearest cluster recomputed in the difference
     # form (one cluster block for k <= 256, two blocks and the combine kernel
     # above).  Every s_i, b_i and argmin against the oracle, with and without
-    # the backward record (the argmin tracked in the main pass, or found by a
-    # second pass over the accumulator).
+    # the backward record (the argmin tracked in the main pass and the row
+    # read from the A buffer, or found by a second pass over the accumulator
+    # and the row read back from global memory), for every storage type.
     X, labs, ks = _close_clusters(30_000, D, k, k, B=1)
     lab = labs[0].contiguous()
-    agg = sil.aggregate(X, lab, k, metric)
-    r = sil.score(X, lab, k, agg, metric, want_s=True, save=save, path="tensor")
+    cs = None
+    if dtype == torch.float8_e4m3fn:
+        X, cs = synth.to_fp8_e4m3(X)
+    else:
+        X = X.to(dtype)
+    agg = sil.aggregate(X, lab, k, metric, col_scale=cs)
+    r = sil.score(X, lab, k, agg, metric, col_scale=cs, want_s=True, save=save, path="tensor")
     torch.cuda.synchronize()
-    ref = oracle.linear(X.cpu().double().numpy(), lab.cpu().numpy(), k, metric)
-    assert_scores(r.s, r.S, ref, what=f"close {metric} D={D} k={k} save={save}")
+    ref = oracle.linear(dequant(X, cs), lab.cpu().numpy(), k, metric)
+    assert_scores(r.s, r.S, ref, what=f"close {metric} {dtype} D={D} k={k} save={save}")
     if save:
         a, b, ks_ = sil.unpack_saved(r.saved, X.shape[0])
         np.testing.assert_allclose(b.cpu().double().numpy(), ref["b"], rtol=1e-4, atol=1e-4)
