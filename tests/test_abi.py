@@ -147,6 +147,12 @@ def test_tensor_plan_is_host_arithmetic():
     # four blocks of 256 (two A buffers beside the resident split centroids)
     assert sil.tensor_plan(torch.float32, 64, 100) == (112, 1)
     assert sil.tensor_plan(torch.bfloat16, 128, 1000) == (256, 4)
+    # the precision recipe's other storage types: the fastest of the
+    # best-modelled candidates when timed on a GB300 (FP8 blocks of 256,
+    # FP32 seven blocks of 144 with one A buffer)
+    assert sil.tensor_plan_candidates(torch.float8_e4m3fn, 128, 1000, 1)[0] == (256, 2, 1, 0, 0)
+    assert sil.tensor_plan_candidates(torch.float32, 128, 1000, 1)[0] == (144, 1, 1, 0, 0)
+    assert sil.tensor_plan_candidates(torch.bfloat16, 128, 1000, 1)[0] == (256, 2, 1, 0, 0)
     for dt, d, k in [(torch.float32, 128, 256), (torch.float8_e4m3fn, 128, 1000),
                      (torch.float32, 32, 513), (torch.bfloat16, 64, 4096)]:
         bk, nb = sil.tensor_plan(dt, d, k)
